@@ -1,0 +1,269 @@
+/*
+ * hespmv: encrypted sparse matrix-vector multiplication over the CSSC format
+ * on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: "Efficient Privacy-Preserving Sparse Matrix-Vector Multiplication
+ * Using Homomorphic Encryption" (CSSC format, Section 4.3; Algorithms 1-5).
+ * The matrix owner encodes its CSR matrix as CSSC, splits it into
+ * ciphertext-sized chunks and encrypts the chunk values; the vector owner
+ * reorganises its vector by the chunk column indices and encrypts it; the
+ * evaluator multiplies chunk pairs, aggregates rows by rotate-and-add and
+ * masks, and returns one ciphertext per row partition; the key holder
+ * decrypts and undoes the row permutation.
+ *
+ * Scheme: BGV over an RNS basis Q = q_0..q_{L-1} (NTT-friendly primes below
+ * 2^50) with K special primes for hybrid key switching in dnum digits, and
+ * plaintext modulus t (prime, t = 1 mod 2N).  Plaintext slots: row 0 of the
+ * batching encoding (N/2 slots), rotated left by HE-Rot (Section 2.1).
+ *
+ * Conventions common to every call
+ *  - Every function returns HESPMV_OK (0) or an error code below; nothing
+ *    throws across this interface.  hespmv_last_error() gives a message.
+ *  - Ciphertext layout on the device: uint64 words [2][L][N] per ciphertext,
+ *    component-major, limb-major, residues in [0, q_l), NTT domain with index
+ *    i holding the evaluation at psi_l^(2*bitrev(i)+1).  A batch of n
+ *    ciphertexts is n such blocks back to back.
+ *  - "device" pointers are CUDA device addresses on the context's device;
+ *    "host" pointers are ordinary host memory owned by the caller, read or
+ *    written only during the call (or, for *_async, until the stream reaches
+ *    the copy).
+ *  - Device memory the library needs comes from params.alloc/params.free
+ *    when given (the Python binding passes PyTorch's caching allocator),
+ *    else from cudaMalloc/cudaFree.
+ *  - Work is enqueued on the caller's stream (cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Calls without a stream argument
+ *    (keygen, encrypt, decrypt, uploads of keys) synchronise the device
+ *    before returning.
+ */
+#ifndef HESPMV_H
+#define HESPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HESPMV_OK 0
+#define HESPMV_E_INVALID 1     /* bad argument, malformed CSR, wrong sizes   */
+#define HESPMV_E_NOMEM 2       /* an allocation failed                        */
+#define HESPMV_E_CUDA 3        /* a CUDA runtime call or kernel failed        */
+#define HESPMV_E_RANGE 4       /* declared value bounds could reach t/2       */
+#define HESPMV_E_UNSUPPORTED 5 /* parameters outside what the kernels handle  */
+#define HESPMV_E_TIMEOUT 6     /* a bounded device-side wait expired          */
+#define HESPMV_E_REJECTED 7    /* admission control refused a request         */
+
+/* rotation key policy */
+#define HESPMV_ROT_POW2 0  /* keys for 2^i; rotation by k chains its set bits, LSB first */
+#define HESPMV_ROT_EXACT 1 /* one key per requested step                                */
+
+/* which operand hespmv_encrypt encodes */
+#define HESPMV_MATRIX 0
+#define HESPMV_VECTOR 1
+
+/* which key hespmv_key_export copies out */
+#define HESPMV_KEY_SECRET 0 /* s in the NTT domain over the L+K primes: [L+K][N]   */
+#define HESPMV_KEY_PUBLIC 1 /* (pk0, pk1): [2][L][N]                               */
+#define HESPMV_KEY_RELIN 2  /* relinearisation key: [dnum][2][L+K][N]              */
+#define HESPMV_KEY_GALOIS 3 /* Galois key of element g: [dnum][2][L+K][N]          */
+
+typedef void *(*hespmv_alloc_fn)(size_t bytes, void *user);
+typedef void (*hespmv_free_fn)(void *ptr, void *user);
+
+typedef struct hespmv_params {
+    int32_t log2n;      /* ring degree N = 2^log2n, 4 <= log2n <= 15          */
+    int32_t L;          /* ciphertext primes, 1..16                             */
+    int32_t K;          /* special primes, 1..4                                 */
+    int32_t dnum;       /* key-switching digits; alpha = ceil(L/dnum)           */
+    uint64_t t;         /* plaintext modulus: prime, t = 1 mod 2N, t < 2^50     */
+    int32_t prime_bits; /* ciphertext prime size; 0 means 50 (the only size run) */
+    int32_t rot_policy; /* HESPMV_ROT_POW2 or HESPMV_ROT_EXACT                  */
+    int32_t slots;      /* chunk capacity s; 0 means N/2 (row 0 of the slots)   */
+    int32_t device;     /* CUDA device ordinal; -1 = host-only context (format
+                           layer and parameter tables, no device calls)       */
+    hespmv_alloc_fn alloc; /* optional device allocator (NULL: cudaMalloc)     */
+    hespmv_free_fn free;   /* its matching free                                 */
+    void *alloc_user;      /* passed back to alloc/free                         */
+} hespmv_params;
+
+typedef struct hespmv_ctx hespmv_ctx;         /* scheme, tables, keys, workspace */
+typedef struct hespmv_cssc hespmv_cssc;       /* CSSC + partitions + chunk plan */
+typedef struct hespmv_ctbatch hespmv_ctbatch; /* device ciphertexts [n][2][L][N] */
+
+/* Message of the last failing call on this context (never NULL). */
+const char *hespmv_last_error(const hespmv_ctx *ctx);
+
+/* Library version string (never NULL). */
+const char *hespmv_version(void);
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context: chooses the primes (largest q < 2^prime_bits with
+ * q = 1 mod 2N, descending; first L form Q, next K form P), the smallest
+ * primitive 2N-th roots, twiddle and RNS tables, all resident on the device.
+ * The paper fixes one BFV parameter set (Section 5); the parameters here
+ * are the caller's.  *ctx receives a handle released by hespmv_destroy. */
+int hespmv_create(const hespmv_params *p, hespmv_ctx **ctx);
+void hespmv_destroy(hespmv_ctx *ctx);
+
+/* Copy out the moduli (L+K words: Q then P) and roots psi (L+K words); the
+ * plaintext root zeta goes to *zeta.  Any pointer may be NULL. */
+int hespmv_ctx_moduli(const hespmv_ctx *ctx, uint64_t *moduli, uint64_t *psi, uint64_t *zeta);
+
+/* Bytes of device memory the context holds now (tables, keys, workspace,
+ * cached masks). */
+int hespmv_ctx_device_bytes(const hespmv_ctx *ctx, size_t *bytes);
+
+/* -------------------------------------------------------------------- keys */
+
+/* Generate the secret key, public key, relinearisation key and the Galois
+ * keys from `seed` (Section 5: one relinearisation key set plus rotation
+ * keys).  rot_steps lists left-rotation amounts (NULL/0 with POW2: every
+ * power of two below N/2).  Randomness: SplitMix64 streams derived from
+ * seed.  Synchronous. */
+int hespmv_keygen(hespmv_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps);
+
+/* Copy a key to host memory (layouts at HESPMV_KEY_*); n_words must be the
+ * exact size.  galois_elt selects the Galois key (ignored otherwise). */
+int hespmv_key_export(hespmv_ctx *ctx, int32_t which, uint32_t galois_elt, uint64_t *host_out,
+                      size_t n_words);
+
+/* ------------------------------------------------------- format (client A) */
+
+/* Build the CSSC form of a CSR matrix (Algorithm 5: rows by descending
+ * non-zero count, stable; left alignment; column-major VA/CI; CP of length
+ * Lmax+1), partition it into blocks of at most s rows (Section 4.7) and cut
+ * each block into chunks (Algorithm 2, padded-area capacity h*c <= s).
+ * rowptr[rows+1], colidx[nnz] strictly ascending within each row, values
+ * vals[nnz] (integers; fixed-point values are quantised by the caller).
+ * max_abs_x > 0 declares |x_j| <= max_abs_x; if any row could then reach
+ * t/2 the call fails with HESPMV_E_RANGE.  max_abs_x <= 0 skips the check.
+ * Host only (no device work).  Release with hespmv_cssc_free. */
+int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
+                       const int64_t *rowptr, const int32_t *colidx, const int64_t *vals,
+                       int64_t max_abs_x, hespmv_cssc **out);
+void hespmv_cssc_free(hespmv_cssc *m);
+
+/* Counts: partitions, chunks (= ciphertexts per operand), rotations that
+ * Algorithm 4 performs (HE-Rot calls), elementary key switches they take
+ * under the context's policy, rows, cols, nnz. Any pointer may be NULL. */
+int hespmv_cssc_info(const hespmv_cssc *m, int32_t *n_parts, int32_t *n_chunks, int64_t *n_rot,
+                     int64_t *n_keyswitch, int32_t *rows, int32_t *cols, int64_t *nnz);
+
+/* Per chunk: rows h (rList), columns c (cList), partition index.  Arrays of
+ * n_chunks entries; any may be NULL. */
+int hespmv_cssc_chunks(const hespmv_cssc *m, int32_t *h, int32_t *c, int32_t *part);
+
+/* The chunk column indices Client A sends to Client B (Algorithm 1): chunk
+ * k's h*c slot indices, concatenated in chunk order; -1 marks padding.
+ * *ci points into the handle (valid until hespmv_cssc_free). */
+int hespmv_cssc_colindex(const hespmv_cssc *m, const int32_t **ci, size_t *len);
+
+/* The CSSC arrays of partition `part` (Algorithm 5): pointers into the
+ * handle.  VA/CI have nnz_part entries, CP has Lmax+1, RM has the
+ * partition's rows (local row indices). */
+int hespmv_cssc_arrays(const hespmv_cssc *m, int32_t part, const int64_t **va, const int32_t **ci,
+                       size_t *nnz_part, const int64_t **cp, size_t *cp_len, const int32_t **rm,
+                       size_t *rm_len, int32_t *row0);
+
+/* Distinct left-rotation amounts Algorithm 4 needs for this matrix
+ * (ascending).  Writes at most cap entries; *n receives the total. */
+int hespmv_cssc_rotation_steps(const hespmv_cssc *m, int32_t *steps, size_t cap, size_t *n);
+
+/* --------------------------------------------------------- ciphertext batch */
+
+int hespmv_ctbatch_create(hespmv_ctx *ctx, size_t n_ct, hespmv_ctbatch **out);
+void hespmv_ctbatch_free(hespmv_ctbatch *b);
+/* Device address and count of a batch. */
+int hespmv_ctbatch_data(const hespmv_ctbatch *b, uint64_t **dev, size_t *n_ct);
+/* Host <-> device copies of n_ct whole ciphertexts, on `stream`. */
+int hespmv_ctbatch_upload(hespmv_ctbatch *b, const uint64_t *host, size_t n_ct, void *stream);
+int hespmv_ctbatch_download(const hespmv_ctbatch *b, uint64_t *host, size_t n_ct, void *stream);
+
+/* Encode and encrypt one operand (Algorithm 1, Client A / Client B).
+ * which = HESPMV_MATRIX: the chunk values; HESPMV_VECTOR: x (cols entries)
+ * reorganised by the chunk column indices (Algorithm 3).  Ciphertext k uses
+ * encryption randomness stream k of `seed`.  *out gets n_chunks
+ * ciphertexts.  Synchronous. */
+int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
+                   uint64_t seed, hespmv_ctbatch **out);
+
+/* ------------------------------------------------------------ evaluation */
+
+/* The cloud lines of Algorithm 1 with Aggregation (Algorithm 4): for every
+ * chunk k, HE-Mult(A_k, X_k) with relinearisation; per chunk the totalSum
+ * rotate-and-add over its c column blocks of stride h; then per partition
+ * res = sum_k intraRes_k * mask_{h_k}.  A and X hold n_chunks ciphertexts.
+ * If *y is NULL a batch of n_parts ciphertexts is created; otherwise *y
+ * must hold n_parts ciphertexts and is overwritten.  Enqueued on stream. */
+int hespmv_spmv(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                const hespmv_ctbatch *X, hespmv_ctbatch **y, void *stream);
+
+/* hespmv_spmv from host buffers: copies A_host and X_host (n_chunks
+ * ciphertexts each) to the device, evaluates, copies the n_parts result
+ * ciphertexts to y_host, and synchronises `stream`. */
+int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_host,
+                     const uint64_t *X_host, uint64_t *y_host, void *stream);
+
+/* Many independent SpMVs in one batched evaluation (same context and keys):
+ * every stage runs once over the chunks of all n instances.  y[i] as in
+ * hespmv_spmv. */
+int hespmv_spmv_batched(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
+                        const hespmv_ctbatch *const *A, const hespmv_ctbatch *const *X,
+                        hespmv_ctbatch **y, void *stream);
+
+/* ---------------------------------------------------------- key holder */
+
+/* Decrypt the n_parts result ciphertexts and undo the row permutation
+ * (Algorithm 1, last lines): out_rows[rows] receives the centred values.
+ * Synchronous. */
+int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
+                   int64_t *out_rows);
+
+/* Decrypt ciphertext `index` of a batch to its N slot values in [0, t):
+ * row 0 slots 0..N/2-1 then row 1. Synchronous. */
+int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
+                         uint64_t *slots_out);
+
+/* -------------------------------------------------- HE primitives (device) */
+/* All pointers below are device addresses of n whole ciphertexts (or
+ * polynomials where stated); in-place use (out == in) is allowed except
+ * where noted.  Enqueued on stream. */
+
+/* Forward / inverse negacyclic NTT of n_items x n_limbs polynomials stored
+ * back to back; limb k of each item uses modulus index prime0 + k (0..L-1 =
+ * Q, L..L+K-1 = P, L+K = t). */
+int hespmv_ntt_forward(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,
+                       int32_t n_items, void *stream);
+int hespmv_ntt_inverse(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,
+                       int32_t n_items, void *stream);
+
+/* HE-Add (Section 2.1). */
+int hespmv_he_add(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n,
+                  void *stream);
+/* Tensor product: d = (a0 b0, a0 b1 + a1 b0, a1 b1), out [n][3][L][N]. */
+int hespmv_he_tensor(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
+                     void *stream);
+/* Relinearise d [n][3][L][N] -> out [n][2][L][N] (out must not alias d). */
+int hespmv_he_relin(hespmv_ctx *ctx, const uint64_t *d, uint64_t *out, size_t n, void *stream);
+/* HE-Mult (Section 2.1): tensor + relinearisation. */
+int hespmv_he_mult(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n,
+                   void *stream);
+/* HE-Rot (Section 2.1): slot j of the result holds slot j+k (each row);
+ * under POW2 a chain of key switches. out must not alias ct. */
+int hespmv_he_rotate(hespmv_ctx *ctx, const uint64_t *ct, int32_t k, uint64_t *out, size_t n,
+                     void *stream);
+/* HE-CMult by the mask [1]^r [0]^(N/2-r) of Algorithm 4. */
+int hespmv_he_cmult_mask(hespmv_ctx *ctx, const uint64_t *ct, int32_t r, uint64_t *out, size_t n,
+                         void *stream);
+/* Hybrid key switch of polynomials d [n][L][N] with the relinearisation key
+ * (galois_elt = 0) or the Galois key of galois_elt: out [n][2][L][N]. */
+int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, uint64_t *out,
+                     size_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HESPMV_H */

@@ -1,0 +1,315 @@
+"""Python front end of the hespmv C ABI.
+
+Thin wrappers that marshal arguments to the entry points of the same names
+(``hespmv_create``, ``hespmv_keygen``, ``hespmv_encode_cssc``,
+``hespmv_encrypt``, ``hespmv_spmv``, ``hespmv_decrypt`` ...).  PyTorch is
+used only as the device allocator (the caching allocator backs every device
+buffer the library asks for) and as the source of CUDA streams.
+"""
+import ctypes
+from ctypes import byref, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+from . import binding as B
+
+
+def _u64p(a):
+    return a.ctypes.data_as(B.u64p)
+
+
+def _i64p(a):
+    return a.ctypes.data_as(B.i64p)
+
+
+def _i32p(a):
+    return a.ctypes.data_as(B.i32p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(stream.cuda_stream)
+
+
+class TorchAllocator:
+    """Device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_fn = B.ALLOC_FN(self._alloc)
+        self.free_fn = B.FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device="cuda:%d" % self.device)
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, user):
+        self.live.pop(ptr, None)
+
+
+class Context:
+    """Scheme parameters, tables and keys on one GPU (hespmv_create)."""
+
+    def __init__(self, log2n, L, K, dnum, t, rot_policy="pow2", slots=0, device=0,
+                 torch_alloc=True, prime_bits=0):
+        self.lib = B.load()
+        self.allocator = TorchAllocator(device) if torch_alloc else None
+        p = B.hespmv_params()
+        p.log2n, p.L, p.K, p.dnum, p.t = log2n, L, K, dnum, t
+        p.prime_bits = prime_bits
+        p.rot_policy = B.HESPMV_ROT_EXACT if rot_policy == "exact" else B.HESPMV_ROT_POW2
+        p.slots = slots
+        p.device = device
+        if self.allocator is not None:
+            p.alloc = self.allocator.alloc_fn
+            p.free = self.allocator.free_fn
+        self._params = p
+        h = c_void_p()
+        rc = self.lib.hespmv_create(byref(p), byref(h))
+        self.h = h
+        if rc != B.HESPMV_OK:
+            msg = self.lib.hespmv_last_error(h).decode() if h else ""
+            if h:
+                self.lib.hespmv_destroy(h)
+                self.h = None
+            raise B.HespmvError(rc, msg)
+        self.N = 1 << log2n
+        self.L, self.K, self.dnum, self.t = L, K, dnum, t
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hespmv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        B.check(rc, self.h)
+
+    def moduli(self):
+        n = self.L + self.K
+        q = np.zeros(n, dtype=np.uint64)
+        psi = np.zeros(n, dtype=np.uint64)
+        z = np.zeros(1, dtype=np.uint64)
+        self.check(self.lib.hespmv_ctx_moduli(self.h, _u64p(q), _u64p(psi), _u64p(z)))
+        return [int(v) for v in q], [int(v) for v in psi], int(z[0])
+
+    def device_bytes(self):
+        n = c_size_t()
+        self.check(self.lib.hespmv_ctx_device_bytes(self.h, byref(n)))
+        return n.value
+
+    def keygen(self, seed, rot_steps=None):
+        if rot_steps is None:
+            self.check(self.lib.hespmv_keygen(self.h, c_uint64(seed), None, 0))
+        else:
+            a = np.ascontiguousarray(rot_steps, dtype=np.int32)
+            self.check(self.lib.hespmv_keygen(self.h, c_uint64(seed), _i32p(a), len(a)))
+
+    def key_export(self, which, galois=0):
+        N, L, LK = self.N, self.L, self.L + self.K
+        size = {B.HESPMV_KEY_SECRET: LK * N, B.HESPMV_KEY_PUBLIC: 2 * L * N,
+                B.HESPMV_KEY_RELIN: self.dnum * 2 * LK * N,
+                B.HESPMV_KEY_GALOIS: self.dnum * 2 * LK * N}[which]
+        out = np.zeros(size, dtype=np.uint64)
+        self.check(self.lib.hespmv_key_export(self.h, which, galois, _u64p(out), size))
+        return out
+
+    def encode_cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x=0):
+        return Cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x)
+
+    def encrypt(self, m, which, x=None, seed=0):
+        out = c_void_p()
+        xp = None
+        if x is not None:
+            xa = np.ascontiguousarray(x, dtype=np.int64)
+            xp = _i64p(xa)
+        self.check(self.lib.hespmv_encrypt(self.h, m.h, which, xp, c_uint64(seed), byref(out)))
+        return CtBatch(self, out)
+
+    def spmv(self, m, A, X, y=None, stream=None):
+        yh = c_void_p(y.h.value if y is not None else None)
+        self.check(self.lib.hespmv_spmv(self.h, m.h, A.h, X.h, byref(yh), _stream_handle(stream)))
+        return y if y is not None else CtBatch(self, yh)
+
+    def spmv_batched(self, ms, As, Xs, ys=None, stream=None):
+        n = len(ms)
+        arr = c_void_p * n
+        mh = arr(*[m.h for m in ms])
+        ah = arr(*[a.h for a in As])
+        xh = arr(*[x.h for x in Xs])
+        yh = arr(*[(y.h if y is not None else None) for y in (ys or [None] * n)])
+        self.check(self.lib.hespmv_spmv_batched(self.h, n, mh, ah, xh, yh, _stream_handle(stream)))
+        if ys is not None and all(y is not None for y in ys):
+            return ys
+        return [CtBatch(self, c_void_p(yh[i])) for i in range(n)]
+
+    def spmv_host(self, m, A_host, X_host, y_host, stream=None):
+        self.check(self.lib.hespmv_spmv_host(self.h, m.h, _u64p(A_host), _u64p(X_host),
+                                             _u64p(y_host), _stream_handle(stream)))
+
+    def decrypt(self, m, y):
+        out = np.zeros(m.rows, dtype=np.int64)
+        self.check(self.lib.hespmv_decrypt(self.h, m.h, y.h, _i64p(out)))
+        return out
+
+    def decrypt_slots(self, b, index=0):
+        out = np.zeros(self.N, dtype=np.uint64)
+        self.check(self.lib.hespmv_decrypt_slots(self.h, b.h, index, _u64p(out)))
+        return out
+
+    # ---- primitives on device pointers (ints) ----
+    def ntt(self, ptr, prime0, n_limbs, n_items=1, inverse=False, stream=None):
+        fn = self.lib.hespmv_ntt_inverse if inverse else self.lib.hespmv_ntt_forward
+        self.check(fn(self.h, c_void_p(ptr), prime0, n_limbs, n_items, _stream_handle(stream)))
+
+    def he_add(self, a, b, out, n=1, stream=None):
+        self.check(self.lib.hespmv_he_add(self.h, c_void_p(a), c_void_p(b), c_void_p(out), n,
+                                          _stream_handle(stream)))
+
+    def he_tensor(self, a, b, d, n=1, stream=None):
+        self.check(self.lib.hespmv_he_tensor(self.h, c_void_p(a), c_void_p(b), c_void_p(d), n,
+                                             _stream_handle(stream)))
+
+    def he_relin(self, d, out, n=1, stream=None):
+        self.check(self.lib.hespmv_he_relin(self.h, c_void_p(d), c_void_p(out), n,
+                                            _stream_handle(stream)))
+
+    def he_mult(self, a, b, out, n=1, stream=None):
+        self.check(self.lib.hespmv_he_mult(self.h, c_void_p(a), c_void_p(b), c_void_p(out), n,
+                                           _stream_handle(stream)))
+
+    def he_rotate(self, ct, k, out, n=1, stream=None):
+        self.check(self.lib.hespmv_he_rotate(self.h, c_void_p(ct), k, c_void_p(out), n,
+                                             _stream_handle(stream)))
+
+    def he_cmult_mask(self, ct, r, out, n=1, stream=None):
+        self.check(self.lib.hespmv_he_cmult_mask(self.h, c_void_p(ct), r, c_void_p(out), n,
+                                                 _stream_handle(stream)))
+
+    def keyswitch(self, d, galois, out, n=1, stream=None):
+        self.check(self.lib.hespmv_keyswitch(self.h, c_void_p(d), galois, c_void_p(out), n,
+                                             _stream_handle(stream)))
+
+
+class Cssc:
+    """Client-side CSSC form, partitions and chunk plan (hespmv_encode_cssc)."""
+
+    def __init__(self, ctx, rows, cols, rowptr, colidx, vals, max_abs_x=0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        va = np.ascontiguousarray(vals, dtype=np.int64)
+        h = c_void_p()
+        ctx.check(self.lib.hespmv_encode_cssc(ctx.h, rows, cols, int(rp[-1]) if len(rp) else 0,
+                                              _i64p(rp), _i32p(ci), _i64p(va),
+                                              c_int64(max_abs_x), byref(h)))
+        self.h = h
+        info = [c_int32(), c_int32(), c_int64(), c_int64(), c_int32(), c_int32(), c_int64()]
+        ctx.check(self.lib.hespmv_cssc_info(h, *[byref(v) for v in info]))
+        (self.n_parts, self.n_chunks, self.n_rot, self.n_keyswitch, self.rows, self.cols,
+         self.nnz) = [v.value for v in info]
+
+    def chunks(self):
+        n = self.n_chunks
+        h = np.zeros(n, dtype=np.int32)
+        c = np.zeros(n, dtype=np.int32)
+        p = np.zeros(n, dtype=np.int32)
+        self.ctx.check(self.lib.hespmv_cssc_chunks(self.h, _i32p(h), _i32p(c), _i32p(p)))
+        return h, c, p
+
+    def colindex(self):
+        ptr = B.i32p()
+        n = c_size_t()
+        self.ctx.check(self.lib.hespmv_cssc_colindex(self.h, byref(ptr), byref(n)))
+        return np.ctypeslib.as_array(ptr, shape=(n.value,)).copy() if n.value else np.zeros(0, np.int32)
+
+    def arrays(self, part):
+        va, ci, cp, rm = B.i64p(), B.i32p(), B.i64p(), B.i32p()
+        nv, ncp, nrm = c_size_t(), c_size_t(), c_size_t()
+        row0 = c_int32()
+        self.ctx.check(self.lib.hespmv_cssc_arrays(self.h, part, byref(va), byref(ci), byref(nv),
+                                                   byref(cp), byref(ncp), byref(rm), byref(nrm),
+                                                   byref(row0)))
+
+        def arr(p, n, dt):
+            return np.ctypeslib.as_array(p, shape=(n,)).copy() if n else np.zeros(0, dt)
+        return (arr(va, nv.value, np.int64), arr(ci, nv.value, np.int32),
+                arr(cp, ncp.value, np.int64), arr(rm, nrm.value, np.int32), row0.value)
+
+    def rotation_steps(self):
+        n = c_size_t()
+        self.ctx.check(self.lib.hespmv_cssc_rotation_steps(self.h, None, 0, byref(n)))
+        out = np.zeros(max(1, n.value), dtype=np.int32)
+        self.ctx.check(self.lib.hespmv_cssc_rotation_steps(self.h, _i32p(out), n.value, byref(n)))
+        return [int(v) for v in out[:n.value]]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hespmv_cssc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CtBatch:
+    """Device ciphertexts [n][2][L][N] (hespmv_ctbatch)."""
+
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h if isinstance(h, c_void_p) else c_void_p(h)
+        p = B.u64p()
+        n = c_size_t()
+        ctx.check(ctx.lib.hespmv_ctbatch_data(self.h, byref(p), byref(n)))
+        self.ptr = ctypes.cast(p, c_void_p).value
+        self.n = n.value
+
+    @classmethod
+    def create(cls, ctx, n):
+        h = c_void_p()
+        ctx.check(ctx.lib.hespmv_ctbatch_create(ctx.h, n, byref(h)))
+        return cls(ctx, h)
+
+    @property
+    def words_per_ct(self):
+        return 2 * self.ctx.L * self.ctx.N
+
+    def download(self, stream=None):
+        out = np.zeros(self.n * self.words_per_ct, dtype=np.uint64)
+        self.ctx.check(self.ctx.lib.hespmv_ctbatch_download(self.h, _u64p(out), self.n,
+                                                            _stream_handle(stream)))
+        return out.reshape(self.n, 2, self.ctx.L, self.ctx.N)
+
+    def upload(self, host, stream=None):
+        a = np.ascontiguousarray(host, dtype=np.uint64)
+        n = a.size // self.words_per_ct
+        self.ctx.check(self.ctx.lib.hespmv_ctbatch_upload(self.h, _u64p(a), n, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.ctx.lib.hespmv_ctbatch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

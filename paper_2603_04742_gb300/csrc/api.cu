@@ -1,0 +1,960 @@
+// C-ABI entry points of hespmv: context and tables, key generation,
+// client-side format and encryption, the cloud evaluation of Algorithms 1
+// and 4, decryption, and the HE primitives.
+#include <algorithm>
+#include <cstring>
+#include <set>
+
+#include "kernels.h"
+
+using namespace hespmv;
+
+namespace {
+
+const uint64_t kSecretStream = 1, kPkAStream = 2, kPkEStream = 3;
+const uint64_t kEncBase = 1ull << 62;
+uint64_t ksk_a_stream(uint64_t kid, uint64_t j) { return 16 + 2 * (kid * 64 + j); }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define FAIL(code, msg)        \
+    do {                       \
+        ctx->err = (msg);      \
+        return (code);         \
+    } while (0)
+
+#define NEED_DEVICE(ctx)                                                      \
+    do {                                                                      \
+        if ((ctx)->device < 0) FAIL(HESPMV_E_INVALID, "host-only context");  \
+    } while (0)
+
+#define CK(x)                                                                          \
+    do {                                                                               \
+        cudaError_t _e = (x);                                                          \
+        if (_e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+void *dev_alloc(hespmv_ctx *ctx, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    void *p = nullptr;
+    if (ctx->p.alloc) {
+        p = ctx->p.alloc(bytes, ctx->p.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(hespmv_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->p.free)
+        ctx->p.free(p, ctx->p.alloc_user);
+    else
+        cudaFree(p);
+}
+
+// allocation owned by the context until destroy
+template <class T>
+T *owned(hespmv_ctx *ctx, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    void *p = dev_alloc(ctx, bytes);
+    if (p) {
+        ctx->allocs.push_back({p, bytes});
+        ctx->owned_bytes += bytes;
+    }
+    return (T *)p;
+}
+
+template <class T>
+bool upload(hespmv_ctx *ctx, T *&dst, const std::vector<T> &src) {
+    dst = owned<T>(ctx, std::max<size_t>(src.size(), 1));
+    if (!dst) return false;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// workspace of at least `bytes`; reallocation waits for the device first
+uint64_t *workspace(hespmv_ctx *ctx, size_t bytes) {
+    if (ctx->ws_bytes >= bytes) return (uint64_t *)ctx->ws;
+    cudaDeviceSynchronize();
+    dev_free(ctx, ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    size_t want = std::max(bytes, ctx->ws_bytes * 3 / 2);
+    ctx->ws = dev_alloc(ctx, want);
+    if (!ctx->ws) {
+        ctx->ws = dev_alloc(ctx, bytes);
+        want = bytes;
+    }
+    if (!ctx->ws) return nullptr;
+    ctx->ws_bytes = want;
+    return (uint64_t *)ctx->ws;
+}
+
+// words of key-switching scratch for n items
+size_t ks_words(const Ctx &c, size_t n) {
+    const size_t LK = c.L + c.K;
+    return n * (size_t)c.N * (c.L + c.dnum * LK + 2 * LK + 2 * c.L);
+}
+
+// Hybrid key switch of n polynomials d (item stride d_stride words) with `key`;
+// out [n][2][L][N] = ModDown(sum_j ModUp_j(d) * key_j) (+ add per add_mask).
+cudaError_t keyswitch_n(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
+                        uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
+                        int add_mask, size_t n, uint64_t *scratch, cudaStream_t st) {
+    const int64_t N = c.N, L = c.L, LK = c.L + c.K;
+    uint64_t *dcoef = scratch;
+    uint64_t *ext = dcoef + n * L * N;
+    uint64_t *acc = ext + n * c.dnum * LK * N;
+    uint64_t *delta = acc + n * 2 * LK * N;
+    cudaError_t e;
+    if ((e = op_copy_strided(d, d_stride, dcoef, L * N, L * N, n, st))) return e;
+    if ((e = launch_ntt(c, dcoef, 0, (int)L, (int)n, L * N, true, st))) return e;
+    if ((e = op_modup(c, dcoef, ext, n, st))) return e;
+    if ((e = launch_ntt(c, ext, 0, (int)LK, (int)(n * c.dnum), LK * N, false, st))) return e;
+    if ((e = op_inner(c, ext, key, acc, n, st))) return e;
+    if ((e = launch_ntt(c, acc + L * N, (int)L, c.K, (int)(n * 2), LK * N, true, st))) return e;
+    if ((e = op_moddown_delta(c, acc, delta, n, st))) return e;
+    if ((e = launch_ntt(c, delta, 0, (int)L, (int)(n * 2), L * N, false, st))) return e;
+    return op_moddown_final(c, acc, delta, add, add_is, add_cs, add_mask, out, n, st);
+}
+
+uint32_t pow5(uint64_t e, uint64_t twoN) {
+    uint64_t r = 1, b = 5 % twoN;
+    for (; e; e >>= 1) {
+        if (e & 1) r = r * b % twoN;
+        b = b * b % twoN;
+    }
+    return (uint32_t)r;
+}
+
+// Galois elements applied, in order, for a left rotation by k.
+std::vector<uint32_t> rotation_chain(const hespmv_ctx *ctx, int64_t k) {
+    const uint64_t N = ctx->h.N, half = N / 2, twoN = 2 * N;
+    k %= (int64_t)half;
+    if (k < 0) k += half;
+    std::vector<uint32_t> out;
+    if (k == 0) return out;
+    if (ctx->p.rot_policy == HESPMV_ROT_EXACT) {
+        out.push_back(pow5((uint64_t)k, twoN));
+        return out;
+    }
+    for (int b = 0; (k >> b) != 0; ++b)
+        if ((k >> b) & 1) out.push_back(pow5(1ull << b, twoN));
+    return out;
+}
+
+const int32_t *galois_perm(hespmv_ctx *ctx, uint32_t g) {
+    auto it = ctx->perms.find(g);
+    if (it != ctx->perms.end()) return it->second;
+    const int N = ctx->h.N, logn = ctx->h.log2n;
+    const uint64_t twoN = 2 * (uint64_t)N;
+    std::vector<int32_t> perm(N);
+    for (int i = 0; i < N; ++i) {
+        const uint64_t e = (2 * (uint64_t)host_bitrev((uint32_t)i, logn) + 1) * g % twoN;
+        perm[i] = (int32_t)ntt_index_of_exponent(e, logn);
+    }
+    int32_t *d = nullptr;
+    if (!upload(ctx, d, perm)) return nullptr;
+    ctx->perms[g] = d;
+    return d;
+}
+
+int make_ksk(hespmv_ctx *ctx, uint64_t seed, uint64_t kid, const uint64_t *sp, uint64_t *out,
+             uint64_t *tmp_e, int64_t *coef) {
+    const Ctx c = view(ctx);
+    const int64_t LK = c.L + c.K, N = c.N, LKN = LK * N;
+    for (int j = 0; j < c.dnum; ++j) {
+        uint64_t *b = out + (2 * j) * LKN, *a = out + (2 * j + 1) * LKN;
+        CK(op_sample_uniform(c, seed, ksk_a_stream(kid, j), a, 0, (int)LK, 0));
+        CK(op_sample_signed(c, seed, ksk_a_stream(kid, j) + 1, 0, kCbd21, coef, 1, 0));
+        CK(op_signed_to_limbs(c, coef, tmp_e, 0, (int)LK, 1, 0));
+        CK(launch_ntt(c, tmp_e, 0, (int)LK, 1, LKN, false, 0));
+        CK(op_ksk_combine(c, a, tmp_e, ctx->sk, sp, j, b, 0));
+    }
+    return HESPMV_OK;
+}
+
+int check_ctx(hespmv_ctx *ctx) { return ctx ? HESPMV_OK : HESPMV_E_INVALID; }
+
+const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
+    auto it = ctx->masks.find(r);
+    if (it != ctx->masks.end()) return it->second;
+    const Ctx c = view(ctx);
+    const int N = c.N;
+    uint64_t *m = owned<uint64_t>(ctx, (size_t)c.L * N);
+    void *tmp = dev_alloc(ctx, (size_t)N * 8 * 2);
+    if (!m || !tmp) {
+        dev_free(ctx, tmp);
+        return nullptr;
+    }
+    std::vector<int64_t> ones(N / 2, 0);
+    for (int j = 0; j < r && j < N / 2; ++j) ones[j] = 1;
+    int64_t *dvals = (int64_t *)tmp;
+    uint64_t *E = (uint64_t *)tmp + N;  // words [N, 2N) of tmp
+    bool ok = cudaMemcpyAsync(dvals, ones.data(), (N / 2) * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && op_scatter_slots(c, dvals, N / 2, E, 1, st) == cudaSuccess;
+    ok = ok && launch_ntt(c, E, c.L + c.K, 1, 1, N, true, st) == cudaSuccess;
+    ok = ok && op_lift(c, E, m, 1, st) == cudaSuccess;
+    ok = ok && launch_ntt(c, m, 0, c.L, 1, (int64_t)c.L * N, false, st) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    dev_free(ctx, tmp);
+    if (!ok) return nullptr;
+    ctx->masks[r] = m;
+    return m;
+}
+
+int batch_new(hespmv_ctx *ctx, size_t n, hespmv_ctbatch **out) {
+    const size_t words = n * 2 * (size_t)ctx->h.L * ctx->h.N;
+    hespmv_ctbatch *b = new hespmv_ctbatch();
+    b->ctx = ctx;
+    b->n = n;
+    b->bytes = words * 8;
+    b->data = (uint64_t *)dev_alloc(ctx, b->bytes);
+    if (!b->data) {
+        delete b;
+        FAIL(HESPMV_E_NOMEM, "ciphertext batch allocation failed");
+    }
+    *out = b;
+    return HESPMV_OK;
+}
+
+// Rotate n ciphertexts by k (chain of Galois elements); out must not alias src.
+// scratch: 3 ciphertext batches of n + ks_words(n).
+int rotate_n(hespmv_ctx *ctx, const uint64_t *src, int32_t k, uint64_t *out, size_t n,
+             uint64_t *scratch, cudaStream_t st) {
+    const Ctx c = view(ctx);
+    const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
+    std::vector<uint32_t> chain = rotation_chain(ctx, k);
+    if (chain.empty()) {
+        CK(cudaMemcpyAsync(out, src, n * CT * 8, cudaMemcpyDeviceToDevice, st));
+        return HESPMV_OK;
+    }
+    uint64_t *perm_buf = scratch;
+    uint64_t *bufs[2] = {perm_buf + n * CT, perm_buf + 2 * n * CT};
+    uint64_t *ks = perm_buf + 3 * n * CT;
+    const uint64_t *cur = src;
+    for (size_t s = 0; s < chain.size(); ++s) {
+        const uint32_t g = chain[s];
+        auto it = ctx->gk.find(g);
+        if (it == ctx->gk.end()) FAIL(HESPMV_E_INVALID, "missing Galois key for element " + std::to_string(g));
+        const int32_t *perm = galois_perm(ctx, g);
+        if (!perm) FAIL(HESPMV_E_NOMEM, "permutation upload failed");
+        // the last step writes `out`; earlier ones alternate between two buffers
+        uint64_t *dst = (s + 1 == chain.size()) ? out : bufs[s & 1];
+        CK(op_permute(c, cur, perm_buf, perm, n * 2 * c.L, st));
+        CK(keyswitch_n(c, perm_buf + LN, CT, it->second, dst, perm_buf, CT, LN, 1, n, ks, st));
+        cur = dst;
+    }
+    if (cur != out) CK(cudaMemcpyAsync(out, cur, n * CT * 8, cudaMemcpyDeviceToDevice, st));
+    return HESPMV_OK;
+}
+
+// Cloud evaluation of one or more SpMVs (Algorithm 1 cloud lines + Algorithm 4).
+int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
+              const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
+              cudaStream_t st) {
+    const Ctx c = view(ctx);
+    const int64_t N = c.N, LN = (int64_t)c.L * N, CT = 2 * LN;
+    size_t total_chunks = 0;
+    for (size_t i = 0; i < n_inst; ++i) total_chunks += ms[i]->plan.chunks.size();
+    // masks first (synchronous, cached)
+    for (size_t i = 0; i < n_inst; ++i)
+        for (const Chunk &ch : ms[i]->plan.chunks)
+            if (!mask_plaintext(ctx, ch.h, st)) FAIL(HESPMV_E_NOMEM, "mask plaintext creation failed");
+    // group size of the batched HE-Mult
+    const size_t G = std::max<size_t>(1, std::min<size_t>(total_chunks, 32));
+    const size_t prod_w = total_chunks * CT;
+    const size_t d_w = G * 3 * LN;
+    const size_t ks_w = ks_words(c, G);
+    const size_t rot_w = 2 * CT + 3 * CT + ks_words(c, 1);  // V copy, tmp, rotation scratch
+    const size_t need = (prod_w + d_w + std::max(ks_w, rot_w)) * 8;
+    uint64_t *ws = workspace(ctx, need);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + d_w;
+    // 1) HE-Mult of every chunk pair, G at a time
+    std::vector<std::pair<const uint64_t *, const uint64_t *>> pairs;
+    pairs.reserve(total_chunks);
+    for (size_t i = 0; i < n_inst; ++i)
+        for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k)
+            pairs.push_back({A[i] + k * CT, X[i] + k * CT});
+    size_t k0 = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        const size_t nk = ms[i]->plan.chunks.size();
+        // contiguous runs within one instance are batched together
+        for (size_t k = 0; k < nk; k += G) {
+            const size_t g = std::min(G, nk - k);
+            CK(op_tensor(c, A[i] + k * CT, X[i] + k * CT, dbuf, g, st));
+            CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + (k0 + k) * CT, dbuf, 3 * LN,
+                           LN, 3, g, scr, st));
+        }
+        k0 += nk;
+    }
+    // 2) totalSum per chunk
+    uint64_t *Vc = scr, *tmp = Vc + CT, *rs = tmp + CT;
+    std::vector<int32_t> steps;
+    std::vector<uint8_t> orig;
+    k0 = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        for (const Chunk &ch : ms[i]->plan.chunks) {
+            uint64_t *w = prod + k0 * CT;
+            total_sum_steps(ch.h, ch.c, steps, orig);
+            if (!steps.empty()) {
+                CK(cudaMemcpyAsync(Vc, w, CT * 8, cudaMemcpyDeviceToDevice, st));
+                for (size_t s = 0; s < steps.size(); ++s) {
+                    int rc = rotate_n(ctx, orig[s] ? Vc : w, steps[s], tmp, 1, rs, st);
+                    if (rc) return rc;
+                    CK(op_add(c, w, tmp, w, 2, st));
+                }
+            }
+            ++k0;
+        }
+    }
+    // 3) masked accumulation per partition
+    k0 = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        const Plan &pl = ms[i]->plan;
+        for (size_t p = 0; p < pl.parts.size(); ++p) {
+            uint64_t *res = Y[i] + p * CT;
+            const Partition &P = pl.parts[p];
+            if (P.n_chunks == 0) {
+                CK(cudaMemsetAsync(res, 0, CT * 8, st));
+                continue;
+            }
+            for (int k = 0; k < P.n_chunks; ++k) {
+                const Chunk &ch = pl.chunks[P.chunk0 + k];
+                CK(op_cmult_acc(c, res, prod + (k0 + P.chunk0 + k) * CT, ctx->masks[ch.h], k == 0, st));
+            }
+        }
+        k0 += pl.chunks.size();
+    }
+    return HESPMV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hespmv_version(void) { return "hespmv 0.1 (sm_103a)"; }
+
+const char *hespmv_last_error(const hespmv_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
+    if (!p || !out) return HESPMV_E_INVALID;
+    *out = nullptr;
+    if ((p->alloc == nullptr) != (p->free == nullptr)) return HESPMV_E_INVALID;
+    if (p->rot_policy != HESPMV_ROT_POW2 && p->rot_policy != HESPMV_ROT_EXACT) return HESPMV_E_INVALID;
+    hespmv_ctx *ctx = new hespmv_ctx();
+    ctx->p = *p;
+    ctx->device = p->device;
+    if (!build_tables(*p, ctx->h, ctx->err)) {
+        const int code = HESPMV_E_UNSUPPORTED;
+        *out = ctx;  // keep the message readable
+        return code;
+    }
+    if (p->device == -1) {  // host-only: format layer and parameter tables
+        *out = ctx;
+        return HESPMV_OK;
+    }
+    DeviceGuard g(ctx->device);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
+        cudaGetLastError();
+        ctx->err = "no CUDA device " + std::to_string(p->device);
+        *out = ctx;
+        return HESPMV_E_CUDA;
+    }
+    HostTables &h = ctx->h;
+    DevTables &d = ctx->d;
+    bool ok = upload(ctx, d.mc, h.mc) && upload(ctx, d.tw, h.tw) && upload(ctx, d.modup_inv, h.modup_inv) &&
+              upload(ctx, d.modup_mod, h.modup_mod) && upload(ctx, d.md_pk, h.md_pk) &&
+              upload(ctx, d.md_phat, h.md_phat) && upload(ctx, d.md_t, h.md_t) &&
+              upload(ctx, d.md_pinv, h.md_pinv) && upload(ctx, d.p_mod_q, h.p_mod_q) &&
+              upload(ctx, d.slot_idx, h.slot_idx) && upload(ctx, d.dec, h.dec) &&
+              upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod);
+    if (!ok) {
+        ctx->err = "table upload failed";
+        *out = ctx;
+        return HESPMV_E_NOMEM;
+    }
+    *out = ctx;
+    return HESPMV_OK;
+}
+
+void hespmv_destroy(hespmv_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->device < 0) {
+        delete ctx;
+        return;
+    }
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &a : ctx->allocs) dev_free(ctx, a.first);
+    dev_free(ctx, ctx->ws);
+    dev_free(ctx, ctx->io);
+    delete ctx;
+}
+
+int hespmv_ctx_moduli(const hespmv_ctx *ctx, uint64_t *moduli, uint64_t *psi, uint64_t *zeta) {
+    if (!ctx || ctx->h.q.empty()) return HESPMV_E_INVALID;
+    const int LK = ctx->h.L + ctx->h.K;
+    if (moduli) memcpy(moduli, ctx->h.q.data(), LK * 8);
+    if (psi) memcpy(psi, ctx->h.psi.data(), LK * 8);
+    if (zeta) *zeta = ctx->h.psi[LK];
+    return HESPMV_OK;
+}
+
+int hespmv_ctx_device_bytes(const hespmv_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return HESPMV_E_INVALID;
+    *bytes = ctx->owned_bytes + ctx->ws_bytes;
+    return HESPMV_OK;
+}
+
+int hespmv_keygen(hespmv_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps) {
+    if (!ctx || ctx->h.q.empty()) return HESPMV_E_INVALID;
+    if (n_steps && !rot_steps) FAIL(HESPMV_E_INVALID, "rot_steps is NULL");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t N = c.N, L = c.L, LK = c.L + c.K, LKN = LK * N;
+    if (!ctx->sk) {
+        ctx->sk = owned<uint64_t>(ctx, LKN);
+        ctx->pk = owned<uint64_t>(ctx, 2 * L * N);
+        ctx->rlk = owned<uint64_t>(ctx, (size_t)c.dnum * 2 * LKN);
+        if (!ctx->sk || !ctx->pk || !ctx->rlk) FAIL(HESPMV_E_NOMEM, "key allocation failed");
+    }
+    void *tmp = dev_alloc(ctx, (size_t)(2 * LKN + N) * 8);
+    if (!tmp) FAIL(HESPMV_E_NOMEM, "keygen scratch allocation failed");
+    uint64_t *tmp_e = (uint64_t *)tmp, *sp = tmp_e + LKN;
+    int64_t *coef = (int64_t *)(sp + LKN);
+    int rc = HESPMV_OK;
+    do {
+        // secret key s: ternary, NTT over Q u P
+        if (op_sample_signed(c, seed, kSecretStream, 0, kTernary, coef, 1, 0) ||
+            op_signed_to_limbs(c, coef, ctx->sk, 0, (int)LK, 1, 0) ||
+            launch_ntt(c, ctx->sk, 0, (int)LK, 1, LKN, false, 0)) {
+            rc = HESPMV_E_CUDA;
+            break;
+        }
+        // public key (-a s + t e, a)
+        uint64_t *pk1 = ctx->pk + L * N;
+        if (op_sample_uniform(c, seed, kPkAStream, pk1, 0, (int)L, 0) ||
+            op_sample_signed(c, seed, kPkEStream, 0, kCbd21, coef, 1, 0) ||
+            op_signed_to_limbs(c, coef, tmp_e, 0, (int)L, 1, 0) ||
+            launch_ntt(c, tmp_e, 0, (int)L, 1, L * N, false, 0) ||
+            op_pk_combine(c, pk1, tmp_e, ctx->sk, ctx->pk, 0)) {
+            rc = HESPMV_E_CUDA;
+            break;
+        }
+        // relinearisation key: s' = s^2
+        if (op_mul_limbs(c, ctx->sk, ctx->sk, sp, 0, (int)LK, 1, 0)) {
+            rc = HESPMV_E_CUDA;
+            break;
+        }
+        if ((rc = make_ksk(ctx, seed, 0, sp, ctx->rlk, tmp_e, coef))) break;
+        // Galois keys
+        std::set<uint32_t> elts;
+        const int64_t half = N / 2;
+        if (rot_steps == nullptr || n_steps == 0) {
+            if (ctx->p.rot_policy == HESPMV_ROT_POW2)
+                for (int64_t b = 1; b < half; b <<= 1) elts.insert(pow5((uint64_t)b, 2 * N));
+        } else {
+            for (size_t i = 0; i < n_steps; ++i)
+                for (uint32_t e : rotation_chain(ctx, rot_steps[i])) elts.insert(e);
+        }
+        for (uint32_t e : elts) {
+            uint64_t *key = ctx->gk.count(e) ? ctx->gk[e] : owned<uint64_t>(ctx, (size_t)c.dnum * 2 * LKN);
+            const int32_t *perm = galois_perm(ctx, e);
+            if (!key || !perm) {
+                rc = HESPMV_E_NOMEM;
+                ctx->err = "Galois key allocation failed";
+                break;
+            }
+            ctx->gk[e] = key;
+            if (op_permute(c, ctx->sk, sp, perm, LK, 0)) {
+                rc = HESPMV_E_CUDA;
+                break;
+            }
+            if ((rc = make_ksk(ctx, seed, e, sp, key, tmp_e, coef))) break;
+        }
+    } while (0);
+    cudaError_t e = cudaDeviceSynchronize();
+    dev_free(ctx, tmp);
+    if (rc == HESPMV_E_CUDA && ctx->err.empty()) ctx->err = "keygen kernel launch failed";
+    if (rc) return rc;
+    if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("keygen: ") + cudaGetErrorString(e));
+    ctx->have_keys = true;
+    return HESPMV_OK;
+}
+
+int hespmv_key_export(hespmv_ctx *ctx, int32_t which, uint32_t galois_elt, uint64_t *host_out,
+                      size_t n_words) {
+    if (!ctx || !host_out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "no keys");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const size_t N = ctx->h.N, L = ctx->h.L, LK = L + ctx->h.K;
+    const uint64_t *src = nullptr;
+    size_t words = 0;
+    switch (which) {
+        case HESPMV_KEY_SECRET: src = ctx->sk; words = LK * N; break;
+        case HESPMV_KEY_PUBLIC: src = ctx->pk; words = 2 * L * N; break;
+        case HESPMV_KEY_RELIN: src = ctx->rlk; words = ctx->h.dnum * 2 * LK * N; break;
+        case HESPMV_KEY_GALOIS: {
+            auto it = ctx->gk.find(galois_elt);
+            if (it == ctx->gk.end()) FAIL(HESPMV_E_INVALID, "no Galois key for that element");
+            src = it->second;
+            words = ctx->h.dnum * 2 * LK * N;
+            break;
+        }
+        default: FAIL(HESPMV_E_INVALID, "unknown key kind");
+    }
+    if (n_words != words) FAIL(HESPMV_E_INVALID, "n_words does not match the key size");
+    CK(cudaMemcpy(host_out, src, words * 8, cudaMemcpyDeviceToHost));
+    return HESPMV_OK;
+}
+
+int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
+                       const int64_t *rowptr, const int32_t *colidx, const int64_t *vals,
+                       int64_t max_abs_x, hespmv_cssc **out) {
+    if (!ctx || !out || ctx->h.q.empty()) return HESPMV_E_INVALID;
+    *out = nullptr;
+    hespmv_cssc *m = new hespmv_cssc();
+    m->ctx = ctx;
+    std::string err = build_plan(rows, cols, nnz, rowptr, colidx, vals, ctx->h.slots, m->plan);
+    if (!err.empty()) {
+        delete m;
+        FAIL(HESPMV_E_INVALID, "malformed CSR: " + err);
+    }
+    if (max_abs_x > 0) {
+        typedef unsigned __int128 u128;
+        const u128 half_t = (u128)ctx->h.t;
+        for (int32_t i = 0; i < rows; ++i) {
+            u128 s = 0;
+            bool big = false;
+            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                const int64_t v = vals[k];
+                s += (u128)(v < 0 ? -(u128)v : (u128)v);
+                if (s > ((u128)1 << 64)) big = true;
+            }
+            if (big || 2 * s * (u128)max_abs_x >= half_t) {
+                delete m;
+                FAIL(HESPMV_E_RANGE, "row " + std::to_string(i) +
+                                         ": sum |a_ij| * max|x| could reach t/2");
+            }
+        }
+    }
+    std::set<int32_t> st;
+    std::vector<int32_t> steps;
+    std::vector<uint8_t> orig;
+    for (const Chunk &ch : m->plan.chunks) {
+        total_sum_steps(ch.h, ch.c, steps, orig);
+        m->n_rot += (int64_t)steps.size();
+        for (int32_t k : steps) {
+            st.insert(k);
+            m->n_ks += (int64_t)rotation_chain(ctx, k).size();
+        }
+    }
+    m->steps.assign(st.begin(), st.end());
+    *out = m;
+    return HESPMV_OK;
+}
+
+void hespmv_cssc_free(hespmv_cssc *m) { delete m; }
+
+int hespmv_cssc_info(const hespmv_cssc *m, int32_t *n_parts, int32_t *n_chunks, int64_t *n_rot,
+                     int64_t *n_keyswitch, int32_t *rows, int32_t *cols, int64_t *nnz) {
+    if (!m) return HESPMV_E_INVALID;
+    if (n_parts) *n_parts = (int32_t)m->plan.parts.size();
+    if (n_chunks) *n_chunks = (int32_t)m->plan.chunks.size();
+    if (n_rot) *n_rot = m->n_rot;
+    if (n_keyswitch) *n_keyswitch = m->n_ks;
+    if (rows) *rows = m->plan.rows;
+    if (cols) *cols = m->plan.cols;
+    if (nnz) *nnz = m->plan.nnz;
+    return HESPMV_OK;
+}
+
+int hespmv_cssc_chunks(const hespmv_cssc *m, int32_t *h, int32_t *c, int32_t *part) {
+    if (!m) return HESPMV_E_INVALID;
+    for (size_t k = 0; k < m->plan.chunks.size(); ++k) {
+        if (h) h[k] = m->plan.chunks[k].h;
+        if (c) c[k] = m->plan.chunks[k].c;
+        if (part) part[k] = m->plan.chunks[k].part;
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_cssc_colindex(const hespmv_cssc *m, const int32_t **ci, size_t *len) {
+    if (!m || !ci || !len) return HESPMV_E_INVALID;
+    *ci = m->plan.slot_ci.data();
+    *len = m->plan.slot_ci.size();
+    return HESPMV_OK;
+}
+
+int hespmv_cssc_arrays(const hespmv_cssc *m, int32_t part, const int64_t **va, const int32_t **ci,
+                       size_t *nnz_part, const int64_t **cp, size_t *cp_len, const int32_t **rm,
+                       size_t *rm_len, int32_t *row0) {
+    if (!m || part < 0 || part >= (int32_t)m->plan.parts.size()) return HESPMV_E_INVALID;
+    const Partition &P = m->plan.parts[part];
+    if (va) *va = P.va.data();
+    if (ci) *ci = P.ci.data();
+    if (nnz_part) *nnz_part = P.va.size();
+    if (cp) *cp = P.cp.data();
+    if (cp_len) *cp_len = P.cp.size();
+    if (rm) *rm = P.rm.data();
+    if (rm_len) *rm_len = P.rm.size();
+    if (row0) *row0 = P.row0;
+    return HESPMV_OK;
+}
+
+int hespmv_cssc_rotation_steps(const hespmv_cssc *m, int32_t *steps, size_t cap, size_t *n) {
+    if (!m || !n) return HESPMV_E_INVALID;
+    *n = m->steps.size();
+    for (size_t i = 0; i < m->steps.size() && i < cap && steps; ++i) steps[i] = m->steps[i];
+    return HESPMV_OK;
+}
+
+int hespmv_ctbatch_create(hespmv_ctx *ctx, size_t n_ct, hespmv_ctbatch **out) {
+    if (!ctx || !out) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    return batch_new(ctx, n_ct, out);
+}
+
+void hespmv_ctbatch_free(hespmv_ctbatch *b) {
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    dev_free(b->ctx, b->data);
+    delete b;
+}
+
+int hespmv_ctbatch_data(const hespmv_ctbatch *b, uint64_t **dev, size_t *n_ct) {
+    if (!b) return HESPMV_E_INVALID;
+    if (dev) *dev = b->data;
+    if (n_ct) *n_ct = b->n;
+    return HESPMV_OK;
+}
+
+int hespmv_ctbatch_upload(hespmv_ctbatch *b, const uint64_t *host, size_t n_ct, void *stream) {
+    if (!b || !host || n_ct > b->n) return HESPMV_E_INVALID;
+    hespmv_ctx *ctx = b->ctx;
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(b->data, host, n_ct * 2 * ctx->h.L * ctx->h.N * 8, cudaMemcpyHostToDevice,
+                       (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_ctbatch_download(const hespmv_ctbatch *b, uint64_t *host, size_t n_ct, void *stream) {
+    if (!b || !host || n_ct > b->n) return HESPMV_E_INVALID;
+    hespmv_ctx *ctx = b->ctx;
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(host, b->data, n_ct * 2 * ctx->h.L * ctx->h.N * 8, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
+                   uint64_t seed, hespmv_ctbatch **out) {
+    if (!ctx || !m || !out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    if (which != HESPMV_MATRIX && which != HESPMV_VECTOR) FAIL(HESPMV_E_INVALID, "bad operand kind");
+    if (which == HESPMV_VECTOR && !x && m->plan.cols > 0) FAIL(HESPMV_E_INVALID, "x is NULL");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const Plan &pl = m->plan;
+    const size_t n = pl.chunks.size();
+    const int64_t N = c.N, half = N / 2, L = c.L, LN = L * N;
+    hespmv_ctbatch *b = nullptr;
+    int rc = batch_new(ctx, n, &b);
+    if (rc) return rc;
+    const size_t G = std::max<size_t>(1, std::min<size_t>(n, 64));
+    // per group: vals (half int64), E (N), mq, u, e0, e1 ([L][N] each), coef (N int64)
+    const size_t words = G * (half + N + 4 * LN + N);
+    uint64_t *ws = workspace(ctx, words * 8);
+    if (!ws) {
+        hespmv_ctbatch_free(b);
+        FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    }
+    int64_t *dvals = (int64_t *)ws;
+    uint64_t *E = ws + G * half, *mq = E + G * N, *u = mq + G * LN, *e0 = u + G * LN,
+             *e1 = e0 + G * LN;
+    int64_t *coef = (int64_t *)(e1 + G * LN);
+    std::vector<int64_t> host(G * half);
+    for (size_t k0 = 0; k0 < n; k0 += G) {
+        const size_t gn = std::min(G, n - k0);
+        std::fill(host.begin(), host.end(), 0);
+        for (size_t k = 0; k < gn; ++k) {
+            const Chunk &ch = pl.chunks[k0 + k];
+            const int64_t cnt = (int64_t)ch.h * ch.c;
+            for (int64_t s = 0; s < cnt; ++s) {
+                if (which == HESPMV_MATRIX) {
+                    host[k * half + s] = pl.slot_vals[ch.slot0 + s];
+                } else {
+                    const int32_t ci = pl.slot_ci[ch.slot0 + s];
+                    host[k * half + s] = ci >= 0 ? x[ci] : 0;
+                }
+            }
+        }
+        const uint64_t sbase = kEncBase + 4 * (uint64_t)k0;
+        bool ok = cudaMemcpy(dvals, host.data(), gn * half * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && !op_scatter_slots(c, dvals, half, E, gn, 0);
+        ok = ok && !launch_ntt(c, E, c.L + c.K, 1, (int)gn, N, true, 0);
+        ok = ok && !op_lift(c, E, mq, gn, 0);
+        ok = ok && !launch_ntt(c, mq, 0, (int)L, (int)gn, LN, false, 0);
+        ok = ok && !op_sample_signed(c, seed, sbase + 1, 4, kTernary, coef, gn, 0);
+        ok = ok && !op_signed_to_limbs(c, coef, u, 0, (int)L, gn, 0);
+        ok = ok && !op_sample_signed(c, seed, sbase + 2, 4, kCbd21, coef, gn, 0);
+        ok = ok && !op_signed_to_limbs(c, coef, e0, 0, (int)L, gn, 0);
+        ok = ok && !op_sample_signed(c, seed, sbase + 3, 4, kCbd21, coef, gn, 0);
+        ok = ok && !op_signed_to_limbs(c, coef, e1, 0, (int)L, gn, 0);
+        ok = ok && !launch_ntt(c, u, 0, (int)L, (int)(3 * gn), LN, false, 0);
+        ok = ok && !op_enc_combine(c, u, e0, e1, mq, ctx->pk, b->data + k0 * 2 * LN, gn, 0);
+        ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+        if (!ok) {
+            hespmv_ctbatch_free(b);
+            FAIL(HESPMV_E_CUDA, std::string("encrypt: ") + cudaGetErrorString(cudaGetLastError()));
+        }
+    }
+    *out = b;
+    return HESPMV_OK;
+}
+
+int hespmv_spmv(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                const hespmv_ctbatch *X, hespmv_ctbatch **y, void *stream) {
+    return hespmv_spmv_batched(ctx, 1, &m, &A, &X, y, stream);
+}
+
+int hespmv_spmv_batched(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
+                        const hespmv_ctbatch *const *A, const hespmv_ctbatch *const *X,
+                        hespmv_ctbatch **y, void *stream) {
+    if (!ctx || (n && (!m || !A || !X || !y))) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    std::vector<const uint64_t *> a(n), x(n);
+    std::vector<uint64_t *> out(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (!m[i] || !A[i] || !X[i]) FAIL(HESPMV_E_INVALID, "null handle");
+        const size_t nc = m[i]->plan.chunks.size(), np = m[i]->plan.parts.size();
+        if (A[i]->n < nc || X[i]->n < nc) FAIL(HESPMV_E_INVALID, "operand batches are smaller than the chunk count");
+        if (y[i] == nullptr) {
+            int rc = batch_new(ctx, np, &y[i]);
+            if (rc) return rc;
+        } else if (y[i]->n < np) {
+            FAIL(HESPMV_E_INVALID, "result batch is smaller than the partition count");
+        }
+        a[i] = A[i]->data;
+        x[i] = X[i]->data;
+        out[i] = y[i]->data;
+    }
+    return spmv_core(ctx, n, m, a.data(), x.data(), out.data(), (cudaStream_t)stream);
+}
+
+int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_host,
+                     const uint64_t *X_host, uint64_t *y_host, void *stream) {
+    if (!ctx || !m || !A_host || !X_host || !y_host) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const size_t nc = m->plan.chunks.size(), np = m->plan.parts.size();
+    const size_t ct_bytes = 2 * (size_t)ctx->h.L * ctx->h.N * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    // device staging owned by the context, grown on demand
+    const size_t need = (2 * nc + np) * ct_bytes;
+    if (ctx->io_bytes < need) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, ctx->io);
+        ctx->io = dev_alloc(ctx, need);
+        ctx->io_bytes = ctx->io ? need : 0;
+    }
+    uint64_t *io = (uint64_t *)ctx->io;
+    if (!io) FAIL(HESPMV_E_NOMEM, "staging allocation failed");
+    uint64_t *dA = io, *dX = io + nc * ct_bytes / 8, *dY = dX + nc * ct_bytes / 8;
+    int rc = HESPMV_OK;
+    if (cudaMemcpyAsync(dA, A_host, nc * ct_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dX, X_host, nc * ct_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = HESPMV_E_CUDA;
+        ctx->err = "upload failed";
+    }
+    if (!rc) {
+        const uint64_t *pa = dA, *px = dX;
+        uint64_t *py = dY;
+        rc = spmv_core(ctx, 1, &m, &pa, &px, &py, st);
+    }
+    if (!rc && (cudaMemcpyAsync(y_host, dY, np * ct_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)) {
+        rc = HESPMV_E_CUDA;
+        ctx->err = "download failed";
+    }
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
+                         uint64_t *slots_out) {
+    if (!ctx || !b || !slots_out || index >= b->n) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t N = c.N, LN = (int64_t)c.L * N;
+    uint64_t *ws = workspace(ctx, (LN + 2 * N) * 8);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    uint64_t *x = ws, *msg = x + LN, *slots = msg + N;
+    CK(op_dec_phase(c, b->data + index * 2 * LN, ctx->sk, x, 0));
+    CK(launch_ntt(c, x, 0, c.L, 1, LN, true, 0));
+    CK(op_crt_to_t(c, x, msg, 0));
+    CK(launch_ntt(c, msg, c.L + c.K, 1, 1, N, false, 0));
+    CK(op_gather_slots(c, msg, slots, 0));
+    CK(cudaMemcpy(slots_out, slots, N * 8, cudaMemcpyDeviceToHost));
+    return HESPMV_OK;
+}
+
+int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
+                   int64_t *out_rows) {
+    if (!ctx || !m || !y || (!out_rows && m->plan.rows)) return HESPMV_E_INVALID;
+    if (y->n < m->plan.parts.size()) FAIL(HESPMV_E_INVALID, "result batch too small");
+    const uint64_t t = ctx->h.t;
+    std::vector<uint64_t> slots(ctx->h.N);
+    for (size_t p = 0; p < m->plan.parts.size(); ++p) {
+        int rc = hespmv_decrypt_slots(ctx, y, p, slots.data());
+        if (rc) return rc;
+        const Partition &P = m->plan.parts[p];
+        for (int32_t idx = 0; idx < P.rows; ++idx) {
+            const uint64_t v = slots[idx];
+            out_rows[P.row0 + P.rm[idx]] = (2 * v > t) ? (int64_t)v - (int64_t)t : (int64_t)v;
+        }
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_ntt_forward(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,
+                       int32_t n_items, void *stream) {
+    if (!ctx || !data || prime0 < 0 || n_limbs < 1 || prime0 + n_limbs > ctx->h.L + ctx->h.K + 1)
+        return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(launch_ntt(view(ctx), data, prime0, n_limbs, n_items, (int64_t)n_limbs * ctx->h.N, false,
+                  (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_ntt_inverse(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,
+                       int32_t n_items, void *stream) {
+    if (!ctx || !data || prime0 < 0 || n_limbs < 1 || prime0 + n_limbs > ctx->h.L + ctx->h.K + 1)
+        return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(launch_ntt(view(ctx), data, prime0, n_limbs, n_items, (int64_t)n_limbs * ctx->h.N, true,
+                  (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_he_add(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n,
+                  void *stream) {
+    if (!ctx || !a || !b || !out) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(op_add(view(ctx), a, b, out, 2 * n, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_he_tensor(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
+                     void *stream) {
+    if (!ctx || !a || !b || !d) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(op_tensor(view(ctx), a, b, d, n, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_he_relin(hespmv_ctx *ctx, const uint64_t *d, uint64_t *out, size_t n, void *stream) {
+    if (!ctx || !d || !out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t LN = (int64_t)c.L * c.N;
+    uint64_t *ws = workspace(ctx, ks_words(c, n) * 8);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    CK(keyswitch_n(c, d + 2 * LN, 3 * LN, ctx->rlk, out, d, 3 * LN, LN, 3, n, ws,
+                   (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_he_mult(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n,
+                   void *stream) {
+    if (!ctx || !a || !b || !out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t LN = (int64_t)c.L * c.N;
+    uint64_t *ws = workspace(ctx, (n * 3 * LN + ks_words(c, n)) * 8);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(op_tensor(c, a, b, ws, n, st));
+    CK(keyswitch_n(c, ws + 2 * LN, 3 * LN, ctx->rlk, out, ws, 3 * LN, LN, 3, n, ws + n * 3 * LN, st));
+    return HESPMV_OK;
+}
+
+int hespmv_he_rotate(hespmv_ctx *ctx, const uint64_t *ct, int32_t k, uint64_t *out, size_t n,
+                     void *stream) {
+    if (!ctx || !ct || !out || ct == out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t CT = 2 * (int64_t)c.L * c.N;
+    uint64_t *ws = workspace(ctx, (3 * n * CT + ks_words(c, n)) * 8);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    return rotate_n(ctx, ct, k, out, n, ws, (cudaStream_t)stream);
+}
+
+int hespmv_he_cmult_mask(hespmv_ctx *ctx, const uint64_t *ct, int32_t r, uint64_t *out, size_t n,
+                         void *stream) {
+    if (!ctx || !ct || !out || r < 0) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const uint64_t *m = mask_plaintext(ctx, r, (cudaStream_t)stream);
+    if (!m) FAIL(HESPMV_E_NOMEM, "mask creation failed");
+    CK(op_cmult(view(ctx), ct, m, out, n, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, uint64_t *out,
+                     size_t n, void *stream) {
+    if (!ctx || !d || !out) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const uint64_t *key = ctx->rlk;
+    if (galois_elt) {
+        auto it = ctx->gk.find(galois_elt);
+        if (it == ctx->gk.end()) FAIL(HESPMV_E_INVALID, "no Galois key for that element");
+        key = it->second;
+    }
+    const Ctx c = view(ctx);
+    const int64_t LN = (int64_t)c.L * c.N;
+    uint64_t *ws = workspace(ctx, ks_words(c, n) * 8);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    CK(keyswitch_n(c, d, LN, key, out, nullptr, 0, 0, 0, n, ws, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+}  // extern "C"

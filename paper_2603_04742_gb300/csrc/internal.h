@@ -1,0 +1,157 @@
+// Internal structures of the hespmv library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hespmv.h"
+#include "modarith.cuh"
+
+namespace hespmv {
+
+constexpr int kMaxPrimes = 21;  // L + K + 1 (t) <= 16 + 4 + 1
+
+// Host-side parameter tables (built once per context, then uploaded).
+struct HostTables {
+    int log2n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, slots = 0;
+    uint64_t t = 0;
+    std::vector<uint64_t> q;     // L + K + 1 moduli: Q, then P, then t
+    std::vector<uint64_t> psi;   // primitive 2N-th roots (index L+K: zeta for t)
+    std::vector<ModConst> mc;    // per modulus
+    // twiddles per modulus: [4][N] = psi_brv, psi_brv_shoup, ipsi_brv, ipsi_brv_shoup
+    std::vector<uint64_t> tw;
+    // ModUp constants, per digit j, source prime i (local index), target l:
+    //   qhat_inv[j][i] (Shoup pair) and qhat_mod[j][i][l] (Shoup pair)
+    std::vector<uint64_t> modup_inv;   // [dnum][alpha][2]
+    std::vector<uint64_t> modup_mod;   // [dnum][alpha][L+K][2]
+    // ModDown constants: per special prime k: (t^-1 * Phat_k^-1 mod p_k) Shoup pair,
+    // per (k, i): Phat_k mod q_i Shoup pair; per i: t mod q_i, P^-1 mod q_i Shoup pairs
+    std::vector<uint64_t> md_pk;       // [K][2]
+    std::vector<uint64_t> md_phat;     // [K][L][2]
+    std::vector<uint64_t> md_t;        // [L][2]
+    std::vector<uint64_t> md_pinv;     // [L][2]
+    // gadget: P mod q_i (Shoup pair) for the Q primes
+    std::vector<uint64_t> p_mod_q;     // [L][2]
+    // slot positions in the NTT domain: [N/2] for row 0, then [N/2] for row 1
+    std::vector<int32_t> slot_idx;
+    // decryption CRT: per Q prime (Qhat_i^-1 mod q_i, Shoup) and (Qhat_i mod t, Shoup),
+    // then (Q mod t, Shoup) and 1/q_i as doubles
+    std::vector<uint64_t> dec;         // [L][4] + [2]
+    std::vector<double> dec_inv_q;     // [L]
+    std::vector<uint64_t> t_mod;       // t mod q_l, [L+K]
+};
+
+// Device copies of the tables.
+struct DevTables {
+    ModConst *mc = nullptr;
+    uint64_t *tw = nullptr;
+    uint64_t *modup_inv = nullptr;
+    uint64_t *modup_mod = nullptr;
+    uint64_t *md_pk = nullptr;
+    uint64_t *md_phat = nullptr;
+    uint64_t *md_t = nullptr;
+    uint64_t *md_pinv = nullptr;
+    uint64_t *p_mod_q = nullptr;
+    int32_t *slot_idx = nullptr;
+    uint64_t *dec = nullptr;
+    double *dec_inv_q = nullptr;
+    uint64_t *t_mod = nullptr;
+};
+
+bool build_tables(const hespmv_params &p, HostTables &h, std::string &err);
+
+// Host-side bit reversal, primality and roots (used by the table builder).
+uint32_t host_bitrev(uint32_t x, int bits);
+uint32_t ntt_index_of_exponent(uint64_t e, int log2n);  // e odd, mod 2N
+
+// ------------------------------------------------------------------ format
+struct Chunk {
+    int32_t h = 0, c = 0, part = 0;
+    int64_t slot0 = 0;    // offset of this chunk's h*c slots in the concatenated arrays
+};
+
+struct Partition {
+    int32_t row0 = 0, rows = 0;
+    std::vector<int64_t> va;   // CSSC value array
+    std::vector<int32_t> ci;   // CSSC column indices
+    std::vector<int64_t> cp;   // Lmax + 1
+    std::vector<int32_t> rm;   // local row of sorted row p
+    int32_t chunk0 = 0, n_chunks = 0;
+};
+
+struct Plan {
+    int32_t rows = 0, cols = 0, s = 0;
+    int64_t nnz = 0;
+    std::vector<Partition> parts;
+    std::vector<Chunk> chunks;
+    std::vector<int64_t> slot_vals;   // concatenated chunk slot values
+    std::vector<int32_t> slot_ci;     // concatenated chunk slot column indices
+};
+
+// Returns empty string on success.
+std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *rowptr,
+                       const int32_t *colidx, const int64_t *vals, int32_t s, Plan &plan);
+// totalSum rotation amounts of a chunk (r rows, c columns) in order; flags
+// tell whether the step rotates the running sum (doubling) or the original.
+void total_sum_steps(int32_t r, int32_t c, std::vector<int32_t> &steps,
+                     std::vector<uint8_t> &from_original);
+
+// ------------------------------------------------------------ kernels (host launchers)
+struct Ctx;
+// NTT of n_items x n_limbs polynomials, item stride in words; limb k uses prime0 + k.
+cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, int n_items,
+                       int64_t item_stride, bool inverse, cudaStream_t st);
+
+}  // namespace hespmv
+
+// The opaque handles of the C ABI.
+struct hespmv_ctx {
+    hespmv_params p{};
+    hespmv::HostTables h;
+    hespmv::DevTables d;
+    std::string err;
+    int device = 0;
+    std::vector<std::pair<void *, size_t>> allocs;  // table/key blocks owned by the context
+    size_t owned_bytes = 0;
+    // keys (device)
+    bool have_keys = false;
+    uint64_t *sk = nullptr;    // [L+K][N]
+    uint64_t *pk = nullptr;    // [2][L][N]
+    uint64_t *rlk = nullptr;   // [dnum][2][L+K][N]
+    std::map<uint32_t, uint64_t *> gk;          // Galois element -> key
+    std::map<uint32_t, int32_t *> perms;        // Galois element -> device permutation [N]
+    std::map<int32_t, uint64_t *> masks;        // r -> mask plaintext [L][N]
+    // workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    // staging for evaluations from host buffers
+    void *io = nullptr;
+    size_t io_bytes = 0;
+};
+
+struct hespmv_cssc {
+    hespmv_ctx *ctx = nullptr;
+    hespmv::Plan plan;
+    std::vector<int32_t> steps;   // distinct rotation steps
+    int64_t n_rot = 0, n_ks = 0;
+};
+
+struct hespmv_ctbatch {
+    hespmv_ctx *ctx = nullptr;
+    uint64_t *data = nullptr;
+    size_t n = 0;
+    size_t bytes = 0;
+};
+
+namespace hespmv {
+struct Ctx {
+    const hespmv_ctx *c;
+    int N, L, K, dnum, alpha, log2n;
+};
+inline Ctx view(const hespmv_ctx *c) {
+    return Ctx{c, c->h.N, c->h.L, c->h.K, c->h.dnum, c->h.alpha, c->h.log2n};
+}
+}  // namespace hespmv

@@ -1,0 +1,75 @@
+// Host launchers of the elementwise, key-switching, sampling and
+// encode/decrypt kernels.  All run on the given stream; sizes in words.
+#pragma once
+#include "internal.h"
+
+namespace hespmv {
+
+// ct batches [n][2][L][N]
+cudaError_t op_add(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n_polys,
+                   cudaStream_t st);   // n_polys polynomials of L limbs
+cudaError_t op_tensor(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
+                      cudaStream_t st);
+// out = ct * pt (pt [L][N] shared by all n ciphertexts)
+cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint64_t *out, size_t n,
+                     cudaStream_t st);
+// acc (one ct) += w (one ct) * pt
+cudaError_t op_cmult_acc(const Ctx &c, uint64_t *acc, const uint64_t *w, const uint64_t *pt,
+                         bool first, cudaStream_t st);
+// out[p][i] = in[p][perm[i]] for n_polys polynomials (limbs are polynomials here)
+cudaError_t op_permute(const Ctx &c, const uint64_t *in, uint64_t *out, const int32_t *perm,
+                       size_t n_limbs_total, cudaStream_t st);
+// pointwise product of two arrays of polynomials over limbs [prime0, prime0+n_limbs)
+cudaError_t op_mul_limbs(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                         int prime0, int n_limbs, size_t n_items, cudaStream_t st);
+// copy n_items strided blocks of `words` words
+cudaError_t op_copy_strided(const uint64_t *src, int64_t src_stride, uint64_t *dst,
+                            int64_t dst_stride, int64_t words, size_t n_items, cudaStream_t st);
+
+// key switching pieces, n items
+cudaError_t op_modup(const Ctx &c, const uint64_t *dcoef, uint64_t *ext, size_t n, cudaStream_t st);
+cudaError_t op_inner(const Ctx &c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, size_t n,
+                     cudaStream_t st);
+cudaError_t op_moddown_delta(const Ctx &c, const uint64_t *acc, uint64_t *delta, size_t n,
+                             cudaStream_t st);
+// out[c] = (acc[c] - delta[c]) * P^-1 (+ add_c), add given as base + item/component strides;
+// add_mask bit c selects which components get the addend
+cudaError_t op_moddown_final(const Ctx &c, const uint64_t *acc, const uint64_t *delta,
+                             const uint64_t *add, int64_t add_item_stride, int64_t add_comp_stride,
+                             int add_mask, uint64_t *out, size_t n, cudaStream_t st);
+
+// sampling: signed coefficients [n_items][N]; stream of item k = stream0 + k * step
+enum SampleKind { kTernary = 0, kCbd21 = 1 };
+cudaError_t op_sample_signed(const Ctx &c, uint64_t seed, uint64_t stream0, uint64_t step, int kind,
+                             int64_t *out, size_t n_items, cudaStream_t st);
+// signed coefficients -> residues over limbs [prime0, prime0+n_limbs): out [n_items][n_limbs][N]
+cudaError_t op_signed_to_limbs(const Ctx &c, const int64_t *coef, uint64_t *out, int prime0,
+                               int n_limbs, size_t n_items, cudaStream_t st);
+// uniform residues (NTT domain by definition) over limbs [prime0, prime0+n_limbs)
+cudaError_t op_sample_uniform(const Ctx &c, uint64_t seed, uint64_t stream, uint64_t *out,
+                              int prime0, int n_limbs, cudaStream_t st);
+// key digit: b = -a*s + t*e + g*sp over all L+K limbs; g = P mod q_l on digit limbs
+cudaError_t op_ksk_combine(const Ctx &c, const uint64_t *a, const uint64_t *e, const uint64_t *s,
+                           const uint64_t *sp, int digit, uint64_t *b, cudaStream_t st);
+// pk0 = -a*s + t*e over Q
+cudaError_t op_pk_combine(const Ctx &c, const uint64_t *a, const uint64_t *e, const uint64_t *s,
+                          uint64_t *pk0, cudaStream_t st);
+// ct = (u pk0 + t e0 + m, u pk1 + t e1) for n items; u,e0,e1,m [n][L][N]
+cudaError_t op_enc_combine(const Ctx &c, const uint64_t *u, const uint64_t *e0, const uint64_t *e1,
+                           const uint64_t *m, const uint64_t *pk, uint64_t *ct, size_t n,
+                           cudaStream_t st);
+
+// encoding: values [n][nvals] (int64) -> E [n][N] mod t at the slot positions of row 0
+cudaError_t op_scatter_slots(const Ctx &c, const int64_t *vals, int64_t nvals, uint64_t *E,
+                             size_t n, cudaStream_t st);
+// m [n][N] in [0,t) -> centred residues over Q: out [n][L][N]
+cudaError_t op_lift(const Ctx &c, const uint64_t *m, uint64_t *out, size_t n, cudaStream_t st);
+// x [L][N] = c0 + c1*s
+cudaError_t op_dec_phase(const Ctx &c, const uint64_t *ct, const uint64_t *s, uint64_t *x,
+                         cudaStream_t st);
+// x coef [L][N] -> m [N] = ([x]_Q centred) mod t
+cudaError_t op_crt_to_t(const Ctx &c, const uint64_t *x, uint64_t *m, cudaStream_t st);
+// slots[j] = E[slot_idx[j]] for j < N
+cudaError_t op_gather_slots(const Ctx &c, const uint64_t *E, uint64_t *slots, cudaStream_t st);
+
+}  // namespace hespmv

@@ -1,0 +1,78 @@
+// Device modular arithmetic for word-size primes (q < 2^62; the contexts use
+// primes below 2^50 and a plaintext modulus t below 2^50).
+#pragma once
+#include <cstdint>
+
+namespace hespmv {
+
+// Per-modulus constants, resident in device memory.
+struct ModConst {
+    uint64_t q;
+    uint64_t mu;      // Barrett: floor(2^(2k) / q)
+    uint64_t ninv;    // N^-1 mod q
+    uint64_t ninv_s;  // Shoup companion of ninv
+    uint64_t w1ninv;  // psi^-1 * N^-1 mod q (last inverse butterfly)
+    uint64_t w1ninv_s;
+    int32_t k;        // bit length of q
+    int32_t pad;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return a >= b ? a - b : a + q - b;
+}
+
+// a * w mod q for a constant w < q with ws = floor(w * 2^64 / q); any a < 2^64.
+// The quotient estimate is low by at most one, so one subtraction suffices.
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    uint64_t qh = __umul64hi(a, ws);
+    uint64_t r = a * w - qh * q;
+    return r >= q ? r - q : r;
+}
+
+// Same, result left in [0, 2q).
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t ws,
+                                                   uint64_t q) {
+    uint64_t qh = __umul64hi(a, ws);
+    return a * w - qh * q;
+}
+
+// Barrett reduction of a 128-bit value x = hi:lo < 2^(2k), q of k bits:
+// q1 = x >> (k-1), q3 = (q1 * mu) >> (k+1), r = x - q3 q in [0, 3q).
+__device__ __forceinline__ uint64_t barrett_reduce(uint64_t hi, uint64_t lo, uint64_t q,
+                                                   uint64_t mu, int k) {
+    uint64_t q1 = (hi << (65 - k)) | (lo >> (k - 1));
+    uint64_t plo = q1 * mu;
+    uint64_t phi = __umul64hi(q1, mu);
+    uint64_t q3 = (phi << (63 - k)) | (plo >> (k + 1));
+    uint64_t r = lo - q3 * q;
+    if (r >= q) r -= q;
+    if (r >= q) r -= q;
+    return r;
+}
+
+// a * b mod q for a, b < q.
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const ModConst &m) {
+    return barrett_reduce(__umul64hi(a, b), a * b, m.q, m.mu, m.k);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): output i of the generator with
+// state s is mix(s + (i + 1) * gamma).
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t splitmix_at(uint64_t state, uint64_t i) {
+    return splitmix_mix(state + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace hespmv

@@ -1,0 +1,235 @@
+// Negacyclic NTT / inverse NTT over word-size primes, batched over limbs.
+//
+// Forward: Cooley-Tukey with the 2N-th root folded into the twiddles, so
+// index i of the output holds a(psi^(2*bitrev(i)+1)).  Stage s (s = 0..logN-1)
+// has m = 2^s groups; the pair (j, j+t), t = N/2^(s+1), in group i uses
+// W = psi^bitrev(m+i).  Inverse: Gentleman-Sande with psi^-bitrev(m+i) in the
+// reverse stage order, N^-1 folded into the last stage.
+//
+// A limb of N = 2^n words is viewed as R x C (R = 2^n1 rows, C = 2^n2
+// contiguous columns).  The first n1 stages only pair words of the same
+// column, the last n2 stages only words of the same row, so the transform is
+// two tile passes over shared memory ("columns" then "rows"; the inverse in
+// the opposite order).  Small rings (N <= 4096) run one "rows" pass with
+// n1 = 0.
+#include "internal.h"
+
+namespace hespmv {
+
+struct NttArgs {
+    uint64_t *data;
+    int64_t item_stride;  // words between items
+    int n_limbs;          // limbs per item (contiguous, N words apart)
+    int prime0;           // modulus index of limb 0
+    const ModConst *mc;
+    const uint64_t *tw;   // [modulus][4][N]
+    int log2n;
+};
+
+__device__ __forceinline__ void limb_of(const NttArgs &a, uint64_t *&x, int &prime) {
+    const int N = 1 << a.log2n;
+    const int limb = blockIdx.y;
+    const int item = limb / a.n_limbs;
+    const int k = limb - item * a.n_limbs;
+    x = a.data + (int64_t)item * a.item_stride + (int64_t)k * N;
+    prime = a.prime0 + k;
+}
+
+// First n1 forward stages on columns [c0, c0+TC) of the R x C view.
+__global__ void k_ntt_fwd_cols(NttArgs a, int n1, int TC) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n;
+    const int R = 1 << n1, C = N >> n1;
+    const uint64_t q = a.mc[prime].q;
+    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;
+    const uint64_t *tws = tw + N;
+    const int c0 = blockIdx.x * TC;
+    for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+        const int r = e / TC, cc = e - r * TC;
+        sm[e] = x[(int64_t)r * C + c0 + cc];
+    }
+    __syncthreads();
+    for (int s = 0; s < n1; ++s) {
+        const int half = R >> (s + 1), m = 1 << s;
+        for (int b = threadIdx.x; b < (R / 2) * TC; b += blockDim.x) {
+            const int cc = b % TC, bb = b / TC;
+            const int grp = bb / half, pos = bb - grp * half;
+            const int r = grp * 2 * half + pos;
+            const uint64_t W = tw[m + grp], Ws = tws[m + grp];
+            const uint64_t u = sm[r * TC + cc];
+            const uint64_t v = mul_shoup(sm[(r + half) * TC + cc], W, Ws, q);
+            sm[r * TC + cc] = add_mod(u, v, q);
+            sm[(r + half) * TC + cc] = sub_mod(u, v, q);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+        const int r = e / TC, cc = e - r * TC;
+        x[(int64_t)r * C + c0 + cc] = sm[e];
+    }
+}
+
+// Last n2 forward stages on rows [r0, r0+TR).
+__global__ void k_ntt_fwd_rows(NttArgs a, int n1, int TR) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n;
+    const int C = N >> n1;
+    const uint64_t q = a.mc[prime].q;
+    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;
+    const uint64_t *tws = tw + N;
+    const int r0 = blockIdx.x * TR;
+    uint64_t *base = x + (int64_t)r0 * C;
+    for (int e = threadIdx.x; e < TR * C; e += blockDim.x) sm[e] = base[e];
+    __syncthreads();
+    for (int s = n1; s < a.log2n; ++s) {
+        const int m = 1 << s, t = N >> (s + 1);
+        const int per_row = C / (2 * t);
+        for (int b = threadIdx.x; b < TR * (C / 2); b += blockDim.x) {
+            const int rr = b / (C / 2), bb = b - rr * (C / 2);
+            const int grp = bb / t, pos = bb - grp * t;
+            const int idx = rr * C + grp * 2 * t + pos;
+            const int i = (r0 + rr) * per_row + grp;
+            const uint64_t u = sm[idx];
+            const uint64_t v = mul_shoup(sm[idx + t], tw[m + i], tws[m + i], q);
+            sm[idx] = add_mod(u, v, q);
+            sm[idx + t] = sub_mod(u, v, q);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < TR * C; e += blockDim.x) base[e] = sm[e];
+}
+
+// Inverse stages logN-1 .. n1 on rows (N^-1 folded in when n1 == 0).
+__global__ void k_ntt_inv_rows(NttArgs a, int n1, int TR) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n;
+    const int C = N >> n1;
+    const ModConst mc = a.mc[prime];
+    const uint64_t q = mc.q;
+    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;
+    const uint64_t *itws = itw + N;
+    const int r0 = blockIdx.x * TR;
+    uint64_t *base = x + (int64_t)r0 * C;
+    for (int e = threadIdx.x; e < TR * C; e += blockDim.x) sm[e] = base[e];
+    __syncthreads();
+    for (int s = a.log2n - 1; s >= n1; --s) {
+        const int m = 1 << s, t = N >> (s + 1);
+        const int per_row = C / (2 * t);
+        for (int b = threadIdx.x; b < TR * (C / 2); b += blockDim.x) {
+            const int rr = b / (C / 2), bb = b - rr * (C / 2);
+            const int grp = bb / t, pos = bb - grp * t;
+            const int idx = rr * C + grp * 2 * t + pos;
+            const int i = (r0 + rr) * per_row + grp;
+            const uint64_t u = sm[idx], v = sm[idx + t];
+            if (s == 0) {
+                sm[idx] = mul_shoup(u + v, mc.ninv, mc.ninv_s, q);
+                sm[idx + t] = mul_shoup(u + q - v, mc.w1ninv, mc.w1ninv_s, q);
+            } else {
+                sm[idx] = add_mod(u, v, q);
+                sm[idx + t] = mul_shoup(u + q - v, itw[m + i], itws[m + i], q);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < TR * C; e += blockDim.x) base[e] = sm[e];
+}
+
+// Inverse stages n1-1 .. 0 on columns, N^-1 folded into stage 0.
+__global__ void k_ntt_inv_cols(NttArgs a, int n1, int TC) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n;
+    const int R = 1 << n1, C = N >> n1;
+    const ModConst mc = a.mc[prime];
+    const uint64_t q = mc.q;
+    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;
+    const uint64_t *itws = itw + N;
+    const int c0 = blockIdx.x * TC;
+    for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+        const int r = e / TC, cc = e - r * TC;
+        sm[e] = x[(int64_t)r * C + c0 + cc];
+    }
+    __syncthreads();
+    for (int s = n1 - 1; s >= 0; --s) {
+        const int half = R >> (s + 1), m = 1 << s;
+        for (int b = threadIdx.x; b < (R / 2) * TC; b += blockDim.x) {
+            const int cc = b % TC, bb = b / TC;
+            const int grp = bb / half, pos = bb - grp * half;
+            const int r = grp * 2 * half + pos;
+            const uint64_t u = sm[r * TC + cc], v = sm[(r + half) * TC + cc];
+            if (s == 0) {
+                sm[r * TC + cc] = mul_shoup(u + v, mc.ninv, mc.ninv_s, q);
+                sm[(r + half) * TC + cc] = mul_shoup(u + q - v, mc.w1ninv, mc.w1ninv_s, q);
+            } else {
+                sm[r * TC + cc] = add_mod(u, v, q);
+                sm[(r + half) * TC + cc] = mul_shoup(u + q - v, itw[m + grp], itws[m + grp], q);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+        const int r = e / TC, cc = e - r * TC;
+        x[(int64_t)r * C + c0 + cc] = sm[e];
+    }
+}
+
+cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, int n_items,
+                       int64_t item_stride, bool inverse, cudaStream_t st) {
+    if (n_items <= 0 || n_limbs <= 0) return cudaSuccess;
+    NttArgs a;
+    a.data = data;
+    a.item_stride = item_stride;
+    a.n_limbs = n_limbs;
+    a.prime0 = prime0;
+    a.mc = c.c->d.mc;
+    a.tw = c.c->d.tw;
+    a.log2n = c.log2n;
+    const int N = c.N;
+    const int total = n_limbs * n_items;
+    if (total > 65535) {
+        // grid.y limit: split into slices of whole items
+        const int per = 65535 / n_limbs;
+        for (int i0 = 0; i0 < n_items; i0 += per) {
+            cudaError_t e = launch_ntt(c, data + (int64_t)i0 * item_stride, prime0, n_limbs,
+                                       std::min(per, n_items - i0), item_stride, inverse, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if (c.log2n <= 12) {
+        dim3 grid(1, total);
+        const int thr = std::min(256, N / 2);
+        const size_t smem = (size_t)N * 8;
+        if (inverse)
+            k_ntt_inv_rows<<<grid, thr, smem, st>>>(a, 0, 1);
+        else
+            k_ntt_fwd_rows<<<grid, thr, smem, st>>>(a, 0, 1);
+        return cudaGetLastError();
+    }
+    const int n1 = c.log2n / 2;
+    const int R = 1 << n1, C = N >> n1;
+    const int TC = std::max(1, 2048 / R), TR = std::max(1, 2048 / C);
+    const size_t smc = (size_t)R * TC * 8, smr = (size_t)TR * C * 8;
+    dim3 gc(C / TC, total), gr(R / TR, total);
+    if (!inverse) {
+        k_ntt_fwd_cols<<<gc, 256, smc, st>>>(a, n1, TC);
+        k_ntt_fwd_rows<<<gr, 256, smr, st>>>(a, n1, TR);
+    } else {
+        k_ntt_inv_rows<<<gr, 256, smr, st>>>(a, n1, TR);
+        k_ntt_inv_cols<<<gc, 256, smc, st>>>(a, n1, TC);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hespmv

@@ -1,0 +1,315 @@
+"""GPU parity: every RNS residue of every intermediate the C ABI exposes
+(NTT, keys, ciphertexts, tensor, relinearisation, key switch, rotation,
+mask multiply, the SpMV result) equals the oracle's from the same seeds, and
+decryption equals the plaintext SpMV.  Integer work: bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import native
+from oracle import spmv as S
+from oracle.bgv import Oracle
+from oracle.params import Params, plain_modulus
+from paper_2603_04742_gb300 import binding as B
+from paper_2603_04742_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint64)
+
+
+def make_pair(logn, L, K, dnum, t, seed=1, steps=None, policy="pow2", slots=0):
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t, rot_policy=policy, slots=slots)
+    p = Params(log2n=logn, L=L, K=K, dnum=dnum, t=t, slots=slots)
+    orc = Oracle(p)
+    ctx.keygen(seed, steps)
+    gels = set()
+    if steps is None:
+        if policy == "pow2":
+            b = 1
+            while b < p.N // 2:
+                gels.add(pow(5, b, 2 * p.N))
+                b *= 2
+    else:
+        for k in steps:
+            gels.update(orc.rotation_elements(k, policy))
+    orc.keygen(seed, sorted(gels))
+    return ctx, orc
+
+
+@pytest.mark.parametrize("logn", [4, 6, 10, 12, 13, 14, 15])
+def test_ntt_parity_all_moduli(logn):
+    from paper_2603_04742_gb300.api import Context
+    N = 1 << logn
+    t = plain_modulus(N, 1 << 20)
+    ctx = Context(logn, 3, 2, 3, t)
+    q, psi, zeta = ctx.moduli()
+    moduli = q + [t]
+    roots = psi + [zeta]
+    rng = np.random.default_rng(logn)
+    a = np.stack([rng.integers(0, m, size=N, dtype=np.uint64) for m in moduli])
+    d = dev(a)
+    ctx.ntt(d.data_ptr(), 0, len(moduli))
+    got = host(d)
+    for k in range(len(moduli)):
+        assert np.array_equal(got[k], native.ntt(a[k], moduli[k], roots[k])), k
+    ctx.ntt(d.data_ptr(), 0, len(moduli), inverse=True)
+    assert np.array_equal(host(d), a)
+    # batched items: 4 items x 3 Q limbs
+    b = np.concatenate([np.stack([rng.integers(0, m, size=N, dtype=np.uint64) for m in q[:3]])
+                        for _ in range(4)])
+    d = dev(b)
+    ctx.ntt(d.data_ptr(), 0, 3, n_items=4)
+    got = host(d)
+    for r in range(12):
+        assert np.array_equal(got[r], native.ntt(b[r], q[r % 3], psi[r % 3]))
+
+
+def test_keys_parity_c1():
+    logn, L, K, dnum, t = synth.RING["c1"]
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=77)
+    N, LK = 1 << logn, L + K
+    assert np.array_equal(ctx.key_export(B.HESPMV_KEY_SECRET).reshape(LK, N), orc.s)
+    pk = ctx.key_export(B.HESPMV_KEY_PUBLIC).reshape(2, L, N)
+    assert np.array_equal(pk[0], orc.pk[0]) and np.array_equal(pk[1], orc.pk[1])
+    assert np.array_equal(ctx.key_export(B.HESPMV_KEY_RELIN).reshape(orc.rlk.shape), orc.rlk)
+    for g, key in orc.gk.items():
+        assert np.array_equal(ctx.key_export(B.HESPMV_KEY_GALOIS, g).reshape(key.shape), key), g
+
+
+def test_keys_parity_two_special_primes():
+    # alpha = 2 digits and K = 2, small ring
+    N = 1 << 8
+    t = plain_modulus(N, 1 << 16)
+    ctx, orc = make_pair(8, 8, 2, 4, t, seed=5, steps=[1, 3, 7])
+    assert np.array_equal(ctx.key_export(B.HESPMV_KEY_RELIN).reshape(orc.rlk.shape), orc.rlk)
+    for g, key in orc.gk.items():
+        assert np.array_equal(ctx.key_export(B.HESPMV_KEY_GALOIS, g).reshape(key.shape), key)
+
+
+def _random_slot_ciphertexts(ctx, orc, n, seed):
+    """n ciphertexts of random slot vectors, encrypted by the library through
+    a one-chunk-per-ciphertext plan; the oracle encrypts the same values."""
+    N = orc.p.N
+    rng = np.random.default_rng(seed)
+    h = N // 2
+    rows = n * h
+    # a diagonal-like matrix whose CSSC has n aligned columns of height h ...
+    # simpler: encrypt the vector operand of a plan with n chunks of h x 1
+    vals = rng.integers(0, orc.p.t, size=(n, h), dtype=np.int64)
+    # build a CSR with h rows and n columns fully dense: chunk k = column k
+    rowptr = np.arange(0, h * n + 1, n, dtype=np.int64)
+    colidx = np.tile(np.arange(n, dtype=np.int32), h)
+    m = ctx.encode_cssc(h, n, rowptr, colidx, vals.T.reshape(-1))
+    assert m.n_chunks == n and all(c == 1 for c in m.chunks()[1])
+    A = ctx.encrypt(m, B.HESPMV_MATRIX, seed=seed)
+    oc = [orc.encrypt(orc.encode(vals[k]), seed, k) for k in range(n)]
+    got = A.download()
+    for k in range(n):
+        assert np.array_equal(got[k], oc[k]), k
+    return A, oc, vals
+
+
+@pytest.fixture(scope="module")
+def pair_small():
+    N = 1 << 10
+    t = plain_modulus(N, 1 << 20)
+    return make_pair(10, 5, 2, 3, t, seed=11, steps=[1, 2, 5, 100, 511])
+
+
+def test_encrypt_and_ops_parity(pair_small):
+    ctx, orc = pair_small
+    A, oc, vals = _random_slot_ciphertexts(ctx, orc, 3, 21)
+    L, N = orc.p.L, orc.p.N
+    CT = 2 * L * N
+    a_ptr = A.ptr
+    b_ptr = A.ptr + CT * 8
+    # add
+    out = torch.zeros(CT, dtype=torch.int64, device="cuda")
+    ctx.he_add(a_ptr, b_ptr, out.data_ptr())
+    assert np.array_equal(host(out).reshape(2, L, N), orc.add(oc[0], oc[1]))
+    # tensor
+    d = torch.zeros(3 * L * N, dtype=torch.int64, device="cuda")
+    ctx.he_tensor(a_ptr, b_ptr, d.data_ptr())
+    od = orc.tensor(oc[0], oc[1])
+    assert np.array_equal(host(d).reshape(3, L, N), od)
+    # key switch of d2 with the relinearisation key
+    ks = torch.zeros(CT, dtype=torch.int64, device="cuda")
+    ctx.keyswitch(d.data_ptr() + 2 * L * N * 8, 0, ks.data_ptr())
+    assert np.array_equal(host(ks).reshape(2, L, N), orc.keyswitch(od[2], orc.rlk))
+    # relinearisation and HE-Mult
+    ctx.he_relin(d.data_ptr(), out.data_ptr())
+    om = orc.relinearize(od)
+    assert np.array_equal(host(out).reshape(2, L, N), om)
+    out2 = torch.zeros(CT, dtype=torch.int64, device="cuda")
+    ctx.he_mult(a_ptr, b_ptr, out2.data_ptr())
+    assert np.array_equal(host(out2).reshape(2, L, N), om)
+    # rotations (power-of-two chains)
+    for k in (1, 2, 5, 100, 511):
+        ctx.he_rotate(a_ptr, k, out.data_ptr())
+        assert np.array_equal(host(out).reshape(2, L, N), orc.rotate(oc[0], k)), k
+    # mask multiply
+    for r in (1, 37, N // 2):
+        ctx.he_cmult_mask(a_ptr, r, out.data_ptr())
+        assert np.array_equal(host(out).reshape(2, L, N), orc.cmult(oc[0], S.mask_ntt(orc, r)))
+    # decryption of a product
+    slots = ctx.decrypt_slots(A, 0)
+    assert np.array_equal(slots[:N // 2], vals[0] % orc.p.t)
+
+
+def test_rotation_exact_policy_parity():
+    N = 1 << 9
+    t = plain_modulus(N, 1 << 18)
+    ctx, orc = make_pair(9, 3, 1, 3, t, seed=3, steps=[3, 17, 200], policy="exact")
+    A, oc, vals = _random_slot_ciphertexts(ctx, orc, 1, 4)
+    CT = 2 * 3 * N
+    out = torch.zeros(CT, dtype=torch.int64, device="cuda")
+    for k in (3, 17, 200):
+        ctx.he_rotate(A.ptr, k, out.data_ptr())
+        assert np.array_equal(host(out).reshape(2, 3, N), orc.rotate(oc[0], k, "exact"))
+
+
+def run_spmv_pair(ctx, orc, A, x, kseed=1, policy="pow2"):
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    y = ctx.spmv(m, ca, cx)
+    torch.cuda.synchronize()
+    oa = S.encrypt_matrix(orc, plan, 2)
+    ox = S.encrypt_vector(orc, plan, x, 3)
+    ga, gx = ca.download(), cx.download()
+    for k in range(len(oa)):
+        assert np.array_equal(ga[k], oa[k]) and np.array_equal(gx[k], ox[k]), k
+    ores = S.spmv(orc, plan, oa, ox, policy)
+    gy = y.download()
+    for p_ in range(len(ores)):
+        assert np.array_equal(gy[p_], ores[p_]), p_
+    out = ctx.decrypt(m, y)
+    return m, y, out, S.decrypt_result(orc, plan, ores)
+
+
+def test_spmv_small_partitions_parity():
+    N = 1 << 6
+    t = plain_modulus(N, 1 << 20)
+    A, x = synth.small_matrix(9, 70, 50, 400, -9, 9)
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(6, 3, 1, 3, t, slots=24)
+    orc = Oracle(Params(log2n=6, L=3, K=1, dnum=3, t=t, slots=24))
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    steps = m.rotation_steps()
+    ctx.keygen(4, steps)
+    gels = set()
+    for k in steps:
+        gels.update(orc.rotation_elements(k))
+    orc.keygen(4, sorted(gels))
+    m2, y, out, oout = run_spmv_pair(ctx, orc, A, x)
+    assert m2.n_parts == 3
+    assert list(out) == list(A.matvec(x)) == list(oout)
+
+
+@pytest.mark.parametrize("policy", ["pow2", "exact"])
+def test_spmv_c1_parity(policy):
+    logn, L, K, dnum, t = synth.RING["c1"]
+    A, x = synth.workload("c1")
+    from paper_2603_04742_gb300.api import Context
+    probe = Context(logn, L, K, dnum, t, device=-1, torch_alloc=False)
+    steps = probe.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals).rotation_steps()
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=1, steps=steps, policy=policy)
+    m, y, out, oout = run_spmv_pair(ctx, orc, A, x, policy=policy)
+    assert list(out) == list(A.matvec(x))
+
+
+def test_spmv_c2_parity():
+    logn, L, K, dnum, t = synth.RING["c2"]
+    A, x = synth.workload("c2")
+    from paper_2603_04742_gb300.api import Context
+    probe = Context(logn, L, K, dnum, t, device=-1, torch_alloc=False)
+    steps = probe.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals).rotation_steps()
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=1, steps=steps)
+    m, y, out, oout = run_spmv_pair(ctx, orc, A, x)
+    assert list(out) == list(A.matvec(x))
+
+
+def test_spmv_c3_full_size_parity_and_tolerance():
+    """The bench's workload: 27-point stencil, N = 2^15, 8 + 2 primes."""
+    logn, L, K, dnum, t = synth.RING["c3"]
+    A, xf = synth.workload("c3")
+    Af = A.vals.copy()
+    A.vals = synth.quantize(Af)
+    x = synth.quantize(xf)
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=1, steps=[])
+    m, y, out, oout = run_spmv_pair(ctx, orc, A, x)
+    exact = A.matvec(x)
+    assert list(out) == list(exact)
+    # fixed point: result scale 2^30, tolerance 1e-3 relative in the max norm
+    A.vals = Af
+    yref = A.matvec(xf)
+    yhat = np.asarray(out, dtype=np.float64) / float(1 << 30)
+    assert np.max(np.abs(yhat - yref)) <= 1e-3 * np.max(np.abs(yref))
+
+
+def test_spmv_host_buffers_and_batched_match():
+    logn, L, K, dnum, t = synth.RING["c1"]
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t)
+    ctx.keygen(9)
+    insts = [synth.small_matrix(s, 300, 280, 900 + 200 * s) for s in range(3)]
+    ms, As, Xs, ys = [], [], [], []
+    for A, x in insts:
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        ms.append(m)
+        As.append(ctx.encrypt(m, B.HESPMV_MATRIX, seed=5))
+        Xs.append(ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=6))
+        ys.append(ctx.spmv(m, As[-1], Xs[-1]))
+    yb = ctx.spmv_batched(ms, As, Xs)
+    for i, (A, x) in enumerate(insts):
+        assert np.array_equal(yb[i].download(), ys[i].download())
+        assert list(ctx.decrypt(ms[i], yb[i])) == list(A.matvec(x))
+        hA, hX = As[i].download(), Xs[i].download()
+        hy = np.zeros((ms[i].n_parts, 2, L, 1 << logn), dtype=np.uint64)
+        ctx.spmv_host(ms[i], hA, hX, hy)
+        assert np.array_equal(hy, ys[i].download())
+
+
+def test_spmv_edge_cases():
+    logn, L, K, dnum, t = synth.RING["c1"]
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t, slots=64)
+    ctx.keygen(2)
+    N = 1 << logn
+    cases = []
+    # one non-zero; an empty row block in the middle; a full row; rows == slots
+    cases.append((synth.CSR(3, 3, np.array([0, 0, 1, 1]), np.array([2], np.int32),
+                            np.array([7])), np.array([1, 2, 3])))
+    r = np.zeros(129, dtype=np.int64)
+    r[65:] = 1
+    rowptr = np.concatenate([[0], np.cumsum(r)])
+    cases.append((synth.CSR(129, 5, rowptr, np.zeros(64, np.int32), np.arange(64)),
+                  np.array([3, 0, 0, 0, 0])))
+    cases.append((synth.CSR(2, 64, np.array([0, 64, 64]), np.arange(64, dtype=np.int32),
+                            np.ones(64, dtype=np.int64)), np.arange(64)))
+    A, x = synth.small_matrix(1, 64, 64, 64 * 64)   # dense 64 x 64: c spans several blocks
+    cases.append((A, x))
+    for A, x in cases:
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=1)
+        cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=2)
+        y = ctx.spmv(m, ca, cx)
+        assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+    # an all-zero matrix gives zero ciphertexts and zero rows
+    m = ctx.encode_cssc(4, 4, [0, 0, 0, 0, 0], [], [])
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=1)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=np.zeros(4, np.int64), seed=2)
+    y = ctx.spmv(m, ca, cx)
+    assert list(ctx.decrypt(m, y)) == [0, 0, 0, 0]
+    assert not np.any(y.download())
