@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Encrypted SpMV benchmark (one JSON line on stdout).
+
+Workload (default): the 27-point stencil on a 16 x 32 x 32 grid (16,384 rows,
+406,456 non-zeros), values uniform in [-1, 1] in fixed point (2^15), under
+BGV with N = 2^15, 8 ciphertext primes + 2 special primes, dnum = 4.  One
+step is one full encrypted SpMV: the cloud lines of Algorithm 1 (HE-Mult with
+relinearisation per chunk) and Aggregation (Algorithm 4), from device-resident
+encrypted inputs to the device-resident encrypted result.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent SpMV instance (weak
+scaling, no collective on the data path); rank 0 prints the line.
+--impl reference times the CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted SpMV/s and nnz/s at N=2^15, batched vs plain; p50/p99 latency"
+CONFIGS = {
+    "c3": "27-point stencil 16x32x32 (16384 rows, 406456 nnz), fixed point 2^15; "
+          "BGV N=2^15, 8+2 primes of 50 bits, dnum 4, t=1099512938497",
+    "c1": "512x512, 2621 nnz uniform, integers [-15,15]; BGV N=2^12, 3+1 primes, dnum 3, t=65537",
+    "c2": "4096x4096, 16777 nnz, power-law column counts, integers [-127,127]; "
+          "BGV N=2^14, 5+1 primes, dnum 5, t=17006593",
+}
+# dense 32-bit multiply-adds per SM per clock, SM count and maximum SM clock
+# of a GB300; a Shoup modular product needs 10 32x32-bit partial products
+IMAD_PER_SM_CLK = 64
+SMS = 152
+SM_MAX_MHZ = 2070.0
+IMAD_PER_MULMOD = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_workload(name):
+    from paper_2603_04742_gb300 import synth
+    A, x = synth.workload(name)
+    if A.vals.dtype.kind == "f":
+        A.vals = synth.quantize(A.vals)
+        x = synth.quantize(x)
+    return A, x, synth.RING[name]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.device = device
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot):
+    """Algorithmic work of one step in kernel `name`: (mulmods, bytes).
+
+    n_ks = key switches per step (relinearisations + elementary rotations).
+    Bytes: one read of every input and one write of every output."""
+    logn, L, K, dnum = ring[:4]
+    N = 1 << logn
+    LK = L + K
+    alpha = -(-L // dnum)
+    n1 = logn // 2 if logn > 12 else 0
+    n2 = logn - n1
+    w = 8 * N  # bytes per limb
+    fwd_limbs = n_ks * (dnum * LK - L + 2 * L)
+    inv_limbs = n_ks * (L + 2 * K)
+    half = N // 2
+    m = {
+        "k_ntt_fwd_cols": (fwd_limbs * half * n1, fwd_limbs * 2 * w),
+        "k_ntt_fwd_rows": (fwd_limbs * half * n2, fwd_limbs * 2 * w),
+        "k_ntt_inv_rows": (inv_limbs * half * n2, inv_limbs * 2 * w),
+        "k_ntt_inv_cols": (inv_limbs * half * n1, inv_limbs * 2 * w),
+        "k_modup": (n_ks * dnum * alpha * (1 + LK - alpha) * N,
+                    n_ks * (L + dnum * (LK - alpha)) * w),
+        "k_inner": (n_ks * 2 * dnum * LK * N, n_ks * (dnum * LK + 2 * LK) * w + 2 * dnum * LK * w),
+        "k_moddown_delta": (n_ks * 2 * (K + K * L + L) * N, n_ks * 2 * (K + L) * w),
+        "k_moddown_final": (n_ks * 2 * L * N, n_ks * 2 * L * 3 * w),
+        "k_tensor": (n_chunks * 4 * L * N, n_chunks * 7 * L * w),
+        "k_cmult_acc": (n_chunks * 2 * L * N, n_chunks * 2 * L * 3 * w),
+        "k_copy_strided": (0, n_ks * 2 * L * w),
+        "k_permute": (0, 2 * n_ks * 2 * L * w),
+        "k_add": (0, n_rot * 3 * 2 * L * w),
+    }
+    return m.get(name, (0, 0))
+
+
+class OracleSample:
+    """The oracle's cloud evaluation (HE-Mult + relinearisation, totalSum,
+    mask, accumulate) on the first `sample_chunks` chunks of partition 0;
+    keys and ciphertexts are prepared once, outside the timing."""
+
+    def __init__(self, A, x, ring, sample_chunks, seed=1):
+        from oracle import spmv as S
+        from oracle.bgv import Oracle
+        from oracle.params import Params
+        logn, L, K, dnum, t = ring
+        self.S = S
+        self.orc = Oracle(Params(log2n=logn, L=L, K=K, dnum=dnum, t=t))
+        plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, self.orc.p.slots)
+        self.n_total = len(plan.chunks)
+        self.chunks = plan.parts[0].chunks[:sample_chunks]
+        gels = set()
+        for ch in self.chunks:
+            for k in S.rotation_steps(ch.c, ch.h):
+                gels.update(self.orc.rotation_elements(k))
+        self.orc.keygen(seed, sorted(gels))
+        reorg = S.reorg_vector(x, self.chunks)
+        self.ca = [self.orc.encrypt(self.orc.encode(ch.values), 2, k)
+                   for k, ch in enumerate(self.chunks)]
+        self.cx = [self.orc.encrypt(self.orc.encode(v), 3, k) for k, v in enumerate(reorg)]
+
+    def run(self):
+        t0 = time.perf_counter()
+        self.S.cloud(self.orc, self.chunks, self.ca, self.cx)
+        return time.perf_counter() - t0
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step evaluates one chunk of the
+    workload; SpMV/s = 1 / (seconds per chunk x chunks per SpMV)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, x, ring = load_workload(args.config)
+    smp = OracleSample(A, x, ring, 1)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = smp.run()
+        if i >= args.warmup:
+            times.append(dt)
+    n_total = smp.n_total
+    per_chunk = sum(times) / len(times)
+    value = 1.0 / (per_chunk * n_total)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SpMV/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_chunk * n_total * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": CONFIGS[args.config]},
+            "nnz_per_s": value * A.nnz,
+            "cpu_baseline": {"value": value, "unit": "SpMV/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: the oracle's cloud evaluation of 1 of %d chunks "
+                                       "(HE-Mult, relinearisation, totalSum, mask, add); "
+                                       "extrapolated by the chunk count" % n_total},
+            "e2e": {"value": value, "unit": "SpMV/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300.api import Context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    A, x, ring = load_workload(args.config)
+    logn, L, K, dnum, t = ring
+    ctx = Context(logn, L, K, dnum, t, device=local)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    ctx.keygen(1 + rank, m.rotation_steps())
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 10 * rank)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3 + 10 * rank)
+    y = ctx.spmv(m, ca, cx)
+    torch.cuda.synchronize()
+    correct = list(ctx.decrypt(m, y)) == list(A.matvec(x))
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        ctx.spmv(m, ca, cx, y=y, stream=stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.spmv(m, ca, cx, y=y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * 1000.0 / ms
+
+    # e2e through the C ABI from pinned host buffers
+    e2e = None
+    ct_words = 2 * L * (1 << logn)
+    if not args.no_e2e:
+        hA = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
+        hX = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
+        hY = torch.empty(m.n_parts * ct_words, dtype=torch.int64, pin_memory=True)
+        hA.numpy()[:] = ca.download().reshape(-1).view(np.int64)
+        hX.numpy()[:] = cx.download().reshape(-1).view(np.int64)
+        nA, nX, nY = (hA.numpy().view(np.uint64), hX.numpy().view(np.uint64),
+                      hY.numpy().view(np.uint64))
+        for _ in range(2):
+            ctx.spmv_host(m, nA, nX, nY, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.spmv_host(m, nA, nX, nY, stream=stream)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([dt], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        assert np.array_equal(nY.reshape(y.download().shape), y.download())
+        e2e = {"value": world * args.steps / dt, "unit": "SpMV/s",
+               "h2d_bytes_per_step": 2 * m.n_chunks * ct_words * 8,
+               "d2h_bytes_per_step": m.n_parts * ct_words * 8}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    n_ks = m.n_chunks + m.n_keyswitch
+    kernels = {}
+    total_ms = sum(v[1] for v in prof.values())
+    for name, (cnt, kms) in prof.items():
+        mm, by = kernel_model(name, ring, n_ks, m.n_chunks, m.n_parts, m.n_rot)
+        kernels[name] = {"launches_per_step": cnt / args.steps, "ms_per_step": kms / args.steps,
+                         "share": kms / total_ms if total_ms else 0.0,
+                         "mulmods_per_step": mm, "bytes_per_step": by}
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    kt = kernels[top]
+    launch_ms = kt["ms_per_step"] / kt["launches_per_step"]
+    mm_launch = kt["mulmods_per_step"] / kt["launches_per_step"]
+    by_launch = kt["bytes_per_step"] / kt["launches_per_step"]
+    alu_peak = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / IMAD_PER_MULMOD   # mulmod/s
+    hbm_peak = peaks["hbm_gbs"] * 1e9
+    t_alu, t_hbm = mm_launch / alu_peak, by_launch / hbm_peak
+    if t_alu >= t_hbm:
+        ach = mm_launch / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tmulmod/s",
+                "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": top,
+                "peak_source": "derived: %d SMs x %d IMAD/clk x %.0f MHz / %d IMAD per mulmod"
+                               % (SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD)}
+    else:
+        ach = by_launch / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": top,
+                "peak_source": "%s hbm_gbs" % peak_kind}
+    roof["mulmod_rate_measured_T"] = ctx.mulmod_rate(0) / 1e12
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        sample = 8 if args.config == "c3" else 10 ** 9
+        smp = OracleSample(A, x, ring, sample)
+        dt, n_total = smp.run(), smp.n_total
+        n_s = len(smp.chunks)
+        v = 1.0 / (dt * n_total / n_s)
+        cpu = {"value": v, "unit": "SpMV/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle cloud evaluation of %d of %d chunks (%.1f s), scaled to one "
+                         "SpMV" % (n_s, n_total, dt)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "SpMV/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": CONFIGS[args.config], "chunks": m.n_chunks,
+                   "partitions": m.n_parts, "rotations": m.n_rot,
+                   "keyswitches": n_ks,
+                   "l2": "inputs %.0f MB per step > 129 MB L2 (no flush)"
+                         % (2 * m.n_chunks * ct_words * 8 / 1e6),
+                   "parallelism": "independent SpMV per GPU"},
+        "nnz_per_s": value * A.nnz,
+        "correct": bool(correct),
+        "e2e": e2e,
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,9 +120,10 @@ int hespmv_ctx_device_bytes(const hespmv_ctx *ctx, size_t *bytes);
 
 /* Generate the secret key, public key, relinearisation key and the Galois
  * keys from `seed` (Section 5: one relinearisation key set plus rotation
- * keys).  rot_steps lists left-rotation amounts (NULL/0 with POW2: every
- * power of two below N/2).  Randomness: SplitMix64 streams derived from
- * seed.  Synchronous. */
+ * keys).  rot_steps lists the left-rotation amounts to support (n_steps
+ * entries; n_steps = 0 generates no Galois key); rot_steps = NULL with the
+ * POW2 policy generates every power of two below N/2.  Randomness:
+ * SplitMix64 streams derived from seed.  Synchronous. */
 int hespmv_keygen(hespmv_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps);
 
 /* Copy a key to host memory (layouts at HESPMV_KEY_*); n_words must be the
@@ -262,6 +263,26 @@ int hespmv_he_cmult_mask(hespmv_ctx *ctx, const uint64_t *ct, int32_t r, uint64_
  * (galois_elt = 0) or the Galois key of galois_elt: out [n][2][L][N]. */
 int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, uint64_t *out,
                      size_t n, void *stream);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Per-kernel device time.  While enabled, each kernel launch of the library
+ * is bracketed by two CUDA events recorded on its stream (enabling clears
+ * earlier records; the events add host work per launch, not device work). */
+int hespmv_profile_enable(hespmv_ctx *ctx, int32_t enable);
+/* Synchronise the device, fold the recorded events into per-kernel totals
+ * and return in *n the number of distinct kernels seen since enabling. */
+int hespmv_profile_count(hespmv_ctx *ctx, int32_t *n);
+/* Kernel i < *n of hespmv_profile_count: its name (valid until the next
+ * enable), launches and summed device milliseconds. */
+int hespmv_profile_entry(hespmv_ctx *ctx, int32_t i, const char **name, int64_t *launches,
+                         double *ms);
+/* Issue rate of 64-bit modular multiplications on the context's device
+ * (per second), measured by a microbenchmark of independent dependency
+ * chains: kind 0 multiplies by a constant with a precomputed quotient
+ * (Shoup), kind 1 multiplies two variable operands (Barrett).  Synchronous;
+ * allocates its own small buffer with cudaMalloc. */
+int hespmv_mulmod_rate(hespmv_ctx *ctx, int32_t kind, double *per_second);
 
 #ifdef __cplusplus
 }

@@ -116,8 +116,8 @@ class Context:
         if rot_steps is None:
             self.check(self.lib.hespmv_keygen(self.h, c_uint64(seed), None, 0))
         else:
-            a = np.ascontiguousarray(rot_steps, dtype=np.int32)
-            self.check(self.lib.hespmv_keygen(self.h, c_uint64(seed), _i32p(a), len(a)))
+            a = np.ascontiguousarray(list(rot_steps) + [0], dtype=np.int32)   # never NULL
+            self.check(self.lib.hespmv_keygen(self.h, c_uint64(seed), _i32p(a), len(a) - 1))
 
     def key_export(self, which, galois=0):
         N, L, LK = self.N, self.L, self.L + self.K
@@ -170,6 +170,28 @@ class Context:
         out = np.zeros(self.N, dtype=np.uint64)
         self.check(self.lib.hespmv_decrypt_slots(self.h, b.h, index, _u64p(out)))
         return out
+
+    # ---- measurement ----
+    def profile_enable(self, on=True):
+        self.check(self.lib.hespmv_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel name: (launches, device ms)} since profile_enable (synchronises)."""
+        n = c_int32()
+        self.check(self.lib.hespmv_profile_count(self.h, byref(n)))
+        out = {}
+        for i in range(n.value):
+            name = ctypes.c_char_p()
+            cnt = c_int64()
+            ms = ctypes.c_double()
+            self.check(self.lib.hespmv_profile_entry(self.h, i, byref(name), byref(cnt), byref(ms)))
+            out[name.value.decode()] = (cnt.value, ms.value)
+        return out
+
+    def mulmod_rate(self, kind=0):
+        r = ctypes.c_double()
+        self.check(self.lib.hespmv_mulmod_rate(self.h, kind, byref(r)))
+        return r.value
 
     # ---- primitives on device pointers (ints) ----
     def ntt(self, ptr, prime0, n_limbs, n_items=1, inverse=False, stream=None):

@@ -87,6 +87,11 @@ SIGNATURES = {
     "hespmv_he_rotate": (c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "hespmv_he_cmult_mask": (c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "hespmv_keyswitch": (c_int, [c_void_p, c_void_p, c_uint32, c_void_p, c_size_t, c_void_p]),
+    "hespmv_profile_enable": (c_int, [c_void_p, c_int32]),
+    "hespmv_profile_count": (c_int, [c_void_p, i32p]),
+    "hespmv_profile_entry": (c_int, [c_void_p, c_int32, POINTER(c_char_p), i64p,
+                                     POINTER(ctypes.c_double)]),
+    "hespmv_mulmod_rate": (c_int, [c_void_p, c_int32, POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -102,10 +107,10 @@ def load(build_if_missing=True):
     if _lib is not None:
         return _lib
     path = _build.LIB
-    if not os.path.exists(path):
-        if not build_if_missing:
-            raise RuntimeError("hespmv library not built: %s" % path)
-        _build.build()
+    if build_if_missing:
+        _build.build()   # incremental: only stale translation units recompile
+    elif not os.path.exists(path):
+        raise RuntimeError("hespmv library not built: %s" % path)
     lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -119,7 +119,7 @@ cudaError_t keyswitch_n(const Ctx &c, const uint64_t *d, int64_t d_stride, const
     uint64_t *acc = ext + n * c.dnum * LK * N;
     uint64_t *delta = acc + n * 2 * LK * N;
     cudaError_t e;
-    if ((e = op_copy_strided(d, d_stride, dcoef, L * N, L * N, n, st))) return e;
+    if ((e = op_copy_strided(c, d, d_stride, dcoef, L * N, L * N, n, st))) return e;
     if ((e = launch_ntt(c, dcoef, 0, (int)L, (int)n, L * N, true, st))) return e;
     if ((e = op_modup(c, dcoef, ext, n, st))) return e;
     if ((e = launch_ntt(c, ext, 0, (int)LK, (int)(n * c.dnum), LK * N, false, st))) return e;
@@ -405,6 +405,7 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     for (auto &a : ctx->allocs) dev_free(ctx, a.first);
     dev_free(ctx, ctx->ws);
     dev_free(ctx, ctx->io);
+    delete ctx->prof;
     delete ctx;
 }
 
@@ -468,7 +469,7 @@ int hespmv_keygen(hespmv_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size
         // Galois keys
         std::set<uint32_t> elts;
         const int64_t half = N / 2;
-        if (rot_steps == nullptr || n_steps == 0) {
+        if (rot_steps == nullptr) {
             if (ctx->p.rot_policy == HESPMV_ROT_POW2)
                 for (int64_t b = 1; b < half; b <<= 1) elts.insert(pow5((uint64_t)b, 2 * N));
         } else {
@@ -954,6 +955,49 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
     uint64_t *ws = workspace(ctx, ks_words(c, n) * 8);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     CK(keyswitch_n(c, d, LN, key, out, nullptr, 0, 0, 0, n, ws, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
+
+int hespmv_profile_enable(hespmv_ctx *ctx, int32_t enable) {
+    if (!ctx) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    if (!ctx->prof) ctx->prof = new Profiler();
+    if (enable) {
+        cudaDeviceSynchronize();
+        ctx->prof->reset();
+    }
+    ctx->prof->on = enable != 0;
+    return HESPMV_OK;
+}
+
+int hespmv_profile_count(hespmv_ctx *ctx, int32_t *n) {
+    if (!ctx || !n) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    if (!ctx->prof) {
+        *n = 0;
+        return HESPMV_OK;
+    }
+    CK(ctx->prof->collect());
+    *n = (int32_t)ctx->prof->names.size();
+    return HESPMV_OK;
+}
+
+int hespmv_profile_entry(hespmv_ctx *ctx, int32_t i, const char **name, int64_t *launches,
+                         double *ms) {
+    if (!ctx || !ctx->prof || i < 0 || i >= (int32_t)ctx->prof->launches.size()) return HESPMV_E_INVALID;
+    if (name) *name = ctx->prof->names[i].c_str();
+    if (launches) *launches = ctx->prof->launches[i];
+    if (ms) *ms = ctx->prof->ms[i];
+    return HESPMV_OK;
+}
+
+int hespmv_mulmod_rate(hespmv_ctx *ctx, int32_t kind, double *per_second) {
+    if (!ctx || !per_second || (kind != 0 && kind != 1)) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(mulmod_rate(ctx->h, kind, per_second));
     return HESPMV_OK;
 }
 

@@ -99,8 +99,32 @@ std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *r
 void total_sum_steps(int32_t r, int32_t c, std::vector<int32_t> &steps,
                      std::vector<uint8_t> &from_original);
 
+// ------------------------------------------------------------ profiling
+// While enabled, each kernel launch is bracketed by two CUDA events recorded
+// on the launch stream; collect() sums the elapsed times per kernel name.
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<Rec> recs;
+    std::vector<std::string> names;
+    std::map<std::string, int> ids;
+    std::vector<int64_t> launches;
+    std::vector<double> ms;
+    cudaError_t collect();
+    void reset();
+    ~Profiler();
+};
+
 // ------------------------------------------------------------ kernels (host launchers)
 struct Ctx;
+int prof_begin(const Ctx &c, const char *name, cudaStream_t st);
+cudaError_t mulmod_rate(const HostTables &h, int kind, double *rate);
+void prof_end(const Ctx &c, int rec, cudaStream_t st);
 // NTT of n_items x n_limbs polynomials, item stride in words; limb k uses prime0 + k.
 cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, int n_items,
                        int64_t item_stride, bool inverse, cudaStream_t st);
@@ -127,6 +151,7 @@ struct hespmv_ctx {
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    hespmv::Profiler *prof = nullptr;
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;

@@ -23,7 +23,7 @@ cudaError_t op_permute(const Ctx &c, const uint64_t *in, uint64_t *out, const in
 cudaError_t op_mul_limbs(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
                          int prime0, int n_limbs, size_t n_items, cudaStream_t st);
 // copy n_items strided blocks of `words` words
-cudaError_t op_copy_strided(const uint64_t *src, int64_t src_stride, uint64_t *dst,
+cudaError_t op_copy_strided(const Ctx &c, const uint64_t *src, int64_t src_stride, uint64_t *dst,
                             int64_t dst_stride, int64_t words, size_t n_items, cudaStream_t st);
 
 // key switching pieces, n items

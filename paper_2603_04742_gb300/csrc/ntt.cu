@@ -211,10 +211,12 @@ cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, in
         dim3 grid(1, total);
         const int thr = std::min(256, N / 2);
         const size_t smem = (size_t)N * 8;
+        const int r = prof_begin(c, inverse ? "k_ntt_inv_rows" : "k_ntt_fwd_rows", st);
         if (inverse)
             k_ntt_inv_rows<<<grid, thr, smem, st>>>(a, 0, 1);
         else
             k_ntt_fwd_rows<<<grid, thr, smem, st>>>(a, 0, 1);
+        prof_end(c, r, st);
         return cudaGetLastError();
     }
     const int n1 = c.log2n / 2;
@@ -222,12 +224,21 @@ cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, in
     const int TC = std::max(1, 2048 / R), TR = std::max(1, 2048 / C);
     const size_t smc = (size_t)R * TC * 8, smr = (size_t)TR * C * 8;
     dim3 gc(C / TC, total), gr(R / TR, total);
+    int r;
     if (!inverse) {
+        r = prof_begin(c, "k_ntt_fwd_cols", st);
         k_ntt_fwd_cols<<<gc, 256, smc, st>>>(a, n1, TC);
+        prof_end(c, r, st);
+        r = prof_begin(c, "k_ntt_fwd_rows", st);
         k_ntt_fwd_rows<<<gr, 256, smr, st>>>(a, n1, TR);
+        prof_end(c, r, st);
     } else {
+        r = prof_begin(c, "k_ntt_inv_rows", st);
         k_ntt_inv_rows<<<gr, 256, smr, st>>>(a, n1, TR);
+        prof_end(c, r, st);
+        r = prof_begin(c, "k_ntt_inv_cols", st);
         k_ntt_inv_cols<<<gc, 256, smc, st>>>(a, n1, TC);
+        prof_end(c, r, st);
     }
     return cudaGetLastError();
 }

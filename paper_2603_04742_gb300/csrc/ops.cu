@@ -342,7 +342,11 @@ __global__ void k_gather_slots(const uint64_t *E, uint64_t *slots, int N, const 
 #define LAUNCH(kern, total, st, ...)                                  \
     do {                                                              \
         const int64_t _t = (total);                                   \
-        if (_t > 0) kern<<<grid_for(_t), kThreads, 0, st>>>(__VA_ARGS__); \
+        if (_t > 0) {                                                 \
+            const int _r = prof_begin(c, #kern, st);                  \
+            kern<<<grid_for(_t), kThreads, 0, st>>>(__VA_ARGS__);     \
+            prof_end(c, _r, st);                                      \
+        }                                                             \
         return cudaGetLastError();                                    \
     } while (0)
 
@@ -382,7 +386,7 @@ cudaError_t op_mul_limbs(const Ctx &c, const uint64_t *a, const uint64_t *b, uin
     LAUNCH(k_mul_limbs, total, st, a, b, out, total, c.log2n, prime0, n_limbs, c.c->d.mc);
 }
 
-cudaError_t op_copy_strided(const uint64_t *src, int64_t src_stride, uint64_t *dst,
+cudaError_t op_copy_strided(const Ctx &c, const uint64_t *src, int64_t src_stride, uint64_t *dst,
                             int64_t dst_stride, int64_t words, size_t n_items, cudaStream_t st) {
     const int64_t total = words * (int64_t)n_items;
     LAUNCH(k_copy_strided, total, st, src, src_stride, dst, dst_stride, words, total);
