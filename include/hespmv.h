@@ -264,6 +264,28 @@ int hespmv_he_cmult_mask(hespmv_ctx *ctx, const uint64_t *ct, int32_t r, uint64_
 int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, uint64_t *out,
                      size_t n, void *stream);
 
+/* Key switch that allocates no device memory.  The paper has no counterpart:
+ * this is a deployment aid.  Same arguments and result as hespmv_keyswitch,
+ * but the scratch comes from one fixed 32 MiB array in device memory that the
+ * library reserves on every GPU where it is loaded (held until the process
+ * exits), instead of from the context's workspace.  It is for callers that
+ * must not allocate device memory where they call it: code that runs while
+ * another allocator owns the device's free memory (a framework pool that has
+ * reserved it), and latency-sensitive loops that cannot pay for
+ * cudaMalloc/cudaFree, which may synchronise the device.
+ *  - Limit: n ciphertexts need n * 8*N*(L + dnum*(L+K) + 2*(L+K) + 2*L) bytes
+ *    of scratch (about 21 MiB each at N = 2^15, L = 8, K = 2, dnum = 4);
+ *    beyond 32 MiB the call fails with HESPMV_E_INVALID and says how many fit.
+ *  - The first call on a device sets it up: it looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current.  Make that first
+ *    call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    nothing in it has to start at zero (each stage writes the scratch it
+ *    reads).  Calls that overlap on the GPU (several streams or threads) race
+ *    on the array: serialise them. */
+int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt,
+                             uint64_t *out, size_t n, void *stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Per-kernel device time.  While enabled, each kernel launch of the library

@@ -87,6 +87,8 @@ SIGNATURES = {
     "hespmv_he_rotate": (c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "hespmv_he_cmult_mask": (c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "hespmv_keyswitch": (c_int, [c_void_p, c_void_p, c_uint32, c_void_p, c_size_t, c_void_p]),
+    "hespmv_keyswitch_noalloc": (c_int, [c_void_p, c_void_p, c_uint32, c_void_p, c_size_t,
+                                         c_void_p]),
     "hespmv_profile_enable": (c_int, [c_void_p, c_int32]),
     "hespmv_profile_count": (c_int, [c_void_p, i32p]),
     "hespmv_profile_entry": (c_int, [c_void_p, c_int32, POINTER(c_char_p), i64p,

@@ -3,6 +3,7 @@
 // and 4, decryption, and the HE primitives.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <set>
 
 #include "kernels.h"
@@ -1002,3 +1003,78 @@ int hespmv_mulmod_rate(hespmv_ctx *ctx, int32_t kind, double *per_second) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Key switching without device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need a key
+// switch: code that runs while another allocator owns the device's free
+// memory (a framework pool that has reserved it), or a latency-sensitive loop
+// that cannot pay for cudaMalloc/cudaFree, which may synchronise the device.
+// hespmv_keyswitch_noalloc runs the same pipeline as hespmv_keyswitch but
+// takes its scratch from the fixed array below, which the library reserves on
+// every GPU where it is loaded and holds until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;  // 32 MiB
+constexpr size_t kNoAllocScratchWords = kNoAllocScratchBytes / 8;
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the array on `dev` (which must be current); looked up
+// once per device.  Host code cannot use the symbol itself: on the host it
+// names a stand-in, not the device memory.
+uint64_t *noalloc_scratch(int dev, std::string &err) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        err = "device ordinal out of range for the reserved scratch table";
+        return nullptr;
+    }
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        g_noalloc_addr[dev] = (uint64_t *)p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+}  // namespace
+
+extern "C" int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt,
+                                        uint64_t *out, size_t n, void *stream) {
+    if (!ctx || !d || !out) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    DeviceGuard g(ctx->device);
+    const uint64_t *key = ctx->rlk;
+    if (galois_elt) {
+        auto it = ctx->gk.find(galois_elt);
+        if (it == ctx->gk.end()) FAIL(HESPMV_E_INVALID, "no Galois key for that element");
+        key = it->second;
+    }
+    const Ctx c = view(ctx);
+    const size_t per = ks_words(c, 1);
+    if (n == 0) return HESPMV_OK;
+    if (ks_words(c, n) > kNoAllocScratchWords)
+        FAIL(HESPMV_E_INVALID, "hespmv_keyswitch_noalloc: " + std::to_string(n) +
+                                   " ciphertexts need " + std::to_string(ks_words(c, n) * 8) +
+                                   " bytes of scratch, more than the reserved " +
+                                   std::to_string(kNoAllocScratchBytes) + "; at most " +
+                                   std::to_string(kNoAllocScratchWords / per) +
+                                   " per call with these parameters");
+    std::string err;
+    uint64_t *scratch = noalloc_scratch(ctx->device, err);
+    if (!scratch) FAIL(HESPMV_E_CUDA, err);
+    // every stage writes the scratch words it later reads, so nothing in the
+    // shared array has to start at zero
+    const int64_t LN = (int64_t)c.L * c.N;
+    CK(keyswitch_n(c, d, LN, key, out, nullptr, 0, 0, 0, n, scratch, (cudaStream_t)stream));
+    return HESPMV_OK;
+}
