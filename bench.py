@@ -123,32 +123,39 @@ def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot):
     """Algorithmic work of one step in kernel `name`: (mulmods, bytes).
 
     n_ks = key switches per step (relinearisations + elementary rotations).
-    Bytes: one read of every input and one write of every output."""
+    Mulmods count every modular product (NTT butterflies, base conversions,
+    key products, masks); bytes count one read of every input and one write
+    of every output of the kernel (a key is read once per step)."""
     logn, L, K, dnum = ring[:4]
     N = 1 << logn
     LK = L + K
     alpha = -(-L // dnum)
-    n1 = logn // 2 if logn > 12 else 0
+    n1 = logn // 2 if logn > 10 else 0
     n2 = logn - n1
     w = 8 * N  # bytes per limb
-    fwd_limbs = n_ks * (dnum * LK - L + 2 * L)
-    inv_limbs = n_ks * (L + 2 * K)
-    half = N // 2
+    h = N // 2
+    ext = dnum * LK - L          # limbs raised by ModUp (each digit's own limbs excluded)
     m = {
-        "k_ntt_fwd_cols": (fwd_limbs * half * n1, fwd_limbs * 2 * w),
-        "k_ntt_fwd_rows": (fwd_limbs * half * n2, fwd_limbs * 2 * w),
-        "k_ntt_inv_rows": (inv_limbs * half * n2, inv_limbs * 2 * w),
-        "k_ntt_inv_cols": (inv_limbs * half * n1, inv_limbs * 2 * w),
+        # fused key switch (one launch of each per step and batch group)
+        "k_ks_intt_rows": (n_ks * (L + 2 * K) * h * n2, n_ks * (L + 2 * K) * 2 * w),
+        "k_ks_intt_cols": (n_ks * (L + 2 * K) * (h * n1 + N), n_ks * (L + 2 * K) * 2 * w),
+        "k_ks_modup_cols": (n_ks * ext * (h * n1 + alpha * N), n_ks * (L + ext) * w),
+        "k_ks_rows_inner": (n_ks * (ext * h * n2 + 2 * dnum * LK * N),
+                            n_ks * (ext + L + 2 * LK) * w + 2 * dnum * LK * w),
+        "k_ks_moddown_cols": (n_ks * 2 * L * (h * n1 + K * N), n_ks * 2 * (K + L) * w),
+        "k_ks_rows_final": (n_ks * 2 * L * (h * n2 + N), n_ks * 2 * L * 4 * w),
+        # ciphertext arithmetic
+        "k_tensor": (n_chunks * 4 * L * N, n_chunks * 7 * L * w),
+        "k_mask_acc": (n_chunks * 2 * L * N, n_chunks * 2 * L * w + n_parts * 2 * L * w),
+        "k_copy_strided": (0, n_ks * 2 * L * w),
+        "k_permute": (0, n_ks * 2 * 2 * L * w),
+        "k_add": (0, n_rot * 3 * 2 * L * w),
+        # unfused key switch (small rings)
         "k_modup": (n_ks * dnum * alpha * (1 + LK - alpha) * N,
                     n_ks * (L + dnum * (LK - alpha)) * w),
         "k_inner": (n_ks * 2 * dnum * LK * N, n_ks * (dnum * LK + 2 * LK) * w + 2 * dnum * LK * w),
         "k_moddown_delta": (n_ks * 2 * (K + K * L + L) * N, n_ks * 2 * (K + L) * w),
         "k_moddown_final": (n_ks * 2 * L * N, n_ks * 2 * L * 3 * w),
-        "k_tensor": (n_chunks * 4 * L * N, n_chunks * 7 * L * w),
-        "k_cmult_acc": (n_chunks * 2 * L * N, n_chunks * 2 * L * 3 * w),
-        "k_copy_strided": (0, n_ks * 2 * L * w),
-        "k_permute": (0, 2 * n_ks * 2 * L * w),
-        "k_add": (0, n_rot * 3 * 2 * L * w),
     }
     return m.get(name, (0, 0))
 

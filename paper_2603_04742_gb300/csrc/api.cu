@@ -114,6 +114,9 @@ size_t ks_words(const Ctx &c, size_t n) {
 cudaError_t keyswitch_n(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                         uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                         int add_mask, size_t n, uint64_t *scratch, cudaStream_t st) {
+    if (ks_fused_supported(c))
+        return keyswitch_fused(c, d, d_stride, key, out, add, add_is, add_cs, add_mask, n, scratch,
+                               st);
     const int64_t N = c.N, L = c.L, LK = c.L + c.K;
     uint64_t *dcoef = scratch;
     uint64_t *ext = dcoef + n * L * N;
@@ -184,6 +187,9 @@ int make_ksk(hespmv_ctx *ctx, uint64_t seed, uint64_t kid, const uint64_t *sp, u
         CK(launch_ntt(c, tmp_e, 0, (int)LK, 1, LKN, false, 0));
         CK(op_ksk_combine(c, a, tmp_e, ctx->sk, sp, j, b, 0));
     }
+    // keys are kept in Montgomery form (key * 2^64 mod q): the inner product
+    // then needs one reduction per sum of products
+    CK(op_to_mont(c, out, 2 * c.dnum, 0));
     return HESPMV_OK;
 }
 
@@ -209,6 +215,8 @@ const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
     ok = ok && launch_ntt(c, E, c.L + c.K, 1, 1, N, true, st) == cudaSuccess;
     ok = ok && op_lift(c, E, m, 1, st) == cudaSuccess;
     ok = ok && launch_ntt(c, m, 0, c.L, 1, (int64_t)c.L * N, false, st) == cudaSuccess;
+    // Montgomery form: mask products then need one reduction per sum
+    ok = ok && op_to_mont_limbs(c, m, 0, c.L, 1, st) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
     dev_free(ctx, tmp);
     if (!ok) return nullptr;
@@ -262,68 +270,225 @@ int rotate_n(hespmv_ctx *ctx, const uint64_t *src, int32_t k, uint64_t *out, siz
     return HESPMV_OK;
 }
 
+// Batched totalSum schedule for the given matrices (cached per matrix set).
+RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, int GR) {
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)GR);
+    for (size_t i = 0; i < n_inst; ++i) key.push_back(ms[i]->uid);
+    auto it = ctx->rot_plans.find(key);
+    if (it != ctx->rot_plans.end()) return it->second;
+    struct RC {
+        int32_t k;
+        std::vector<int32_t> steps;
+        std::vector<uint8_t> orig;
+    };
+    std::vector<RC> rcs;
+    int32_t k0 = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        for (const Chunk &ch : ms[i]->plan.chunks) {
+            RC r;
+            r.k = k0++;
+            total_sum_steps(ch.h, ch.c, r.steps, r.orig);
+            if (!r.steps.empty()) rcs.push_back(std::move(r));
+        }
+    }
+    RotPlan *P = new RotPlan();
+    P->GR = GR;
+    std::vector<int32_t> idx;
+    auto push = [&](const std::vector<int32_t> &v) {
+        const int64_t off = (int64_t)idx.size();
+        idx.insert(idx.end(), v.begin(), v.end());
+        return off;
+    };
+    const bool exact = ctx->p.rot_policy == HESPMV_ROT_EXACT;
+    const uint64_t twoN = 2 * (uint64_t)ctx->h.N;
+    for (size_t g0 = 0; g0 < rcs.size(); g0 += GR) {
+        const size_t gn = std::min<size_t>(GR, rcs.size() - g0);
+        std::vector<int32_t> gk(gn);
+        size_t maxr = 0;
+        for (size_t g = 0; g < gn; ++g) {
+            gk[g] = rcs[g0 + g].k;
+            maxr = std::max(maxr, rcs[g0 + g].steps.size());
+        }
+        RotOp v;
+        v.kind = RotOp::kVInit;
+        v.m = (int)gn;
+        v.b = push(gk);
+        P->ops.push_back(v);
+        for (size_t r = 0; r < maxr; ++r) {
+            std::vector<int32_t> pg, pk, vg;  // from prod (group id, chunk id), from V
+            std::vector<int32_t> act, actk;
+            for (size_t g = 0; g < gn; ++g) {
+                const RC &c = rcs[g0 + g];
+                if (r >= c.steps.size()) continue;
+                act.push_back((int32_t)g);
+                actk.push_back(c.k);
+                if (c.orig[r])
+                    vg.push_back((int32_t)g);
+                else {
+                    pg.push_back((int32_t)g);
+                    pk.push_back(c.k);
+                }
+            }
+            if (!pg.empty()) {
+                RotOp o;
+                o.kind = RotOp::kCurFromProd;
+                o.m = (int)pg.size();
+                o.a = push(pg);
+                o.b = push(pk);
+                P->ops.push_back(o);
+            }
+            if (!vg.empty()) {
+                RotOp o;
+                o.kind = RotOp::kCurFromV;
+                o.m = (int)vg.size();
+                o.a = push(vg);
+                o.b = o.a;
+                P->ops.push_back(o);
+            }
+            if (exact) {
+                std::map<int32_t, std::vector<int32_t>> by_amount;
+                for (size_t s = 0; s < act.size(); ++s)
+                    by_amount[rcs[g0 + act[s]].steps[r]].push_back(act[s]);
+                for (auto &kv : by_amount) {
+                    RotOp o;
+                    o.kind = RotOp::kElem;
+                    o.g = rotation_chain(ctx, kv.first).at(0);
+                    o.m = (int)kv.second.size();
+                    o.a = push(kv.second);
+                    P->ops.push_back(o);
+                }
+            } else {
+                for (int b = 0; b < 31; ++b) {
+                    std::vector<int32_t> S;
+                    for (int32_t g : act)
+                        if ((rcs[g0 + g].steps[r] >> b) & 1) S.push_back(g);
+                    if (S.empty()) continue;
+                    RotOp o;
+                    o.kind = RotOp::kElem;
+                    o.g = pow5(1ull << b, twoN);
+                    o.m = (int)S.size();
+                    o.a = push(S);
+                    P->ops.push_back(o);
+                }
+            }
+            RotOp o;
+            o.kind = RotOp::kAdd;
+            o.m = (int)act.size();
+            o.a = push(actk);
+            o.b = push(act);
+            P->ops.push_back(o);
+        }
+    }
+    if (!idx.empty()) {
+        P->idx_bytes = idx.size() * sizeof(int32_t);
+        P->d_idx = (int32_t *)dev_alloc(ctx, P->idx_bytes);
+        if (!P->d_idx || cudaMemcpy(P->d_idx, idx.data(), P->idx_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            dev_free(ctx, P->d_idx);
+            delete P;
+            return nullptr;
+        }
+    }
+    ctx->rot_plans[key] = P;
+    return P;
+}
+
 // Cloud evaluation of one or more SpMVs (Algorithm 1 cloud lines + Algorithm 4).
 int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
               cudaStream_t st) {
     const Ctx c = view(ctx);
     const int64_t N = c.N, LN = (int64_t)c.L * N, CT = 2 * LN;
-    size_t total_chunks = 0;
-    for (size_t i = 0; i < n_inst; ++i) total_chunks += ms[i]->plan.chunks.size();
-    // masks first (synchronous, cached)
-    for (size_t i = 0; i < n_inst; ++i)
-        for (const Chunk &ch : ms[i]->plan.chunks)
-            if (!mask_plaintext(ctx, ch.h, st)) FAIL(HESPMV_E_NOMEM, "mask plaintext creation failed");
-    // group size of the batched HE-Mult
-    const size_t G = std::max<size_t>(1, std::min<size_t>(total_chunks, 32));
-    const size_t prod_w = total_chunks * CT;
-    const size_t d_w = G * 3 * LN;
-    const size_t ks_w = ks_words(c, G);
-    const size_t rot_w = 2 * CT + 3 * CT + ks_words(c, 1);  // V copy, tmp, rotation scratch
-    const size_t need = (prod_w + d_w + std::max(ks_w, rot_w)) * 8;
-    uint64_t *ws = workspace(ctx, need);
-    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
-    uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + d_w;
-    // 1) HE-Mult of every chunk pair, G at a time
-    std::vector<std::pair<const uint64_t *, const uint64_t *>> pairs;
-    pairs.reserve(total_chunks);
-    for (size_t i = 0; i < n_inst; ++i)
-        for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k)
-            pairs.push_back({A[i] + k * CT, X[i] + k * CT});
-    size_t k0 = 0;
-    for (size_t i = 0; i < n_inst; ++i) {
-        const size_t nk = ms[i]->plan.chunks.size();
-        // contiguous runs within one instance are batched together
-        for (size_t k = 0; k < nk; k += G) {
-            const size_t g = std::min(G, nk - k);
-            CK(op_tensor(c, A[i] + k * CT, X[i] + k * CT, dbuf, g, st));
-            CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + (k0 + k) * CT, dbuf, 3 * LN,
-                           LN, 3, g, scr, st));
-        }
-        k0 += nk;
-    }
-    // 2) totalSum per chunk
-    uint64_t *Vc = scr, *tmp = Vc + CT, *rs = tmp + CT;
+    size_t total_chunks = 0, rot_chunks = 0;
     std::vector<int32_t> steps;
     std::vector<uint8_t> orig;
-    k0 = 0;
     for (size_t i = 0; i < n_inst; ++i) {
-        for (const Chunk &ch : ms[i]->plan.chunks) {
-            uint64_t *w = prod + k0 * CT;
-            total_sum_steps(ch.h, ch.c, steps, orig);
-            if (!steps.empty()) {
-                CK(cudaMemcpyAsync(Vc, w, CT * 8, cudaMemcpyDeviceToDevice, st));
-                for (size_t s = 0; s < steps.size(); ++s) {
-                    int rc = rotate_n(ctx, orig[s] ? Vc : w, steps[s], tmp, 1, rs, st);
-                    if (rc) return rc;
-                    CK(op_add(c, w, tmp, w, 2, st));
-                }
+        total_chunks += ms[i]->plan.chunks.size();
+        for (const Chunk &ch : ms[i]->plan.chunks) rot_chunks += ch.c > 1;
+    }
+    // masks first (synchronous, cached), and each matrix's per-chunk mask table
+    for (size_t i = 0; i < n_inst; ++i) {
+        hespmv_cssc *m = const_cast<hespmv_cssc *>(ms[i]);
+        for (const Chunk &ch : m->plan.chunks)
+            if (!mask_plaintext(ctx, ch.h, st)) FAIL(HESPMV_E_NOMEM, "mask plaintext creation failed");
+        if (!m->d_masks && !m->plan.chunks.empty()) {
+            std::vector<const uint64_t *> tab;
+            for (const Chunk &ch : m->plan.chunks) tab.push_back(ctx->masks[ch.h]);
+            m->d_masks = (const uint64_t **)dev_alloc(ctx, tab.size() * sizeof(void *));
+            if (!m->d_masks) FAIL(HESPMV_E_NOMEM, "mask table allocation failed");
+            CK(cudaMemcpy(m->d_masks, tab.data(), tab.size() * sizeof(void *), cudaMemcpyHostToDevice));
+        }
+    }
+    // batch sizes: HE-Mult groups of G chunks, rotation groups of GR chunks
+    const size_t G = std::max<size_t>(1, std::min<size_t>(total_chunks, 32));
+    const size_t GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, N >= (1 << 15) ? 32 : 64));
+    RotPlan *rp = nullptr;
+    if (rot_chunks) {
+        rp = rotation_plan(ctx, n_inst, ms, (int)GR);
+        if (!rp) FAIL(HESPMV_E_NOMEM, "rotation schedule upload failed");
+    }
+    const size_t prod_w = total_chunks * CT;
+    const size_t mult_w = G * 3 * LN + ks_words(c, G);
+    const size_t rot_w = rot_chunks ? 4 * GR * CT + ks_words(c, GR) : 0;
+    const size_t need = (prod_w + std::max(mult_w, rot_w)) * 8;
+    uint64_t *ws = workspace(ctx, need);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + G * 3 * LN;
+    // 1) HE-Mult of every chunk pair, G at a time across instances
+    {
+        std::vector<std::pair<size_t, size_t>> all;  // (instance, chunk)
+        all.reserve(total_chunks);
+        for (size_t i = 0; i < n_inst; ++i)
+            for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
+        for (size_t g0 = 0; g0 < all.size(); g0 += G) {
+            const size_t gn = std::min(G, all.size() - g0);
+            size_t s = 0;
+            while (s < gn) {  // tensor over runs of one instance's consecutive chunks
+                const size_t i = all[g0 + s].first, k = all[g0 + s].second;
+                size_t run = 1;
+                while (s + run < gn && all[g0 + s + run].first == i) ++run;
+                CK(op_tensor(c, A[i] + k * CT, X[i] + k * CT, dbuf + s * 3 * LN, run, st));
+                s += run;
             }
-            ++k0;
+            CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + g0 * CT, dbuf, 3 * LN, LN, 3,
+                           gn, scr, st));
+        }
+    }
+    // 2) totalSum: batched rotation rounds
+    if (rp) {
+        uint64_t *V = dbuf, *CUR = V + GR * CT, *PB = CUR + GR * CT, *OB = PB + GR * CT;
+        uint64_t *ks = OB + GR * CT;
+        const int32_t *I = rp->d_idx;
+        for (const RotOp &o : rp->ops) {
+            switch (o.kind) {
+                case RotOp::kVInit:
+                    CK(op_ct_move(c, V, nullptr, prod, I + o.b, nullptr, false, o.m, st));
+                    break;
+                case RotOp::kCurFromProd:
+                    CK(op_ct_move(c, CUR, I + o.a, prod, I + o.b, nullptr, false, o.m, st));
+                    break;
+                case RotOp::kCurFromV:
+                    CK(op_ct_move(c, CUR, I + o.a, V, I + o.b, nullptr, false, o.m, st));
+                    break;
+                case RotOp::kElem: {
+                    auto it = ctx->gk.find(o.g);
+                    if (it == ctx->gk.end())
+                        FAIL(HESPMV_E_INVALID, "missing Galois key for element " + std::to_string(o.g));
+                    const int32_t *perm = galois_perm(ctx, o.g);
+                    if (!perm) FAIL(HESPMV_E_NOMEM, "permutation upload failed");
+                    CK(op_ct_move(c, PB, nullptr, CUR, I + o.a, perm, false, o.m, st));
+                    CK(keyswitch_n(c, PB + LN, CT, it->second, OB, PB, CT, LN, 1, o.m, ks, st));
+                    CK(op_ct_move(c, CUR, I + o.a, OB, nullptr, nullptr, false, o.m, st));
+                    break;
+                }
+                case RotOp::kAdd:
+                    CK(op_ct_move(c, prod, I + o.a, CUR, I + o.b, nullptr, true, o.m, st));
+                    break;
+            }
         }
     }
     // 3) masked accumulation per partition
-    k0 = 0;
+    size_t k0 = 0;
     for (size_t i = 0; i < n_inst; ++i) {
         const Plan &pl = ms[i]->plan;
         for (size_t p = 0; p < pl.parts.size(); ++p) {
@@ -333,10 +498,8 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                 CK(cudaMemsetAsync(res, 0, CT * 8, st));
                 continue;
             }
-            for (int k = 0; k < P.n_chunks; ++k) {
-                const Chunk &ch = pl.chunks[P.chunk0 + k];
-                CK(op_cmult_acc(c, res, prod + (k0 + P.chunk0 + k) * CT, ctx->masks[ch.h], k == 0, st));
-            }
+            CK(op_mask_acc(c, prod + (k0 + P.chunk0) * CT, ms[i]->d_masks + P.chunk0, P.n_chunks, res,
+                           st));
         }
         k0 += pl.chunks.size();
     }
@@ -385,7 +548,9 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
               upload(ctx, d.md_phat, h.md_phat) && upload(ctx, d.md_t, h.md_t) &&
               upload(ctx, d.md_pinv, h.md_pinv) && upload(ctx, d.p_mod_q, h.p_mod_q) &&
               upload(ctx, d.slot_idx, h.slot_idx) && upload(ctx, d.dec, h.dec) &&
-              upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod);
+              upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod) &&
+              upload(ctx, d.ks_zc, h.ks_zc) && upload(ctx, d.ks_yc, h.ks_yc) &&
+              upload(ctx, d.md_phat_t, h.md_phat_t);
     if (!ok) {
         ctx->err = "table upload failed";
         *out = ctx;
@@ -406,6 +571,10 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     for (auto &a : ctx->allocs) dev_free(ctx, a.first);
     dev_free(ctx, ctx->ws);
     dev_free(ctx, ctx->io);
+    for (auto &kv : ctx->rot_plans) {
+        dev_free(ctx, kv.second->d_idx);
+        delete kv.second;
+    }
     delete ctx->prof;
     delete ctx;
 }
@@ -526,6 +695,23 @@ int hespmv_key_export(hespmv_ctx *ctx, int32_t which, uint32_t galois_elt, uint6
     }
     if (n_words != words) FAIL(HESPMV_E_INVALID, "n_words does not match the key size");
     CK(cudaMemcpy(host_out, src, words * 8, cudaMemcpyDeviceToHost));
+    if (which == HESPMV_KEY_RELIN || which == HESPMV_KEY_GALOIS) {
+        // out of Montgomery form: x * 2^-64 mod q_l
+        typedef unsigned __int128 u128;
+        for (size_t l = 0; l < LK; ++l) {
+            const uint64_t q = ctx->h.q[l];
+            const uint64_t r = (uint64_t)(((u128)1 << 64) % q);
+            uint64_t rinv = 1, b = r, e = q - 2;  // r^(q-2) = r^-1
+            for (; e; e >>= 1) {
+                if (e & 1) rinv = (uint64_t)((u128)rinv * b % q);
+                b = (uint64_t)((u128)b * b % q);
+            }
+            for (size_t blk = 0; blk < words / (LK * N); ++blk) {
+                uint64_t *w = host_out + (blk * LK + l) * N;
+                for (size_t k = 0; k < N; ++k) w[k] = (uint64_t)((u128)w[k] * rinv % q);
+            }
+        }
+    }
     return HESPMV_OK;
 }
 
@@ -571,11 +757,20 @@ int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
         }
     }
     m->steps.assign(st.begin(), st.end());
+    m->uid = ctx->next_uid++;
     *out = m;
     return HESPMV_OK;
 }
 
-void hespmv_cssc_free(hespmv_cssc *m) { delete m; }
+void hespmv_cssc_free(hespmv_cssc *m) {
+    if (!m) return;
+    if (m->d_masks) {
+        DeviceGuard g(m->ctx->device);
+        cudaDeviceSynchronize();
+        dev_free(m->ctx, (void *)m->d_masks);
+    }
+    delete m;
+}
 
 int hespmv_cssc_info(const hespmv_cssc *m, int32_t *n_parts, int32_t *n_chunks, int64_t *n_rot,
                      int64_t *n_keyswitch, int32_t *rows, int32_t *cols, int64_t *nnz) {

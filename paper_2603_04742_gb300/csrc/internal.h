@@ -21,7 +21,7 @@ struct HostTables {
     std::vector<uint64_t> q;     // L + K + 1 moduli: Q, then P, then t
     std::vector<uint64_t> psi;   // primitive 2N-th roots (index L+K: zeta for t)
     std::vector<ModConst> mc;    // per modulus
-    // twiddles per modulus: [4][N] = psi_brv, psi_brv_shoup, ipsi_brv, ipsi_brv_shoup
+    // twiddles per modulus: [N][2] (psi^bitrev(k), Shoup) then [N][2] (psi^-bitrev(k), Shoup)
     std::vector<uint64_t> tw;
     // ModUp constants, per digit j, source prime i (local index), target l:
     //   qhat_inv[j][i] (Shoup pair) and qhat_mod[j][i][l] (Shoup pair)
@@ -42,6 +42,12 @@ struct HostTables {
     std::vector<uint64_t> dec;         // [L][4] + [2]
     std::vector<double> dec_inv_q;     // [L]
     std::vector<uint64_t> t_mod;       // t mod q_l, [L+K]
+    // fused key switching: inverse-NTT fold constants (c0, c0 Shoup, c1, c1
+    // Shoup) producing [x * Qhat^-1]_{q_i} (ks_zc, per Q prime) and
+    // [x * t^-1 * Phat_k^-1]_{p_k} (ks_yc, per P prime); Phat_k * t mod q_i
+    std::vector<uint64_t> ks_zc;       // [L][4]
+    std::vector<uint64_t> ks_yc;       // [K][4]
+    std::vector<uint64_t> md_phat_t;   // [K][L][2]
 };
 
 // Device copies of the tables.
@@ -59,6 +65,9 @@ struct DevTables {
     uint64_t *dec = nullptr;
     double *dec_inv_q = nullptr;
     uint64_t *t_mod = nullptr;
+    uint64_t *ks_zc = nullptr;
+    uint64_t *ks_yc = nullptr;
+    uint64_t *md_phat_t = nullptr;
 };
 
 bool build_tables(const hespmv_params &p, HostTables &h, std::string &err);
@@ -131,6 +140,25 @@ cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, in
 
 }  // namespace hespmv
 
+namespace hespmv {
+// Batched totalSum schedule of a set of matrices (Algorithm 4, rotations):
+// chunks that rotate are processed in groups; per round, every rotating
+// chunk's rotation runs as one batched key switch per Galois element, bits
+// in increasing order (each chunk's own chain stays least significant first).
+struct RotOp {
+    enum Kind { kVInit, kCurFromProd, kCurFromV, kElem, kAdd } kind;
+    uint32_t g = 0;         // Galois element (kElem)
+    int m = 0;              // items
+    int64_t a = -1, b = -1; // offsets of the index lists in d_idx (-1: identity)
+};
+struct RotPlan {
+    int GR = 0;             // group capacity
+    std::vector<RotOp> ops;
+    int32_t *d_idx = nullptr;
+    size_t idx_bytes = 0;
+};
+}  // namespace hespmv
+
 // The opaque handles of the C ABI.
 struct hespmv_ctx {
     hespmv_params p{};
@@ -152,6 +180,9 @@ struct hespmv_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     hespmv::Profiler *prof = nullptr;
+    // rotation schedules, keyed by the matrices' ids
+    std::map<std::vector<uint64_t>, hespmv::RotPlan *> rot_plans;
+    uint64_t next_uid = 1;
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;
@@ -162,6 +193,8 @@ struct hespmv_cssc {
     hespmv::Plan plan;
     std::vector<int32_t> steps;   // distinct rotation steps
     int64_t n_rot = 0, n_ks = 0;
+    const uint64_t **d_masks = nullptr;  // device: mask plaintext of each chunk
+    uint64_t uid = 0;                    // unique per context (schedule cache key)
 };
 
 struct hespmv_ctbatch {

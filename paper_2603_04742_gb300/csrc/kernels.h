@@ -10,12 +10,22 @@ cudaError_t op_add(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t 
                    cudaStream_t st);   // n_polys polynomials of L limbs
 cudaError_t op_tensor(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
                       cudaStream_t st);
-// out = ct * pt (pt [L][N] shared by all n ciphertexts)
+// out = ct * pt (pt [L][N] in Montgomery form, shared by all n ciphertexts)
 cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint64_t *out, size_t n,
                      cudaStream_t st);
 // acc (one ct) += w (one ct) * pt
 cudaError_t op_cmult_acc(const Ctx &c, uint64_t *acc, const uint64_t *w, const uint64_t *pt,
                          bool first, cudaStream_t st);
+// out = sum_k w_k * masks[k] for w_k = w0 + k ciphertexts (masks: Montgomery form)
+cudaError_t op_mask_acc(const Ctx &c, const uint64_t *w0, const uint64_t *const *masks,
+                        int nterms, uint64_t *out, cudaStream_t st);
+// dst[di[s]] (= or +=) src[si[s]], optionally through a Galois permutation,
+// for m whole ciphertexts; null index lists mean s
+cudaError_t op_ct_move(const Ctx &c, uint64_t *dst, const int32_t *di, const uint64_t *src,
+                       const int32_t *si, const int32_t *perm, bool add, int m, cudaStream_t st);
+// x <- x * 2^64 mod q over n_items x n_limbs limbs with moduli prime0..
+cudaError_t op_to_mont_limbs(const Ctx &c, uint64_t *x, int prime0, int n_limbs, size_t n_items,
+                             cudaStream_t st);
 // out[p][i] = in[p][perm[i]] for n_polys polynomials (limbs are polynomials here)
 cudaError_t op_permute(const Ctx &c, const uint64_t *in, uint64_t *out, const int32_t *perm,
                        size_t n_limbs_total, cudaStream_t st);
@@ -37,6 +47,14 @@ cudaError_t op_moddown_delta(const Ctx &c, const uint64_t *acc, uint64_t *delta,
 cudaError_t op_moddown_final(const Ctx &c, const uint64_t *acc, const uint64_t *delta,
                              const uint64_t *add, int64_t add_item_stride, int64_t add_comp_stride,
                              int add_mask, uint64_t *out, size_t n, cudaStream_t st);
+
+// fused hybrid key switch (ks.cu), keys in Montgomery form
+bool ks_fused_supported(const Ctx &c);
+cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
+                            uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
+                            int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);
+// x <- x * 2^64 mod q over n_items x (L+K) limbs (keys to Montgomery form)
+cudaError_t op_to_mont(const Ctx &c, uint64_t *x, size_t n_items, cudaStream_t st);
 
 // sampling: signed coefficients [n_items][N]; stream of item k = stream0 + k * step
 enum SampleKind { kTernary = 0, kCbd21 = 1 };

@@ -15,6 +15,9 @@ struct ModConst {
     uint64_t w1ninv_s;
     int32_t k;        // bit length of q
     int32_t pad;
+    uint64_t qneg;    // -q^-1 mod 2^64 (Montgomery reduction)
+    uint64_t rmod;    // 2^64 mod q (to Montgomery form)
+    uint64_t one_s;   // floor(2^64 / q): Shoup companion of 1 (full reduction)
 };
 
 #ifdef __CUDACC__

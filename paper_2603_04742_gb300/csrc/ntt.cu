@@ -13,6 +13,7 @@
 // the opposite order).  Small rings (N <= 4096) run one "rows" pass with
 // n1 = 0.
 #include "internal.h"
+#include "ntt_core.cuh"
 
 namespace hespmv {
 
@@ -44,8 +45,7 @@ __global__ void k_ntt_fwd_cols(NttArgs a, int n1, int TC) {
     const int N = 1 << a.log2n;
     const int R = 1 << n1, C = N >> n1;
     const uint64_t q = a.mc[prime].q;
-    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;
-    const uint64_t *tws = tw + N;
+    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;  // (w, Shoup) pairs
     const int c0 = blockIdx.x * TC;
     for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
         const int r = e / TC, cc = e - r * TC;
@@ -58,7 +58,7 @@ __global__ void k_ntt_fwd_cols(NttArgs a, int n1, int TC) {
             const int cc = b % TC, bb = b / TC;
             const int grp = bb / half, pos = bb - grp * half;
             const int r = grp * 2 * half + pos;
-            const uint64_t W = tw[m + grp], Ws = tws[m + grp];
+            const uint64_t W = tw[2 * (m + grp)], Ws = tw[2 * (m + grp) + 1];
             const uint64_t u = sm[r * TC + cc];
             const uint64_t v = mul_shoup(sm[(r + half) * TC + cc], W, Ws, q);
             sm[r * TC + cc] = add_mod(u, v, q);
@@ -81,8 +81,7 @@ __global__ void k_ntt_fwd_rows(NttArgs a, int n1, int TR) {
     const int N = 1 << a.log2n;
     const int C = N >> n1;
     const uint64_t q = a.mc[prime].q;
-    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;
-    const uint64_t *tws = tw + N;
+    const uint64_t *tw = a.tw + (int64_t)prime * 4 * N;  // (w, Shoup) pairs
     const int r0 = blockIdx.x * TR;
     uint64_t *base = x + (int64_t)r0 * C;
     for (int e = threadIdx.x; e < TR * C; e += blockDim.x) sm[e] = base[e];
@@ -96,7 +95,7 @@ __global__ void k_ntt_fwd_rows(NttArgs a, int n1, int TR) {
             const int idx = rr * C + grp * 2 * t + pos;
             const int i = (r0 + rr) * per_row + grp;
             const uint64_t u = sm[idx];
-            const uint64_t v = mul_shoup(sm[idx + t], tw[m + i], tws[m + i], q);
+            const uint64_t v = mul_shoup(sm[idx + t], tw[2 * (m + i)], tw[2 * (m + i) + 1], q);
             sm[idx] = add_mod(u, v, q);
             sm[idx + t] = sub_mod(u, v, q);
         }
@@ -115,8 +114,7 @@ __global__ void k_ntt_inv_rows(NttArgs a, int n1, int TR) {
     const int C = N >> n1;
     const ModConst mc = a.mc[prime];
     const uint64_t q = mc.q;
-    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;
-    const uint64_t *itws = itw + N;
+    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;  // (w, Shoup) pairs
     const int r0 = blockIdx.x * TR;
     uint64_t *base = x + (int64_t)r0 * C;
     for (int e = threadIdx.x; e < TR * C; e += blockDim.x) sm[e] = base[e];
@@ -135,7 +133,7 @@ __global__ void k_ntt_inv_rows(NttArgs a, int n1, int TR) {
                 sm[idx + t] = mul_shoup(u + q - v, mc.w1ninv, mc.w1ninv_s, q);
             } else {
                 sm[idx] = add_mod(u, v, q);
-                sm[idx + t] = mul_shoup(u + q - v, itw[m + i], itws[m + i], q);
+                sm[idx + t] = mul_shoup(u + q - v, itw[2 * (m + i)], itw[2 * (m + i) + 1], q);
             }
         }
         __syncthreads();
@@ -153,8 +151,7 @@ __global__ void k_ntt_inv_cols(NttArgs a, int n1, int TC) {
     const int R = 1 << n1, C = N >> n1;
     const ModConst mc = a.mc[prime];
     const uint64_t q = mc.q;
-    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;
-    const uint64_t *itws = itw + N;
+    const uint64_t *itw = a.tw + (int64_t)prime * 4 * N + 2 * N;  // (w, Shoup) pairs
     const int c0 = blockIdx.x * TC;
     for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
         const int r = e / TC, cc = e - r * TC;
@@ -173,7 +170,7 @@ __global__ void k_ntt_inv_cols(NttArgs a, int n1, int TC) {
                 sm[(r + half) * TC + cc] = mul_shoup(u + q - v, mc.w1ninv, mc.w1ninv_s, q);
             } else {
                 sm[r * TC + cc] = add_mod(u, v, q);
-                sm[(r + half) * TC + cc] = mul_shoup(u + q - v, itw[m + grp], itws[m + grp], q);
+                sm[(r + half) * TC + cc] = mul_shoup(u + q - v, itw[2 * (m + grp)], itw[2 * (m + grp) + 1], q);
             }
         }
         __syncthreads();
@@ -181,6 +178,201 @@ __global__ void k_ntt_inv_cols(NttArgs a, int n1, int TC) {
     for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
         const int r = e / TC, cc = e - r * TC;
         x[(int64_t)r * C + c0 + cc] = sm[e];
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Register-blocked passes (N >= 2^11: a limb holds at least one 2048-word
+// tile), see ntt_core.cuh.
+
+// Column pass, forward: local stages 0 .. LOGM-1 of the R = 2^LOGM rows.
+template <int LOGM>
+__global__ __launch_bounds__(kNttThreads) void k_fntt_cols(NttArgs a) {
+    constexpr int M = 1 << LOGM, TC = kNttTile / M;
+    constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
+    __shared__ uint64_t sm[kNttTile];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n, C = N >> LOGM;
+    const uint64_t q = a.mc[prime].q;
+    const TwPair *tw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N);
+    const int t = threadIdx.x, cc = t % TC, j = t / TC;
+    uint64_t *col = x + blockIdx.x * TC + cc;
+    uint64_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = col[(int64_t)elem_pos<LOGM, 0, 3>(j, e) * C];
+    fwd_round<LOGM, 0, 3>(v, j, 1, tw, q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[elem_pos<LOGM, 0, 3>(j, e) * TC + cc] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[elem_pos<LOGM, 3, R1>(j, e) * TC + cc];
+    fwd_round<LOGM, 3, R1>(v, j, 1, tw, q);
+    if constexpr (R2 > 0) {
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sm[elem_pos<LOGM, 3, R1>(j, e) * TC + cc] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sm[elem_pos<LOGM, 3 + R1, R2>(j, e) * TC + cc];
+        fwd_round<LOGM, 3 + R1, R2>(v, j, 1, tw, q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) col[(int64_t)elem_pos<LOGM, 3 + R1, R2>(j, e) * C] = v[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) col[(int64_t)elem_pos<LOGM, 3, R1>(j, e) * C] = v[e];
+    }
+}
+
+// Row pass, forward: local stages of each C = 2^LOGM row; output reduced.
+template <int LOGM>
+__global__ __launch_bounds__(kNttThreads) void k_fntt_rows(NttArgs a) {
+    constexpr int M = 1 << LOGM, TR = kNttTile / M, P = M / 8;
+    constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
+    __shared__ uint64_t sm[kRowTileWords];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n, n1 = a.log2n - LOGM;
+    const uint64_t q = a.mc[prime].q, one_s = a.mc[prime].one_s;
+    const TwPair *tw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N);
+    const int t = threadIdx.x, rr = t / P, j = t % P;
+    const int row = blockIdx.x * TR + rr;
+    const uint32_t twb = (1u << n1) + row;
+    uint64_t *base = x + (int64_t)row * M;
+    const RowIdx<M> si{rr};
+    uint64_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = base[elem_pos<LOGM, 0, 3>(j, e)];
+    fwd_round<LOGM, 0, 3>(v, j, twb, tw, q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 0, 3>(j, e))] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3, R1>(j, e))];
+    fwd_round<LOGM, 3, R1>(v, j, twb, tw, q);
+    if constexpr (R2 > 0) {
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3, R1>(j, e))] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))];
+        fwd_round<LOGM, 3 + R1, R2>(v, j, twb, tw, q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) base[elem_pos<LOGM, 3 + R1, R2>(j, e)] = reduce_full(v[e], q, one_s);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) base[elem_pos<LOGM, 3, R1>(j, e)] = reduce_full(v[e], q, one_s);
+    }
+}
+
+// Row pass, inverse: local stages LOGM-1 .. 0 of each row (first inverse pass).
+template <int LOGM>
+__global__ __launch_bounds__(kNttThreads) void k_intt_rows(NttArgs a) {
+    constexpr int M = 1 << LOGM, TR = kNttTile / M, P = M / 8;
+    constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
+    __shared__ uint64_t sm[kRowTileWords];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n, n1 = a.log2n - LOGM;
+    const uint64_t q = a.mc[prime].q;
+    const TwPair *itw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N + 2 * N);
+    const int t = threadIdx.x, rr = t / P, j = t % P;
+    const int row = blockIdx.x * TR + rr;
+    const uint32_t twb = (1u << n1) + row;
+    uint64_t *base = x + (int64_t)row * M;
+    const RowIdx<M> si{rr};
+    uint64_t v[8];
+    if constexpr (R2 > 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = base[elem_pos<LOGM, 3 + R1, R2>(j, e)];
+        inv_round<LOGM, 3 + R1, R2>(v, j, twb, itw, q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3, R1>(j, e))];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = base[elem_pos<LOGM, 3, R1>(j, e)];
+    }
+    inv_round<LOGM, 3, R1>(v, j, twb, itw, q);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3, R1>(j, e))] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 0, 3>(j, e))];
+    inv_round<LOGM, 0, 3>(v, j, twb, itw, q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) base[elem_pos<LOGM, 0, 3>(j, e)] = v[e];
+}
+
+// Column pass, inverse: local stages LOGM-1 .. 0 of the columns, with N^-1
+// folded into stage 0; output reduced to [0, q).
+template <int LOGM>
+__global__ __launch_bounds__(kNttThreads) void k_intt_cols(NttArgs a) {
+    constexpr int M = 1 << LOGM, TC = kNttTile / M;
+    constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
+    __shared__ uint64_t sm[kNttTile];
+    uint64_t *x;
+    int prime;
+    limb_of(a, x, prime);
+    const int N = 1 << a.log2n, C = N >> LOGM;
+    const ModConst mc = a.mc[prime];
+    const uint64_t q = mc.q;
+    const TwPair *itw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N + 2 * N);
+    const int t = threadIdx.x, cc = t % TC, j = t / TC;
+    uint64_t *col = x + blockIdx.x * TC + cc;
+    uint64_t v[8];
+    if constexpr (R2 > 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = col[(int64_t)elem_pos<LOGM, 3 + R1, R2>(j, e) * C];
+        inv_round<LOGM, 3 + R1, R2>(v, j, 1, itw, q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sm[elem_pos<LOGM, 3 + R1, R2>(j, e) * TC + cc] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sm[elem_pos<LOGM, 3, R1>(j, e) * TC + cc];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = col[(int64_t)elem_pos<LOGM, 3, R1>(j, e) * C];
+    }
+    inv_round<LOGM, 3, R1>(v, j, 1, itw, q);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[elem_pos<LOGM, 3, R1>(j, e) * TC + cc] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = sm[elem_pos<LOGM, 0, 3>(j, e) * TC + cc];
+    inv_round_last<LOGM, 3>(v, j, 1, itw, q, mc.ninv, mc.ninv_s, mc.w1ninv, mc.w1ninv_s);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) col[(int64_t)elem_pos<LOGM, 0, 3>(j, e) * C] = v[e];
+}
+
+template <int LC, int LR>
+static void launch_fast(const NttArgs &a, const Ctx &c, int total, bool inverse, cudaStream_t st) {
+    const int N = c.N;
+    dim3 gc((N >> LC) / (kNttTile >> LC), total), gr((N >> LR) / (kNttTile >> LR), total);
+    int r;
+    if (!inverse) {
+        r = prof_begin(c, "k_fntt_cols", st);
+        k_fntt_cols<LC><<<gc, kNttThreads, 0, st>>>(a);
+        prof_end(c, r, st);
+        r = prof_begin(c, "k_fntt_rows", st);
+        k_fntt_rows<LR><<<gr, kNttThreads, 0, st>>>(a);
+        prof_end(c, r, st);
+    } else {
+        r = prof_begin(c, "k_intt_rows", st);
+        k_intt_rows<LR><<<gr, kNttThreads, 0, st>>>(a);
+        prof_end(c, r, st);
+        r = prof_begin(c, "k_intt_cols", st);
+        k_intt_cols<LC><<<gc, kNttThreads, 0, st>>>(a);
+        prof_end(c, r, st);
     }
 }
 
@@ -206,6 +398,14 @@ cudaError_t launch_ntt(const Ctx &c, uint64_t *data, int prime0, int n_limbs, in
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
+    }
+    switch (c.log2n) {  // register-blocked two-pass transform, R = 2^(n/2) rows
+        case 15: launch_fast<7, 8>(a, c, total, inverse, st); return cudaGetLastError();
+        case 14: launch_fast<7, 7>(a, c, total, inverse, st); return cudaGetLastError();
+        case 13: launch_fast<6, 7>(a, c, total, inverse, st); return cudaGetLastError();
+        case 12: launch_fast<6, 6>(a, c, total, inverse, st); return cudaGetLastError();
+        case 11: launch_fast<5, 6>(a, c, total, inverse, st); return cudaGetLastError();
+        default: break;
     }
     if (c.log2n <= 12) {
         dim3 grid(1, total);

@@ -43,13 +43,76 @@ __global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *d, int6
     }
 }
 
+__device__ __forceinline__ uint64_t mont_reduce(uint64_t hi, uint64_t lo, uint64_t q,
+                                                uint64_t qneg) {
+    const uint64_t m = lo * qneg;
+    uint64_t r = hi + __umul64hi(m, q) + (lo != 0);
+    return r >= q ? r - q : r;
+}
+
+// ct * pt with the plaintext in Montgomery form (mask plaintexts)
 __global__ void k_cmult(const uint64_t *ct, const uint64_t *pt, uint64_t *out, int64_t total,
                         int log2n, int L, const ModConst *mc) {
     const int64_t LN = (int64_t)L << log2n;
     GRID_STRIDE(i, total) {
         const int64_t r = i % LN;
-        const int l = (int)(r >> log2n);
-        out[i] = mul_mod(ct[i], pt[r], mc[l]);
+        const ModConst m = mc[(int)(r >> log2n)];
+        const uint64_t a = ct[i], b = pt[r];
+        out[i] = mont_reduce(__umul64hi(a, b), a * b, m.q, m.qneg);
+    }
+}
+
+// out = sum_k w_k * mask_k over the nterms ciphertexts w_k = w0 + k * 2LN
+// (Algorithm 4, inter-chunk aggregation); masks in Montgomery form, 128-bit
+// sums reduced once per block of 4096 terms.
+__global__ void k_mask_acc(const uint64_t *w0, const uint64_t *const *masks, int nterms,
+                           uint64_t *out, int64_t total, int log2n, int L, const ModConst *mc) {
+    const int64_t LN = (int64_t)L << log2n;
+    GRID_STRIDE(i, total) {  // total = 2 * L * N
+        const int64_t r = i % LN;
+        const ModConst m = mc[(int)(r >> log2n)];
+        uint64_t s = 0;
+        for (int k0 = 0; k0 < nterms; k0 += 4096) {
+            const int k1 = min(nterms, k0 + 4096);
+            uint64_t hi = 0, lo = 0;
+            for (int k = k0; k < k1; ++k) {
+                const uint64_t a = w0[(int64_t)k * 2 * LN + i], b = masks[k][r];
+                const uint64_t pl = a * b;
+                lo += pl;
+                hi += __umul64hi(a, b) + (lo < pl);
+            }
+            s = add_mod(s, mont_reduce(hi, lo, m.q, m.qneg), m.q);
+        }
+        out[i] = s;
+    }
+}
+
+// dst[di[s]] (=, +=) src[si[s]] (through the Galois permutation if perm),
+// s < m whole ciphertexts; a null index list is the identity
+__global__ void k_ct_move(uint64_t *dst, const int32_t *di, const uint64_t *src, const int32_t *si,
+                          const int32_t *perm, int add, int64_t total, int log2n, int L,
+                          const ModConst *mc) {
+    const int64_t CT = (int64_t)2 * L << log2n;
+    GRID_STRIDE(i, total) {
+        const int64_t s = i / CT, w = i - s * CT;
+        const int64_t ds = di ? di[s] : s, ss = si ? si[s] : s;
+        const int64_t sw = perm ? ((w >> log2n) << log2n) + perm[w & ((1 << log2n) - 1)] : w;
+        const uint64_t v = src[ss * CT + sw];
+        uint64_t *o = dst + ds * CT + w;
+        if (add) {
+            const uint64_t q = mc[(w >> log2n) % L].q;
+            *o = add_mod(*o, v, q);
+        } else {
+            *o = v;
+        }
+    }
+}
+
+__global__ void k_to_mont_limbs(uint64_t *x, int64_t total, int log2n, int prime0, int nl,
+                                const ModConst *mc) {
+    GRID_STRIDE(i, total) {
+        const ModConst m = mc[prime0 + (int)((i >> log2n) % nl)];
+        x[i] = mul_mod(x[i], m.rmod, m);
     }
 }
 
@@ -126,7 +189,8 @@ __global__ void k_modup(const uint64_t *dcoef, uint64_t *ext, int64_t total, int
     }
 }
 
-// acc[c][l] = sum_j ext[j][l] * key[j][c][l]
+// acc[c][l] = sum_j ext[j][l] * key[j][c][l]; the key is in Montgomery form,
+// so one reduction of the 128-bit sum gives the plain residue
 __global__ void k_inner(const uint64_t *ext, const uint64_t *key, uint64_t *acc, int64_t total,
                         int log2n, int L, int K, int dnum, const ModConst *mc) {
     const int LK = L + K;
@@ -135,14 +199,26 @@ __global__ void k_inner(const uint64_t *ext, const uint64_t *key, uint64_t *acc,
         const int64_t item = i / LKN, r = i - item * LKN;
         const int l = (int)(r >> log2n);
         const ModConst m = mc[l];
-        uint64_t s0 = 0, s1 = 0;
+        uint64_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
         for (int j = 0; j < dnum; ++j) {
             const uint64_t e = ext[(item * dnum + j) * LKN + r];
-            s0 = add_mod(s0, mul_mod(e, key[(int64_t)(2 * j) * LKN + r], m), m.q);
-            s1 = add_mod(s1, mul_mod(e, key[(int64_t)(2 * j + 1) * LKN + r], m), m.q);
+            const uint64_t w0 = key[(int64_t)(2 * j) * LKN + r], w1 = key[(int64_t)(2 * j + 1) * LKN + r];
+            uint64_t lo = e * w0;
+            l0 += lo;
+            h0 += __umul64hi(e, w0) + (l0 < lo);
+            lo = e * w1;
+            l1 += lo;
+            h1 += __umul64hi(e, w1) + (l1 < lo);
         }
-        acc[(item * 2) * LKN + r] = s0;
-        acc[(item * 2 + 1) * LKN + r] = s1;
+        acc[(item * 2) * LKN + r] = mont_reduce(h0, l0, m.q, m.qneg);
+        acc[(item * 2 + 1) * LKN + r] = mont_reduce(h1, l1, m.q, m.qneg);
+    }
+}
+
+__global__ void k_to_mont(uint64_t *x, int64_t total, int log2n, int LK, const ModConst *mc) {
+    GRID_STRIDE(i, total) {
+        const ModConst m = mc[(i >> log2n) % LK];
+        x[i] = mul_mod(x[i], m.rmod, m);
     }
 }
 
@@ -368,6 +444,25 @@ cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint6
     LAUNCH(k_cmult, total, st, ct, pt, out, total, c.log2n, c.L, c.c->d.mc);
 }
 
+cudaError_t op_mask_acc(const Ctx &c, const uint64_t *w0, const uint64_t *const *masks,
+                        int nterms, uint64_t *out, cudaStream_t st) {
+    const int64_t total = (int64_t)2 * c.L * c.N;
+    LAUNCH(k_mask_acc, total, st, w0, masks, nterms, out, total, c.log2n, c.L, c.c->d.mc);
+}
+
+cudaError_t op_ct_move(const Ctx &c, uint64_t *dst, const int32_t *di, const uint64_t *src,
+                       const int32_t *si, const int32_t *perm, bool add, int m, cudaStream_t st) {
+    const int64_t total = (int64_t)m * 2 * c.L * c.N;
+    LAUNCH(k_ct_move, total, st, dst, di, src, si, perm, add ? 1 : 0, total, c.log2n, c.L,
+           c.c->d.mc);
+}
+
+cudaError_t op_to_mont_limbs(const Ctx &c, uint64_t *x, int prime0, int n_limbs, size_t n_items,
+                             cudaStream_t st) {
+    const int64_t total = (int64_t)n_items * n_limbs * c.N;
+    LAUNCH(k_to_mont_limbs, total, st, x, total, c.log2n, prime0, n_limbs, c.c->d.mc);
+}
+
 cudaError_t op_cmult_acc(const Ctx &c, uint64_t *acc, const uint64_t *w, const uint64_t *pt,
                          bool first, cudaStream_t st) {
     const int64_t total = (int64_t)2 * c.L * c.N;
@@ -390,6 +485,11 @@ cudaError_t op_copy_strided(const Ctx &c, const uint64_t *src, int64_t src_strid
                             int64_t dst_stride, int64_t words, size_t n_items, cudaStream_t st) {
     const int64_t total = words * (int64_t)n_items;
     LAUNCH(k_copy_strided, total, st, src, src_stride, dst, dst_stride, words, total);
+}
+
+cudaError_t op_to_mont(const Ctx &c, uint64_t *x, size_t n_items, cudaStream_t st) {
+    const int64_t total = (int64_t)n_items * (c.L + c.K) * c.N;
+    LAUNCH(k_to_mont, total, st, x, total, c.log2n, c.L + c.K, c.c->d.mc);
 }
 
 cudaError_t op_modup(const Ctx &c, const uint64_t *dcoef, uint64_t *ext, size_t n, cudaStream_t st) {

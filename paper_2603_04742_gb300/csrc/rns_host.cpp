@@ -127,10 +127,10 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         uint64_t *T = &h.tw[(size_t)m * 4 * N];
         for (uint64_t k = 0; k < N; ++k) {
             uint32_t b = host_bitrev((uint32_t)k, p.log2n);
-            T[k] = pw[b];
-            T[N + k] = shoup(pw[b], q);
-            T[2 * N + k] = ipw[b];
-            T[3 * N + k] = shoup(ipw[b], q);
+            T[2 * k] = pw[b];  // forward pairs (w, Shoup), then inverse pairs
+            T[2 * k + 1] = shoup(pw[b], q);
+            T[2 * N + 2 * k] = ipw[b];
+            T[2 * N + 2 * k + 1] = shoup(ipw[b], q);
         }
         ModConst &c = h.mc[m];
         memset(&c, 0, sizeof(c));
@@ -139,8 +139,13 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         c.mu = (uint64_t)(((u128)1 << (2 * c.k)) / q);
         c.ninv = invm(N % q, q);
         c.ninv_s = shoup(c.ninv, q);
-        c.w1ninv = mulm(T[2 * N + 1], c.ninv, q);
+        c.w1ninv = mulm(T[2 * N + 2], c.ninv, q);
         c.w1ninv_s = shoup(c.w1ninv, q);
+        uint64_t inv = q;  // Newton iteration for q^-1 mod 2^64 (q odd)
+        for (int it = 0; it < 6; ++it) inv *= 2 - q * inv;
+        c.qneg = 0 - inv;
+        c.rmod = (0 - q) % q;
+        c.one_s = shoup(1, q);
     }
     const int L = p.L, K = p.K, LK = L + K, A = h.alpha;
     // ModUp constants
@@ -226,6 +231,33 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
     h.dec[(size_t)L * 4 + 1] = shoup(Qt, p.t);
     h.t_mod.resize(LK);
     for (int l = 0; l < LK; ++l) h.t_mod[l] = p.t % h.q[l];
+    // fused key-switching constants
+    h.ks_zc.assign((size_t)L * 4, 0);
+    for (int i = 0; i < L; ++i) {
+        const int j = i / A;
+        const uint64_t qi = h.q[i], qinv = h.modup_inv[((size_t)j * A + (i - j * A)) * 2];
+        const uint64_t c0 = mulm(h.mc[i].ninv, qinv, qi), c1 = mulm(h.mc[i].w1ninv, qinv, qi);
+        h.ks_zc[i * 4 + 0] = c0;
+        h.ks_zc[i * 4 + 1] = shoup(c0, qi);
+        h.ks_zc[i * 4 + 2] = c1;
+        h.ks_zc[i * 4 + 3] = shoup(c1, qi);
+    }
+    h.ks_yc.assign((size_t)K * 4, 0);
+    h.md_phat_t.assign((size_t)K * L * 2, 0);
+    for (int k = 0; k < K; ++k) {
+        const uint64_t pk = h.q[L + k], v = h.md_pk[k * 2];
+        const uint64_t c0 = mulm(h.mc[L + k].ninv, v, pk), c1 = mulm(h.mc[L + k].w1ninv, v, pk);
+        h.ks_yc[k * 4 + 0] = c0;
+        h.ks_yc[k * 4 + 1] = shoup(c0, pk);
+        h.ks_yc[k * 4 + 2] = c1;
+        h.ks_yc[k * 4 + 3] = shoup(c1, pk);
+        for (int i = 0; i < L; ++i) {
+            const uint64_t qi = h.q[i];
+            const uint64_t w = mulm(h.md_phat[((size_t)k * L + i) * 2], p.t % qi, qi);
+            h.md_phat_t[((size_t)k * L + i) * 2] = w;
+            h.md_phat_t[((size_t)k * L + i) * 2 + 1] = shoup(w, qi);
+        }
+    }
     // batching slot positions
     h.slot_idx.resize(N);
     uint64_t e = 1;

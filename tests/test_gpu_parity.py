@@ -119,11 +119,13 @@ def _random_slot_ciphertexts(ctx, orc, n, seed):
     return A, oc, vals
 
 
-@pytest.fixture(scope="module")
-def pair_small():
-    N = 1 << 10
+@pytest.fixture(scope="module", params=[10, 12])
+def pair_small(request):
+    # 2^10 runs the unfused key switch, 2^12 the fused one (alpha = 2, K = 2)
+    logn = request.param
+    N = 1 << logn
     t = plain_modulus(N, 1 << 20)
-    return make_pair(10, 5, 2, 3, t, seed=11, steps=[1, 2, 5, 100, 511])
+    return make_pair(logn, 5, 2, 3, t, seed=11, steps=[1, 2, 5, 100, 511])
 
 
 def test_encrypt_and_ops_parity(pair_small):
