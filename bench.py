@@ -35,6 +35,8 @@ CONFIGS = {
     "c1": "512x512, 2621 nnz uniform, integers [-15,15]; BGV N=2^12, 3+1 primes, dnum 3, t=65537",
     "c2": "4096x4096, 16777 nnz, power-law column counts, integers [-127,127]; "
           "BGV N=2^14, 5+1 primes, dnum 5, t=17006593",
+    "c4": "64 square matrices, n log-U[256,8192], density log-U[5e-4,2e-2], integers [-15,15]; "
+          "BGV N=2^14, 5+1 primes, dnum 5, t=1146881; batched evaluation vs plain calls",
 }
 # dense 32-bit multiply-adds per SM per clock, SM count and maximum SM clock
 # of a GB300; a Shoup modular product needs 10 32x32-bit partial products
@@ -50,9 +52,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--instances", type=int, default=64, help="c4: SpMVs per batched step")
+    ap.add_argument("--pool", type=int, default=32, help="c5: distinct instances")
+    ap.add_argument("--requests", type=int, default=10000, help="c5: Poisson requests")
+    ap.add_argument("--sat-requests", type=int, default=1000, help="c5: closed-loop requests")
+    ap.add_argument("--serial-requests", type=int, default=1000, help="c5: serial-server requests")
+    ap.add_argument("--slots", type=int, default=3, help="c5: concurrent evaluations")
+    ap.add_argument("--max-batch", type=int, default=16, help="c5: requests per evaluation")
     return ap.parse_args()
 
 
@@ -223,107 +232,30 @@ def run_reference(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
+def time_steps(fn, stream, steps, barrier):
+    """Device time per step (ms) of `steps` calls of fn, CUDA events on the
+    launch stream, barrier + synchronize on both sides."""
     import torch
-    import torch.distributed as dist
-
-    from paper_2603_04742_gb300 import binding as B
-    from paper_2603_04742_gb300.api import Context
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    A, x, ring = load_workload(args.config)
-    logn, L, K, dnum, t = ring
-    ctx = Context(logn, L, K, dnum, t, device=local)
-    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
-    ctx.keygen(1 + rank, m.rotation_steps())
-    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 10 * rank)
-    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3 + 10 * rank)
-    y = ctx.spmv(m, ca, cx)
-    torch.cuda.synchronize()
-    correct = list(ctx.decrypt(m, y)) == list(A.matvec(x))
-    stream = torch.cuda.current_stream()
-
-    for _ in range(max(3, args.warmup)):
-        ctx.spmv(m, ca, cx, y=y, stream=stream)
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    clocks = Clocks(local)
-    clocks.start()
-    ctx.profile_enable(True)
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        ctx.spmv(m, ca, cx, y=y, stream=stream)
+    for _ in range(steps):
+        fn()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * 1000.0 / ms
+    return e0.elapsed_time(e1) / steps
 
-    # e2e through the C ABI from pinned host buffers
-    e2e = None
-    ct_words = 2 * L * (1 << logn)
-    if not args.no_e2e:
-        hA = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
-        hX = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
-        hY = torch.empty(m.n_parts * ct_words, dtype=torch.int64, pin_memory=True)
-        hA.numpy()[:] = ca.download().reshape(-1).view(np.int64)
-        hX.numpy()[:] = cx.download().reshape(-1).view(np.int64)
-        nA, nX, nY = (hA.numpy().view(np.uint64), hX.numpy().view(np.uint64),
-                      hY.numpy().view(np.uint64))
-        for _ in range(2):
-            ctx.spmv_host(m, nA, nX, nY, stream=stream)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ctx.spmv_host(m, nA, nX, nY, stream=stream)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([dt], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        assert np.array_equal(nY.reshape(y.download().shape), y.download())
-        e2e = {"value": world * args.steps / dt, "unit": "SpMV/s",
-               "h2d_bytes_per_step": 2 * m.n_chunks * ct_words * 8,
-               "d2h_bytes_per_step": m.n_parts * ct_words * 8}
 
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return 0
-
-    # roofline of the dominant kernel
+def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot):
     peaks, peak_kind = measured_peaks()
-    n_ks = m.n_chunks + m.n_keyswitch
     kernels = {}
     total_ms = sum(v[1] for v in prof.values())
     for name, (cnt, kms) in prof.items():
-        mm, by = kernel_model(name, ring, n_ks, m.n_chunks, m.n_parts, m.n_rot)
-        kernels[name] = {"launches_per_step": cnt / args.steps, "ms_per_step": kms / args.steps,
+        mm, by = kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot)
+        kernels[name] = {"launches_per_step": cnt / steps, "ms_per_step": kms / steps,
                          "share": kms / total_ms if total_ms else 0.0,
                          "mulmods_per_step": mm, "bytes_per_step": by}
     top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
@@ -345,39 +277,257 @@ def main():
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": top,
                 "peak_source": "%s hbm_gbs" % peak_kind}
+    roof["algorithmic_per_launch"] = {"mulmods": mm_launch, "bytes": by_launch}
     roof["mulmod_rate_measured_T"] = ctx.mulmod_rate(0) / 1e12
+    roof["timing"] = ("average launch time of %s over a second pass of the timed steps with "
+                      "CUDA events around each kernel on the launch stream" % top)
+    return kernels, roof
+
+
+def run_serving(args):
+    """c5: Poisson arrivals of SpMV requests drawn from a pool of distinct
+    pre-encrypted instances, served with continuous batching; compared with a
+    serial server (one request at a time) on the same arrival process."""
+    import torch
+
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300 import synth
+    from paper_2603_04742_gb300.api import Context, Server
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    pool = synth.workload("c5", pool=args.pool)
+    ring = synth.RING["c5"]
+    logn, L, K, dnum, t = ring
+    ctx = Context(logn, L, K, dnum, t)
+    ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in pool]
+    ctx.keygen(1, sorted({s for m in ms for s in m.rotation_steps()}))
+    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + i) for i, m in enumerate(ms)]
+    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=500 + i) for i, (m, (_, x)) in enumerate(zip(ms, pool))]
+    ys = [ctx.spmv(m, a, x) for m, a, x in zip(ms, As, Xs)]
+    torch.cuda.synchronize()
+    correct = all(list(ctx.decrypt(m, y)) == list(a.matvec(x)) for m, y, (a, x) in zip(ms, ys, pool))
+    rng = np.random.default_rng(105)
+    budget = args.slots * (6 << 30)
+
+    def serve(n_req, rate, slots, max_batch):
+        srv = Server(ctx, slots=slots, mem_budget_bytes=budget, max_batch=max_batch)
+        picks = rng.integers(0, len(pool), n_req)
+        gaps = rng.exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
+        arrive = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        tickets, sub = [], []
+        for k in range(n_req):
+            while True:
+                dt = arrive[k] - (time.perf_counter() - t0)
+                if dt <= 0:
+                    break
+                if dt > 1e-3:
+                    time.sleep(dt - 5e-4)
+            i = int(picks[k])
+            sub.append(time.perf_counter() - t0)
+            tickets.append(srv.submit(ms[i], As[i], Xs[i]))
+        while srv.stats()["completed"] < n_req:
+            time.sleep(1e-3)
+        st = srv.stats()
+        lat = np.array([srv.poll(tk)[1] for tk in tickets], dtype=np.float64) / 1e6  # ms
+        srv.stop(60000)
+        end = max(s_ + l_ / 1e3 for s_, l_ in zip(sub, lat))
+        nnz = sum(pool[int(i)][0].nnz for i in picks)
+        return {"requests": n_req, "throughput": n_req / end, "nnz_per_s": nnz / end,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "batches": st["batches"],
+                "max_inflight": st["max_inflight"], "slots": slots, "max_batch": max_batch}
+
+    sat = serve(args.sat_requests, None, args.slots, args.max_batch)
+    rate = 0.7 * sat["throughput"]
+    cont = serve(args.requests, rate, args.slots, args.max_batch)
+    serial = serve(args.serial_requests, rate, 1, 1)
+    line = {"metric": METRIC, "value": cont["throughput"], "unit": "SpMV/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "ms_per_step": 1e3 / cont["throughput"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "c5 serving: Poisson arrivals at %.1f req/s (0.7 x saturated), "
+                                   "requests drawn from %d distinct pre-encrypted instances, "
+                                   "N=2^15, 8+2 primes, dnum 4, t=1179649" % (rate, len(pool)),
+                       "pool_chunks": sum(m.n_chunks for m in ms)},
+            "correct": bool(correct), "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},
+            "nnz_per_s": cont["nnz_per_s"], "continuous_batching": cont, "saturated": sat,
+            "serial": serial}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.config == "c5":
+        return run_serving(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300 import synth
+    from paper_2603_04742_gb300.api import Context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world > 1:
+            tt = torch.tensor([v], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            return float(tt.item())
+        return v
+
+    stream = torch.cuda.current_stream()
+    batched = args.config == "c4"
+    if batched:
+        insts = synth.workload("c4", count=args.instances)
+        ring = synth.RING["c4"]
+    else:
+        A, x, ring = load_workload(args.config)
+        insts = [(A, x)]
+    logn, L, K, dnum, t = ring
+    ct_words = 2 * L * (1 << logn)
+    ctx = Context(logn, L, K, dnum, t, device=local)
+    ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in insts]
+    ctx.keygen(1 + rank, sorted({s for m in ms for s in m.rotation_steps()}))
+    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 1000 * rank + i) for i, m in enumerate(ms)]
+    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=xx, seed=3 + 1000 * rank + i)
+          for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
+    if batched:
+        ys = ctx.spmv_batched(ms, As, Xs)
+
+        def step():
+            ctx.spmv_batched(ms, As, Xs, ys, stream=stream)
+    else:
+        ys = [ctx.spmv(ms[0], As[0], Xs[0])]
+
+        def step():
+            ctx.spmv(ms[0], As[0], Xs[0], y=ys[0], stream=stream)
+    torch.cuda.synchronize()
+    correct = all(list(ctx.decrypt(m, y)) == list(a.matvec(xx))
+                  for m, y, (a, xx) in zip(ms, ys, insts))
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_step = max_over_ranks(time_steps(step, stream, args.steps, barrier))
+    clk = clocks.stop()
+    n_spmv = len(insts)
+    nnz = sum(a.nnz for a, _ in insts)
+    value = world * n_spmv * 1000.0 / ms_step
+
+    # per-kernel device times (second pass, kernels one by one)
+    ctx.profile_enable(True)
+    ms_profiled = time_steps(step, stream, args.steps, lambda: None)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+
+    extra = {}
+    if batched:
+        # the same instances as plain evaluations, one call each
+        yp = [ctx.spmv(m, a, xx) for m, a, xx in zip(ms, As, Xs)]
+        torch.cuda.synchronize()
+
+        def plain():
+            for m, a, xx, y in zip(ms, As, Xs, yp):
+                ctx.spmv(m, a, xx, y=y, stream=stream)
+        for _ in range(max(3, args.warmup)):
+            plain()
+        ms_plain = max_over_ranks(time_steps(plain, stream, args.steps, barrier))
+        same = all(np.array_equal(y.download(), z.download()) for y, z in zip(ys, yp))
+        extra["plain"] = {"value": world * n_spmv * 1000.0 / ms_plain, "unit": "SpMV/s",
+                          "ms_per_step": ms_plain, "identical_results": bool(same),
+                          "form": "%d hespmv_spmv calls per step" % n_spmv}
+        extra["batched_vs_plain"] = ms_plain / ms_step
+
+    # e2e through the C ABI from pinned host buffers (single-matrix workloads)
+    e2e = None
+    if not args.no_e2e and not batched:
+        m, ca, cx, y = ms[0], As[0], Xs[0], ys[0]
+        hA = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
+        hX = torch.empty(m.n_chunks * ct_words, dtype=torch.int64, pin_memory=True)
+        hY = torch.empty(m.n_parts * ct_words, dtype=torch.int64, pin_memory=True)
+        hA.numpy()[:] = ca.download().reshape(-1).view(np.int64)
+        hX.numpy()[:] = cx.download().reshape(-1).view(np.int64)
+        nA, nX, nY = (hA.numpy().view(np.uint64), hX.numpy().view(np.uint64),
+                      hY.numpy().view(np.uint64))
+        for _ in range(2):
+            ctx.spmv_host(m, nA, nX, nY, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.spmv_host(m, nA, nX, nY, stream=stream)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        assert np.array_equal(nY.reshape(y.download().shape), y.download())
+        e2e = {"value": world * args.steps / dt, "unit": "SpMV/s",
+               "h2d_bytes_per_step": 2 * m.n_chunks * ct_words * 8,
+               "d2h_bytes_per_step": m.n_parts * ct_words * 8}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    n_chunks = sum(m.n_chunks for m in ms)
+    n_ks = n_chunks + sum(m.n_keyswitch for m in ms)
+    kernels, roof = roofline(ctx, prof, args.steps, ring, n_ks, n_chunks,
+                             sum(m.n_parts for m in ms), sum(m.n_rot for m in ms))
 
     cpu = None
     if not args.no_cpu_baseline:
-        sample = 8 if args.config == "c3" else 10 ** 9
-        smp = OracleSample(A, x, ring, sample)
+        A0, x0 = insts[0]
+        sample = 8 if args.config in ("c3",) else 10 ** 9
+        smp = OracleSample(A0, x0, ring, sample)
         dt, n_total = smp.run(), smp.n_total
         n_s = len(smp.chunks)
-        v = 1.0 / (dt * n_total / n_s)
+        per_spmv = dt * n_total / n_s
+        if batched:   # scale instance 0 to the whole batch by chunk count
+            per_spmv *= n_chunks / max(1, ms[0].n_chunks) / n_spmv
+        v = 1.0 / per_spmv
         cpu = {"value": v, "unit": "SpMV/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle cloud evaluation of %d of %d chunks (%.1f s), scaled to one "
-                         "SpMV" % (n_s, n_total, dt)}
+               "sample": "oracle cloud evaluation of %d of %d chunks of instance 0 (%.1f s), "
+                         "scaled to one SpMV%s" % (n_s, n_total, dt,
+                                                   " of the batch by chunk count" if batched else "")}
 
+    cfg = {"workload": CONFIGS[args.config], "instances": n_spmv, "chunks": n_chunks,
+           "partitions": sum(m.n_parts for m in ms), "rotations": sum(m.n_rot for m in ms),
+           "keyswitches": n_ks,
+           "l2": "inputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * n_chunks * ct_words * 8 / 1e6),
+           "form": "hespmv_spmv_batched, one graph replay per step" if batched
+                   else "hespmv_spmv, one graph replay per step",
+           "parallelism": "independent SpMVs per GPU"}
     line = {
         "metric": METRIC, "value": value, "unit": "SpMV/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": CONFIGS[args.config], "chunks": m.n_chunks,
-                   "partitions": m.n_parts, "rotations": m.n_rot,
-                   "keyswitches": n_ks,
-                   "l2": "inputs %.0f MB per step > 129 MB L2 (no flush)"
-                         % (2 * m.n_chunks * ct_words * 8 / 1e6),
-                   "parallelism": "independent SpMV per GPU"},
-        "nnz_per_s": value * A.nnz,
+        "data": "synthetic", "config": cfg,
+        "nnz_per_s": value * nnz / n_spmv,
         "correct": bool(correct),
         "e2e": e2e,
         "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "graph_launches": args.steps,
+        "ms_per_step_kernels_one_by_one": ms_profiled,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clk,
         "kernels": kernels,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -228,6 +228,38 @@ int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out);
 
+/* ------------------------------------------------------------ serving */
+
+/* A serving loop with continuous batching (keys and operands resident in
+ * HBM).  A host thread takes queued requests first come first served into
+ * batched evaluations; each of `slots` concurrent evaluations runs on its own
+ * stream with its own workspace of mem_budget_bytes / slots bytes, so batches
+ * overlap on the device and new requests are admitted as soon as a slot and
+ * its memory free up (at most max_batch requests per evaluation).  A request
+ * whose own footprint exceeds a slot is rejected (HESPMV_E_REJECTED).  While
+ * a server runs, its context must only be used through the hespmv_server_*
+ * calls (plus reads of ciphertext batches that are not in flight). */
+typedef struct hespmv_server hespmv_server;
+int hespmv_server_start(hespmv_ctx *ctx, int32_t slots, size_t mem_budget_bytes, int32_t max_batch,
+                        hespmv_server **out);
+/* Queue an SpMV of matrix m on device operands A, X (as for hespmv_spmv).
+ * The result goes to y (n_parts ciphertexts), or is computed and dropped when
+ * y is NULL.  *ticket identifies the request.  Thread-safe.  The first request
+ * of a matrix makes its mask plaintexts resident (synchronous). */
+int hespmv_server_submit(hespmv_server *s, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                         const hespmv_ctbatch *X, hespmv_ctbatch *y, uint64_t *ticket);
+/* *done = 1 once the request's device work has finished (its y is final),
+ * 0 while queued or running, -1 if its batch failed.  *latency_ns = time from
+ * submission to the loop's observation of completion (host steady clock). */
+int hespmv_server_poll(hespmv_server *s, uint64_t ticket, int32_t *done, int64_t *latency_ns);
+int hespmv_server_stats(hespmv_server *s, int64_t *submitted, int64_t *completed, int64_t *batches,
+                        int64_t *rejected, int64_t *max_inflight);
+/* Drain and stop: waits at most timeout_ms (< 0: no limit) for every
+ * submitted request; returns HESPMV_E_TIMEOUT if the wait expired (the loop is
+ * then still joined after its in-flight batches finish), then releases the
+ * slots and the handle. */
+int hespmv_server_stop(hespmv_server *s, int64_t timeout_ms);
+
 /* -------------------------------------------------- HE primitives (device) */
 /* All pointers below are device addresses of n whole ciphertexts (or
  * polynomials where stated); in-place use (out == in) is allowed except
@@ -285,6 +317,13 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
  *    on the array: serialise them. */
 int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt,
                              uint64_t *out, size_t n, void *stream);
+
+/* Evaluations (hespmv_spmv, hespmv_spmv_batched, hespmv_spmv_host) are
+ * recorded once into a CUDA graph per set of matrices, buffers and workspace
+ * and replayed afterwards (one launch per evaluation).  enable = 0 makes
+ * every evaluation launch its kernels one by one.  Graphs are not used while
+ * profiling is enabled.  Default: enabled. */
+int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable);
 
 /* ------------------------------------------------------------ measurement */
 

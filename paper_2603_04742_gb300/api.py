@@ -171,6 +171,9 @@ class Context:
         self.check(self.lib.hespmv_decrypt_slots(self.h, b.h, index, _u64p(out)))
         return out
 
+    def set_graphs(self, on=True):
+        self.check(self.lib.hespmv_set_graphs(self.h, 1 if on else 0))
+
     # ---- measurement ----
     def profile_enable(self, on=True):
         self.check(self.lib.hespmv_profile_enable(self.h, 1 if on else 0))
@@ -225,6 +228,51 @@ class Context:
     def keyswitch(self, d, galois, out, n=1, stream=None):
         self.check(self.lib.hespmv_keyswitch(self.h, c_void_p(d), galois, c_void_p(out), n,
                                              _stream_handle(stream)))
+
+
+class Server:
+    """Continuous-batching serving loop (hespmv_server_*)."""
+
+    def __init__(self, ctx, slots=2, mem_budget_bytes=8 << 30, max_batch=16):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        h = c_void_p()
+        ctx.check(self.lib.hespmv_server_start(ctx.h, slots, mem_budget_bytes, max_batch, byref(h)))
+        self.h = h
+
+    def submit(self, m, A, X, y=None):
+        t = c_uint64()
+        rc = self.lib.hespmv_server_submit(self.h, m.h, A.h, X.h, y.h if y is not None else None,
+                                           byref(t))
+        self.ctx.check(rc)
+        return t.value
+
+    def poll(self, ticket):
+        """(done, latency_ns): done 1 finished, 0 pending, -1 failed."""
+        d = c_int32()
+        lat = c_int64()
+        rc = self.lib.hespmv_server_poll(self.h, ticket, byref(d), byref(lat))
+        if rc != B.HESPMV_OK and d.value != -1:
+            self.ctx.check(rc)
+        return d.value, lat.value
+
+    def stats(self):
+        v = [c_int64() for _ in range(5)]
+        self.ctx.check(self.lib.hespmv_server_stats(self.h, *[byref(x) for x in v]))
+        return dict(zip(["submitted", "completed", "batches", "rejected", "max_inflight"],
+                        [x.value for x in v]))
+
+    def stop(self, timeout_ms=-1):
+        if getattr(self, "h", None):
+            h, self.h = self.h, None
+            return self.lib.hespmv_server_stop(h, timeout_ms)
+        return B.HESPMV_OK
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 class Cssc:

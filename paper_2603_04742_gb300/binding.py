@@ -89,6 +89,13 @@ SIGNATURES = {
     "hespmv_keyswitch": (c_int, [c_void_p, c_void_p, c_uint32, c_void_p, c_size_t, c_void_p]),
     "hespmv_keyswitch_noalloc": (c_int, [c_void_p, c_void_p, c_uint32, c_void_p, c_size_t,
                                          c_void_p]),
+    "hespmv_set_graphs": (c_int, [c_void_p, c_int32]),
+    "hespmv_server_start": (c_int, [c_void_p, c_int32, c_size_t, c_int32, POINTER(c_void_p)]),
+    "hespmv_server_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     POINTER(c_uint64)]),
+    "hespmv_server_poll": (c_int, [c_void_p, c_uint64, i32p, i64p]),
+    "hespmv_server_stats": (c_int, [c_void_p, i64p, i64p, i64p, i64p, i64p]),
+    "hespmv_server_stop": (c_int, [c_void_p, c_int64]),
     "hespmv_profile_enable": (c_int, [c_void_p, c_int32]),
     "hespmv_profile_count": (c_int, [c_void_p, i32p]),
     "hespmv_profile_entry": (c_int, [c_void_p, c_int32, POINTER(c_char_p), i64p,

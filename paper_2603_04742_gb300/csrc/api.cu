@@ -3,8 +3,13 @@
 // and 4, decryption, and the HE primitives.
 #include <algorithm>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <set>
+#include <thread>
+#include <unordered_map>
 
 #include "kernels.h"
 
@@ -270,13 +275,10 @@ int rotate_n(hespmv_ctx *ctx, const uint64_t *src, int32_t k, uint64_t *out, siz
     return HESPMV_OK;
 }
 
-// Batched totalSum schedule for the given matrices (cached per matrix set).
-RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, int GR) {
-    std::vector<uint64_t> key;
-    key.push_back((uint64_t)GR);
-    for (size_t i = 0; i < n_inst; ++i) key.push_back(ms[i]->uid);
-    auto it = ctx->rot_plans.find(key);
-    if (it != ctx->rot_plans.end()) return it->second;
+// Batched totalSum schedule for the given matrices (host part): ops and the
+// index lists they refer to.
+void build_rotation_ops(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, int GR,
+                        RotPlan *P, std::vector<int32_t> &idx) {
     struct RC {
         int32_t k;
         std::vector<int32_t> steps;
@@ -292,9 +294,9 @@ RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const 
             if (!r.steps.empty()) rcs.push_back(std::move(r));
         }
     }
-    RotPlan *P = new RotPlan();
     P->GR = GR;
-    std::vector<int32_t> idx;
+    P->ops.clear();
+    idx.clear();
     auto push = [&](const std::vector<int32_t> &v) {
         const int64_t off = (int64_t)idx.size();
         idx.insert(idx.end(), v.begin(), v.end());
@@ -380,8 +382,20 @@ RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const 
             P->ops.push_back(o);
         }
     }
+    P->idx_bytes = idx.size() * sizeof(int32_t);
+}
+
+// The schedule with its index lists on the device, cached per matrix set.
+RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, int GR) {
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)GR);
+    for (size_t i = 0; i < n_inst; ++i) key.push_back(ms[i]->uid);
+    auto it = ctx->rot_plans.find(key);
+    if (it != ctx->rot_plans.end()) return it->second;
+    RotPlan *P = new RotPlan();
+    std::vector<int32_t> idx;
+    build_rotation_ops(ctx, n_inst, ms, GR, P, idx);
     if (!idx.empty()) {
-        P->idx_bytes = idx.size() * sizeof(int32_t);
         P->d_idx = (int32_t *)dev_alloc(ctx, P->idx_bytes);
         if (!P->d_idx || cudaMemcpy(P->d_idx, idx.data(), P->idx_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
             dev_free(ctx, P->d_idx);
@@ -393,51 +407,82 @@ RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const 
     return P;
 }
 
-// Cloud evaluation of one or more SpMVs (Algorithm 1 cloud lines + Algorithm 4).
-int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
-              const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
-              cudaStream_t st) {
+struct SpmvPrep {
+    size_t total_chunks = 0, rot_chunks = 0, G = 1, GR = 1;
+    RotPlan *rp = nullptr;
+    size_t need_bytes = 0;
+};
+
+// Per-matrix device state an evaluation reads: mask plaintexts (cached per
+// chunk height), the matrix's mask table, the Galois permutations of its
+// rotations.  May synchronise and allocate (first use of a matrix only).
+int prepare_matrix(hespmv_ctx *ctx, const hespmv_cssc *cm, cudaStream_t st) {
+    hespmv_cssc *m = const_cast<hespmv_cssc *>(cm);
+    if (m->prepared) return HESPMV_OK;
+    for (const Chunk &ch : m->plan.chunks)
+        if (!mask_plaintext(ctx, ch.h, st)) FAIL(HESPMV_E_NOMEM, "mask plaintext creation failed");
+    if (!m->plan.chunks.empty()) {
+        std::vector<const uint64_t *> tab;
+        for (const Chunk &ch : m->plan.chunks) tab.push_back(ctx->masks[ch.h]);
+        m->d_masks = (const uint64_t **)dev_alloc(ctx, tab.size() * sizeof(void *));
+        if (!m->d_masks) FAIL(HESPMV_E_NOMEM, "mask table allocation failed");
+        CK(cudaMemcpy(m->d_masks, tab.data(), tab.size() * sizeof(void *), cudaMemcpyHostToDevice));
+    }
+    for (int32_t k : m->steps)
+        for (uint32_t g : rotation_chain(ctx, k))
+            if (!galois_perm(ctx, g)) FAIL(HESPMV_E_NOMEM, "permutation upload failed");
+    m->prepared = true;
+    return HESPMV_OK;
+}
+
+// batch sizes and workspace bytes of an evaluation over the given chunk counts
+void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, size_t tune_G, SpmvPrep &pp) {
+    const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
+    pp.total_chunks = total_chunks;
+    pp.rot_chunks = rot_chunks;
+    pp.G = std::max<size_t>(1, std::min<size_t>(total_chunks, tune_G ? tune_G : 32));
+    pp.GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, c.N >= (1 << 15) ? 32 : 64));
+    const size_t prod_w = total_chunks * CT;
+    const size_t mult_w = pp.G * 3 * LN + ks_words(c, pp.G);
+    const size_t rot_w = rot_chunks ? 4 * pp.GR * CT + ks_words(c, pp.GR) : 0;
+    pp.need_bytes = (prod_w + std::max(mult_w, rot_w)) * 8;
+}
+
+// Everything an evaluation needs besides kernel launches: per-matrix state,
+// the (cached) rotation schedule, the workspace size.
+int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, SpmvPrep &pp,
+                 cudaStream_t st) {
+    const Ctx c = view(ctx);
+    size_t total = 0, rot = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        int rc = prepare_matrix(ctx, ms[i], st);
+        if (rc) return rc;
+        total += ms[i]->plan.chunks.size();
+        for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
+    }
+    spmv_sizes(c, total, rot, ctx->tune_G, pp);
+    pp.rp = nullptr;
+    if (rot) {
+        pp.rp = rotation_plan(ctx, n_inst, ms, (int)pp.GR);
+        if (!pp.rp) FAIL(HESPMV_E_NOMEM, "rotation schedule upload failed");
+    }
+    return HESPMV_OK;
+}
+
+// Cloud evaluation of one or more SpMVs (Algorithm 1 cloud lines + Algorithm 4):
+// kernel launches and memsets only, on stream st, in workspace ws.
+int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
+                 const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
+                 const SpmvPrep &pp, uint64_t *ws, cudaStream_t st) {
     const Ctx c = view(ctx);
     const int64_t N = c.N, LN = (int64_t)c.L * N, CT = 2 * LN;
-    size_t total_chunks = 0, rot_chunks = 0;
-    std::vector<int32_t> steps;
-    std::vector<uint8_t> orig;
-    for (size_t i = 0; i < n_inst; ++i) {
-        total_chunks += ms[i]->plan.chunks.size();
-        for (const Chunk &ch : ms[i]->plan.chunks) rot_chunks += ch.c > 1;
-    }
-    // masks first (synchronous, cached), and each matrix's per-chunk mask table
-    for (size_t i = 0; i < n_inst; ++i) {
-        hespmv_cssc *m = const_cast<hespmv_cssc *>(ms[i]);
-        for (const Chunk &ch : m->plan.chunks)
-            if (!mask_plaintext(ctx, ch.h, st)) FAIL(HESPMV_E_NOMEM, "mask plaintext creation failed");
-        if (!m->d_masks && !m->plan.chunks.empty()) {
-            std::vector<const uint64_t *> tab;
-            for (const Chunk &ch : m->plan.chunks) tab.push_back(ctx->masks[ch.h]);
-            m->d_masks = (const uint64_t **)dev_alloc(ctx, tab.size() * sizeof(void *));
-            if (!m->d_masks) FAIL(HESPMV_E_NOMEM, "mask table allocation failed");
-            CK(cudaMemcpy(m->d_masks, tab.data(), tab.size() * sizeof(void *), cudaMemcpyHostToDevice));
-        }
-    }
-    // batch sizes: HE-Mult groups of G chunks, rotation groups of GR chunks
-    const size_t G = std::max<size_t>(1, std::min<size_t>(total_chunks, 32));
-    const size_t GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, N >= (1 << 15) ? 32 : 64));
-    RotPlan *rp = nullptr;
-    if (rot_chunks) {
-        rp = rotation_plan(ctx, n_inst, ms, (int)GR);
-        if (!rp) FAIL(HESPMV_E_NOMEM, "rotation schedule upload failed");
-    }
-    const size_t prod_w = total_chunks * CT;
-    const size_t mult_w = G * 3 * LN + ks_words(c, G);
-    const size_t rot_w = rot_chunks ? 4 * GR * CT + ks_words(c, GR) : 0;
-    const size_t need = (prod_w + std::max(mult_w, rot_w)) * 8;
-    uint64_t *ws = workspace(ctx, need);
-    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    const size_t G = pp.G, GR = pp.GR;
+    const size_t prod_w = pp.total_chunks * CT;
     uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + G * 3 * LN;
     // 1) HE-Mult of every chunk pair, G at a time across instances
     {
         std::vector<std::pair<size_t, size_t>> all;  // (instance, chunk)
-        all.reserve(total_chunks);
+        all.reserve(pp.total_chunks);
         for (size_t i = 0; i < n_inst; ++i)
             for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
         for (size_t g0 = 0; g0 < all.size(); g0 += G) {
@@ -455,11 +500,11 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         }
     }
     // 2) totalSum: batched rotation rounds
-    if (rp) {
+    if (pp.rp) {
         uint64_t *V = dbuf, *CUR = V + GR * CT, *PB = CUR + GR * CT, *OB = PB + GR * CT;
         uint64_t *ks = OB + GR * CT;
-        const int32_t *I = rp->d_idx;
-        for (const RotOp &o : rp->ops) {
+        const int32_t *I = pp.rp->d_idx;
+        for (const RotOp &o : pp.rp->ops) {
             switch (o.kind) {
                 case RotOp::kVInit:
                     CK(op_ct_move(c, V, nullptr, prod, I + o.b, nullptr, false, o.m, st));
@@ -474,9 +519,9 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                     auto it = ctx->gk.find(o.g);
                     if (it == ctx->gk.end())
                         FAIL(HESPMV_E_INVALID, "missing Galois key for element " + std::to_string(o.g));
-                    const int32_t *perm = galois_perm(ctx, o.g);
-                    if (!perm) FAIL(HESPMV_E_NOMEM, "permutation upload failed");
-                    CK(op_ct_move(c, PB, nullptr, CUR, I + o.a, perm, false, o.m, st));
+                    auto pit = ctx->perms.find(o.g);
+                    if (pit == ctx->perms.end()) FAIL(HESPMV_E_INVALID, "missing Galois permutation");
+                    CK(op_ct_move(c, PB, nullptr, CUR, I + o.a, pit->second, false, o.m, st));
                     CK(keyswitch_n(c, PB + LN, CT, it->second, OB, PB, CT, LN, 1, o.m, ks, st));
                     CK(op_ct_move(c, CUR, I + o.a, OB, nullptr, nullptr, false, o.m, st));
                     break;
@@ -503,6 +548,54 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         }
         k0 += pl.chunks.size();
     }
+    return HESPMV_OK;
+}
+
+// Evaluate on `st`: replays a CUDA graph of the same evaluation (same
+// matrices, buffers and workspace) when one is cached, else captures one on
+// the context's capture stream; runs eagerly while profiling is on or when
+// graphs are disabled.
+int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
+              const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
+              cudaStream_t st) {
+    SpmvPrep pp;
+    int rc = spmv_prepare(ctx, n_inst, ms, pp, st);
+    if (rc) return rc;
+    uint64_t *ws = workspace(ctx, pp.need_bytes);
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    const bool profiling = ctx->prof && ctx->prof->on;
+    if (!ctx->use_graphs || profiling) return spmv_enqueue(ctx, n_inst, ms, A, X, Y, pp, ws, st);
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)(uintptr_t)ws);
+    for (size_t i = 0; i < n_inst; ++i) {
+        key.push_back(ms[i]->uid);
+        key.push_back((uint64_t)(uintptr_t)A[i]);
+        key.push_back((uint64_t)(uintptr_t)X[i]);
+        key.push_back((uint64_t)(uintptr_t)Y[i]);
+    }
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 64) {
+            for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+            ctx->graphs.clear();
+        }
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = spmv_enqueue(ctx, n_inst, ms, A, X, Y, pp, ws, ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = ctx->graphs.emplace(key, exec).first;
+    }
+    CK(cudaGraphLaunch(it->second, st));
     return HESPMV_OK;
 }
 
@@ -575,6 +668,8 @@ void hespmv_destroy(hespmv_ctx *ctx) {
         dev_free(ctx, kv.second->d_idx);
         delete kv.second;
     }
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx->prof;
     delete ctx;
 }
@@ -1154,6 +1249,12 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
     return HESPMV_OK;
 }
 
+int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable) {
+    if (!ctx) return HESPMV_E_INVALID;
+    ctx->use_graphs = enable != 0;
+    return HESPMV_OK;
+}
+
 int hespmv_profile_enable(hespmv_ctx *ctx, int32_t enable) {
     if (!ctx) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
@@ -1273,3 +1374,344 @@ extern "C" int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint
     CK(keyswitch_n(c, d, LN, key, out, nullptr, 0, 0, 0, n, scratch, (cudaStream_t)stream));
     return HESPMV_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of SpMV requests (resident keys and operands).
+namespace {
+
+typedef std::chrono::steady_clock Clock;
+
+struct ServeReq {
+    uint64_t ticket = 0;
+    const hespmv_cssc *m = nullptr;
+    const uint64_t *A = nullptr, *X = nullptr;
+    uint64_t *y = nullptr;  // null: result kept in slot scratch and dropped
+    Clock::time_point t_sub;
+};
+
+struct ServeSlot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    uint64_t *ws = nullptr;     // workspace (evaluation + dropped results)
+    size_t cap = 0;             // bytes
+    int32_t *d_idx = nullptr;   // rotation schedule arena (device)
+    int32_t *h_idx = nullptr;   // its pinned host staging
+    size_t idx_cap = 0;         // int32 entries
+    bool busy = false;
+    std::vector<ServeReq> reqs;
+    RotPlan plan;
+};
+
+}  // namespace
+
+struct hespmv_server {
+    hespmv_ctx *ctx = nullptr;
+    std::vector<ServeSlot> slots;
+    int32_t max_batch = 1;
+    std::mutex mu;       // queue, tickets, counters
+    std::mutex ctx_mu;   // context state (caches) shared by submit and the loop
+    std::condition_variable cv;
+    std::deque<ServeReq> queue;
+    std::unordered_map<uint64_t, int64_t> done;  // ticket -> latency ns (-1: failed)
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    std::thread th;
+    int64_t submitted = 0, completed = 0, batches = 0, rejected = 0, max_inflight = 0;
+    int err = HESPMV_OK;
+    std::string errmsg;
+};
+
+namespace {
+
+const size_t kServeIdxCap = 1 << 20;  // schedule entries per slot (4 MiB)
+
+size_t slot_need(const Ctx &c, const std::vector<ServeReq> &reqs, size_t tune_G) {
+    size_t total = 0, rot = 0, drop = 0;
+    for (const ServeReq &r : reqs) {
+        total += r.m->plan.chunks.size();
+        for (const Chunk &ch : r.m->plan.chunks) rot += ch.c > 1;
+        if (!r.y) drop += r.m->plan.parts.size();
+    }
+    SpmvPrep pp;
+    spmv_sizes(c, total, rot, tune_G, pp);
+    return pp.need_bytes + drop * 2 * (size_t)c.L * c.N * 8;
+}
+
+// Launch one batch on a free slot (server thread).
+int serve_launch(hespmv_server *s, ServeSlot &sl, std::vector<ServeReq> &batch) {
+    hespmv_ctx *ctx = s->ctx;
+    const Ctx c = view(ctx);
+    const size_t n = batch.size();
+    const int64_t CT = 2 * (int64_t)c.L * c.N;
+    std::vector<const hespmv_cssc *> ms(n);
+    std::vector<const uint64_t *> A(n), X(n);
+    std::vector<uint64_t *> Y(n);
+    size_t total = 0, rot = 0, drop = 0;
+    for (size_t i = 0; i < n; ++i) {
+        ms[i] = batch[i].m;
+        A[i] = batch[i].A;
+        X[i] = batch[i].X;
+        total += ms[i]->plan.chunks.size();
+        for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
+    }
+    SpmvPrep pp;
+    spmv_sizes(c, total, rot, ctx->tune_G, pp);
+    uint64_t *dropbuf = sl.ws + pp.need_bytes / 8;
+    for (size_t i = 0; i < n; ++i) {
+        if (batch[i].y) {
+            Y[i] = batch[i].y;
+        } else {
+            Y[i] = dropbuf + drop * CT;
+            drop += ms[i]->plan.parts.size();
+        }
+    }
+    if (rot) {
+        std::vector<int32_t> idx;
+        build_rotation_ops(ctx, n, ms.data(), (int)pp.GR, &sl.plan, idx);
+        if (idx.size() > sl.idx_cap) FAIL(HESPMV_E_REJECTED, "batch schedule exceeds the slot arena");
+        memcpy(sl.h_idx, idx.data(), idx.size() * sizeof(int32_t));
+        CK(cudaMemcpyAsync(sl.d_idx, sl.h_idx, idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           sl.st));
+        sl.plan.d_idx = sl.d_idx;
+        pp.rp = &sl.plan;
+    }
+    int rc = spmv_enqueue(ctx, n, ms.data(), A.data(), X.data(), Y.data(), pp, sl.ws, sl.st);
+    if (rc) return rc;
+    CK(cudaEventRecord(sl.ev, sl.st));
+    sl.reqs = std::move(batch);
+    sl.busy = true;
+    return HESPMV_OK;
+}
+
+void serve_loop(hespmv_server *s) {
+    hespmv_ctx *ctx = s->ctx;
+    cudaSetDevice(ctx->device);
+    const Ctx c = view(ctx);
+    for (;;) {
+        // harvest finished slots
+        int inflight = 0;
+        for (ServeSlot &sl : s->slots) {
+            if (!sl.busy) continue;
+            cudaError_t e = cudaEventQuery(sl.ev);
+            if (e == cudaErrorNotReady) {
+                ++inflight;
+                continue;
+            }
+            const Clock::time_point now = Clock::now();
+            std::lock_guard<std::mutex> lock(s->mu);
+            for (const ServeReq &r : sl.reqs) {
+                s->done[r.ticket] =
+                    e == cudaSuccess
+                        ? std::chrono::duration_cast<std::chrono::nanoseconds>(now - r.t_sub).count()
+                        : -1;
+                ++s->completed;
+            }
+            if (e != cudaSuccess && !s->err) {
+                s->err = HESPMV_E_CUDA;
+                s->errmsg = std::string("serving batch: ") + cudaGetErrorString(e);
+            }
+            sl.reqs.clear();
+            sl.busy = false;
+        }
+        // admit: fill every free slot from the queue (first come, first served)
+        for (ServeSlot &sl : s->slots) {
+            if (sl.busy) continue;
+            std::vector<ServeReq> batch;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                while (!s->queue.empty() && (int32_t)batch.size() < s->max_batch) {
+                    batch.push_back(s->queue.front());
+                    if (slot_need(c, batch, ctx->tune_G) > sl.cap) {
+                        batch.pop_back();
+                        break;
+                    }
+                    s->queue.pop_front();
+                }
+            }
+            if (batch.empty()) continue;
+            std::vector<ServeReq> keep = batch;
+            int rc;
+            {
+                std::lock_guard<std::mutex> clock(s->ctx_mu);
+                rc = serve_launch(s, sl, batch);
+            }
+            std::lock_guard<std::mutex> lock(s->mu);
+            if (rc) {
+                for (const ServeReq &r : keep) {
+                    s->done[r.ticket] = -1;
+                    ++s->completed;
+                }
+                if (!s->err) {
+                    s->err = rc;
+                    s->errmsg = ctx->err;
+                }
+            } else {
+                ++s->batches;
+                ++inflight;
+            }
+        }
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            s->max_inflight = std::max<int64_t>(s->max_inflight, inflight);
+            if (s->stopping && s->queue.empty() && inflight == 0) break;
+            if (s->queue.empty() || inflight == (int)s->slots.size())
+                s->cv.wait_for(lock, std::chrono::microseconds(inflight ? 20 : 200));
+        }
+    }
+}
+
+void server_release(hespmv_server *s) {
+    for (ServeSlot &sl : s->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+        dev_free(s->ctx, sl.ws);
+        dev_free(s->ctx, sl.d_idx);
+        if (sl.h_idx) cudaFreeHost(sl.h_idx);
+    }
+    s->slots.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int hespmv_server_start(hespmv_ctx *ctx, int32_t slots, size_t mem_budget_bytes, int32_t max_batch,
+                        hespmv_server **out) {
+    if (!ctx || !out || slots < 1 || slots > 16 || max_batch < 1 || mem_budget_bytes == 0)
+        return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    DeviceGuard g(ctx->device);
+    hespmv_server *s = new hespmv_server();
+    s->ctx = ctx;
+    s->max_batch = max_batch;
+    s->slots.resize(slots);
+    const size_t cap = mem_budget_bytes / slots;
+    for (ServeSlot &sl : s->slots) {
+        sl.cap = cap;
+        sl.idx_cap = kServeIdxCap;
+        bool ok = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaMallocHost((void **)&sl.h_idx, sl.idx_cap * sizeof(int32_t)) == cudaSuccess;
+        sl.ws = ok ? (uint64_t *)dev_alloc(ctx, cap) : nullptr;
+        sl.d_idx = sl.ws ? (int32_t *)dev_alloc(ctx, sl.idx_cap * sizeof(int32_t)) : nullptr;
+        if (!sl.d_idx) {
+            server_release(s);
+            delete s;
+            FAIL(HESPMV_E_NOMEM, "serving slot allocation failed");
+        }
+    }
+    s->th = std::thread(serve_loop, s);
+    *out = s;
+    return HESPMV_OK;
+}
+
+int hespmv_server_submit(hespmv_server *s, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                         const hespmv_ctbatch *X, hespmv_ctbatch *y, uint64_t *ticket) {
+    if (!s || !m || !A || !X || !ticket) return HESPMV_E_INVALID;
+    hespmv_ctx *ctx = s->ctx;
+    const size_t nc = m->plan.chunks.size();
+    if (A->n < nc || X->n < nc || (y && y->n < m->plan.parts.size())) return HESPMV_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stopping) return HESPMV_E_INVALID;
+        if (s->err) return s->err;
+    }
+    if (!m->prepared) {
+        // first request of a matrix: make its masks and tables resident (the
+        // caller's thread; the serving thread never allocates)
+        std::lock_guard<std::mutex> lock(s->ctx_mu);
+        DeviceGuard g(ctx->device);
+        int rc = prepare_matrix(ctx, m, nullptr);
+        if (rc) return rc;
+    }
+    ServeReq r;
+    r.m = m;
+    r.A = A->data;
+    r.X = X->data;
+    r.y = y ? y->data : nullptr;
+    const Ctx c = view(ctx);
+    std::vector<ServeReq> one{r};
+    if (slot_need(c, one, ctx->tune_G) > s->slots[0].cap) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        ++s->rejected;
+        ctx->err = "request needs more device memory than a serving slot holds";
+        return HESPMV_E_REJECTED;
+    }
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        r.ticket = s->next_ticket++;
+        r.t_sub = Clock::now();
+        s->queue.push_back(r);
+        ++s->submitted;
+        *ticket = r.ticket;
+    }
+    s->cv.notify_one();
+    return HESPMV_OK;
+}
+
+int hespmv_server_poll(hespmv_server *s, uint64_t ticket, int32_t *done, int64_t *latency_ns) {
+    if (!s || !done) return HESPMV_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) {
+        *done = 0;
+        if (latency_ns) *latency_ns = 0;
+        return HESPMV_OK;
+    }
+    *done = it->second >= 0 ? 1 : -1;
+    if (latency_ns) *latency_ns = it->second;
+    return it->second >= 0 ? HESPMV_OK : (s->err ? s->err : HESPMV_E_CUDA);
+}
+
+int hespmv_server_stats(hespmv_server *s, int64_t *submitted, int64_t *completed, int64_t *batches,
+                        int64_t *rejected, int64_t *max_inflight) {
+    if (!s) return HESPMV_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (submitted) *submitted = s->submitted;
+    if (completed) *completed = s->completed;
+    if (batches) *batches = s->batches;
+    if (rejected) *rejected = s->rejected;
+    if (max_inflight) *max_inflight = s->max_inflight;
+    return HESPMV_OK;
+}
+
+int hespmv_server_stop(hespmv_server *s, int64_t timeout_ms) {
+    if (!s) return HESPMV_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stopping = true;
+    }
+    s->cv.notify_one();
+    // wait for the queue to drain and the last batches to finish, bounded
+    const Clock::time_point t0 = Clock::now();
+    bool timed_out = false;
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            if (s->completed >= s->submitted) break;
+        }
+        if (timeout_ms >= 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() > timeout_ms) {
+            timed_out = true;
+            break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    int rc = HESPMV_OK;
+    if (timed_out) {
+        // the loop still owns in-flight work: keep it running until it drains
+        s->th.join();
+        rc = HESPMV_E_TIMEOUT;
+    } else {
+        s->th.join();
+    }
+    DeviceGuard g(s->ctx->device);
+    const int err = s->err;
+    server_release(s);
+    delete s;
+    return rc ? rc : err;
+}
+
+}  // extern "C"

@@ -183,6 +183,11 @@ struct hespmv_ctx {
     // rotation schedules, keyed by the matrices' ids
     std::map<std::vector<uint64_t>, hespmv::RotPlan *> rot_plans;
     uint64_t next_uid = 1;
+    // CUDA graphs of evaluations, keyed by workspace, matrices and buffers
+    bool use_graphs = true;
+    std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
+    size_t tune_G = 0;  // HE-Mult batch size (0: default)
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;
@@ -195,6 +200,7 @@ struct hespmv_cssc {
     int64_t n_rot = 0, n_ks = 0;
     const uint64_t **d_masks = nullptr;  // device: mask plaintext of each chunk
     uint64_t uid = 0;                    // unique per context (schedule cache key)
+    bool prepared = false;               // masks, mask table, permutations resident
 };
 
 struct hespmv_ctbatch {

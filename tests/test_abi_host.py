@@ -147,3 +147,11 @@ def test_host_only_context_refuses_device_calls():
     with pytest.raises(B.HespmvError) as e:
         ctx.keygen(1)
     assert e.value.code == B.HESPMV_E_INVALID
+
+
+def test_server_needs_a_device_context():
+    from paper_2603_04742_gb300.api import Server
+    ctx = host_ctx("c1")
+    with pytest.raises(B.HespmvError) as e:
+        Server(ctx, slots=1, mem_budget_bytes=1 << 20, max_batch=1)
+    assert e.value.code == B.HESPMV_E_INVALID

@@ -315,3 +315,29 @@ def test_spmv_edge_cases():
     y = ctx.spmv(m, ca, cx)
     assert list(ctx.decrypt(m, y)) == [0, 0, 0, 0]
     assert not np.any(y.download())
+
+
+def test_graph_replay_matches_eager():
+    """Evaluations replayed from a CUDA graph equal eager launches, also when
+    the input ciphertexts in the same buffers change between replays."""
+    logn, L, K, dnum, t = synth.RING["c1"]
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t)
+    ctx.keygen(4)
+    A, x = synth.small_matrix(12, 400, 300, 2500)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=1)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=2)
+    ctx.set_graphs(False)
+    y_eager = ctx.spmv(m, ca, cx).download()
+    ctx.set_graphs(True)
+    y = ctx.spmv(m, ca, cx)
+    for _ in range(3):
+        ctx.spmv(m, ca, cx, y=y)
+        assert np.array_equal(y.download(), y_eager)
+    # new inputs in the same device buffers: the replay reads them
+    x2 = (x * 3 + 1) % 7 - 3
+    cx2 = ctx.encrypt(m, B.HESPMV_VECTOR, x=x2, seed=9)
+    cx.upload(cx2.download())
+    ctx.spmv(m, ca, cx, y=y)
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x2))
