@@ -262,12 +262,12 @@ int hespmv_server_stop(hespmv_server *s, int64_t timeout_ms);
 
 /* -------------------------------------------------- HE primitives (device) */
 /* All pointers below are device addresses of n whole ciphertexts (or
- * polynomials where stated); in-place use (out == in) is allowed except
- * where noted.  Enqueued on stream. */
+ * polynomials where stated), 16-byte aligned (E_INVALID otherwise); in-place
+ * use (out == in) is allowed except where noted.  Enqueued on stream. */
 
 /* Forward / inverse negacyclic NTT of n_items x n_limbs polynomials stored
- * back to back; limb k of each item uses modulus index prime0 + k (0..L-1 =
- * Q, L..L+K-1 = P, L+K = t). */
+ * back to back (16-byte aligned, residues in [0, q)); limb k of each item uses
+ * modulus index prime0 + k (0..L-1 = Q, L..L+K-1 = P, L+K = t). */
 int hespmv_ntt_forward(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,
                        int32_t n_items, void *stream);
 int hespmv_ntt_inverse(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t n_limbs,

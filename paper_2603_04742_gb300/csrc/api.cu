@@ -200,6 +200,9 @@ int make_ksk(hespmv_ctx *ctx, uint64_t seed, uint64_t kid, const uint64_t *sp, u
 
 int check_ctx(hespmv_ctx *ctx) { return ctx ? HESPMV_OK : HESPMV_E_INVALID; }
 
+// device buffers handed to the key switch are read with 16-byte vector loads
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
 const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
     auto it = ctx->masks.find(r);
     if (it != ctx->masks.end()) return it->second;
@@ -487,12 +490,19 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
             for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
         for (size_t g0 = 0; g0 < all.size(); g0 += G) {
             const size_t gn = std::min(G, all.size() - g0);
+            const size_t i = all[g0].first, k = all[g0].second;
+            if (ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
+                // one matrix's consecutive chunks: tensor product fused into the key switch
+                CK(relin_tensor_fused(c, A[i] + k * CT, X[i] + k * CT, ctx->rlk, prod + g0 * CT, gn,
+                                      scr, st));
+                continue;
+            }
             size_t s = 0;
             while (s < gn) {  // tensor over runs of one instance's consecutive chunks
-                const size_t i = all[g0 + s].first, k = all[g0 + s].second;
+                const size_t ii = all[g0 + s].first, kk = all[g0 + s].second;
                 size_t run = 1;
-                while (s + run < gn && all[g0 + s + run].first == i) ++run;
-                CK(op_tensor(c, A[i] + k * CT, X[i] + k * CT, dbuf + s * 3 * LN, run, st));
+                while (s + run < gn && all[g0 + s + run].first == ii) ++run;
+                CK(op_tensor(c, A[ii] + kk * CT, X[ii] + kk * CT, dbuf + s * 3 * LN, run, st));
                 s += run;
             }
             CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + g0 * CT, dbuf, 3 * LN, LN, 3,
@@ -1140,6 +1150,7 @@ int hespmv_ntt_forward(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t 
     if (!ctx || !data || prime0 < 0 || n_limbs < 1 || prime0 + n_limbs > ctx->h.L + ctx->h.K + 1)
         return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16(data)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     CK(launch_ntt(view(ctx), data, prime0, n_limbs, n_items, (int64_t)n_limbs * ctx->h.N, false,
                   (cudaStream_t)stream));
@@ -1151,6 +1162,7 @@ int hespmv_ntt_inverse(hespmv_ctx *ctx, uint64_t *data, int32_t prime0, int32_t 
     if (!ctx || !data || prime0 < 0 || n_limbs < 1 || prime0 + n_limbs > ctx->h.L + ctx->h.K + 1)
         return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16(data)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     CK(launch_ntt(view(ctx), data, prime0, n_limbs, n_items, (int64_t)n_limbs * ctx->h.N, true,
                   (cudaStream_t)stream));
@@ -1179,6 +1191,7 @@ int hespmv_he_relin(hespmv_ctx *ctx, const uint64_t *d, uint64_t *out, size_t n,
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
+    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N;
@@ -1194,6 +1207,7 @@ int hespmv_he_mult(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64
     if (!ctx || !a || !b || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
+    if (!aligned16(a)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N;
@@ -1210,6 +1224,7 @@ int hespmv_he_rotate(hespmv_ctx *ctx, const uint64_t *ct, int32_t k, uint64_t *o
     if (!ctx || !ct || !out || ct == out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
+    if (!aligned16(ct)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t CT = 2 * (int64_t)c.L * c.N;
@@ -1234,6 +1249,7 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
+    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const uint64_t *key = ctx->rlk;
     if (galois_elt) {
@@ -1347,6 +1363,7 @@ extern "C" int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint
                                         uint64_t *out, size_t n, void *stream) {
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     DeviceGuard g(ctx->device);
     const uint64_t *key = ctx->rlk;

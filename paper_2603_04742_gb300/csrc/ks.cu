@@ -5,11 +5,14 @@
 //   out_c = (sum_j ModUp_j(d) * key_j,c  -  delta_c) * P^-1  (+ addend),
 //   delta_c = t * Conv_{P->Q}([x_c * t^-1]_P),  x_c the P-limbs of the sum:
 //  1. inverse NTT of d, row pass                         (d -> dc)
+//     (with HE-Mult fused in, d = a1 * b1 is formed here, in step 4 and the
+//     addend (a0 b0, a0 b1 + a1 b0) in step 7: no tensor in memory)
 //  2. inverse NTT column pass, N^-1 * Qhat^-1 folded in  (dc -> z)
 //  3. ModUp + forward column pass: one CTA raises a digit's z columns to
 //     every other prime and transforms them                 (z -> ext)
-//  4. forward row pass + inner product with the key: the digit's own primes
-//     use d directly; 128-bit sums, one Montgomery reduction (ext -> acc)
+//  4. forward row pass of the raised limbs, in place             (ext)
+//     and the inner product with the key: the digit's own primes use d
+//     directly; 128-bit sums, one Montgomery reduction           (-> acc)
 //  5. inverse NTT of acc's P limbs, t^-1 * Phat^-1 * N^-1 folded in (-> y)
 //  6. ModDown conversion (t folded in) + forward column pass   (y -> dh)
 //  7. forward row pass of delta + (acc - delta) * P^-1 + addend  (-> out)
@@ -30,6 +33,22 @@ struct KsArgs {
     const uint64_t *pinv;      // [L][2]
     int log2n, L, K, dnum, alpha;
 };
+
+// Input of a key switch: d (NTT domain, item stride ds), or, fused with the
+// tensor product of HE-Mult, d = a1 * b1 for ciphertexts a = ta + i*ts,
+// b = tb + i*ts, whose (a0 b0, a0 b1 + a1 b0) is then the addend.
+struct KsSrc {
+    const uint64_t *d;
+    int64_t ds;
+    const uint64_t *ta, *tb;
+    int64_t ts;
+};
+
+__device__ __forceinline__ uint64_t src_d2(const KsSrc &s, const ModConst &mc, int64_t item,
+                                           int64_t off, int64_t LN) {
+    if (s.d) return s.d[item * s.ds + off];
+    return mul_mod(s.ta[item * s.ts + LN + off], s.tb[item * s.ts + LN + off], mc);
+}
 
 __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
     const uint64_t m = lo * qneg;
@@ -52,9 +71,35 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows(KsArgs a, const ui
     const uint64_t *in = src + item * ss + (int64_t)k * N + (int64_t)row * M;
     uint64_t *out = dst + item * ds + (int64_t)k * N + (int64_t)row * M;
     uint64_t v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = in[Pass<LR>::last(j, e)];
+    load8(v, in + 8 * j);  // = Pass<LR>::last(j, e)
     inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, itw, q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
+}
+
+// first inverse row pass of the key switch: from the input (or a1 * b1)
+template <int LR>
+__global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSrc s, uint64_t *dst) {
+    constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
+    __shared__ uint64_t sm[kRowTileWords];
+    const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L;
+    const int item = blockIdx.y / L, k = blockIdx.y - item * L;
+    const ModConst mc = a.mc[k];
+    const TwPair *itw = (const TwPair *)(a.tw + (int64_t)k * 4 * N + 2 * N);
+    const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
+    const int64_t off = (int64_t)k * N + (int64_t)row * M, LN = (int64_t)L * N;
+    uint64_t v[8];
+    if (s.d) {
+        load8(v, s.d + item * s.ds + off + 8 * j);
+    } else {  // d2 = a1 * b1
+        uint64_t x[8], y[8];
+        load8(x, s.ta + item * s.ts + LN + off + 8 * j);
+        load8(y, s.tb + item * s.ts + LN + off + 8 * j);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = mul_mod(x[e], y[e], mc);
+    }
+    inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, itw, mc.q);
+    uint64_t *out = dst + (int64_t)item * LN + off;
 #pragma unroll
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
 }
@@ -129,66 +174,68 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_modup_cols(KsArgs a, const u
     }
 }
 
-// Forward row pass of every digit's limb l, multiplied with the key and
-// summed: acc [n][2][L+K][N] in [0, q).  Digit limbs of d itself are used as
-// they are (already in the NTT domain).
+// Forward row pass, in place, of every raised limb: ext[item][jd][l] for the
+// primes l outside digit jd (output unreduced, < 32q).
 template <int LR>
-__global__ __launch_bounds__(kNttThreads) void k_ks_rows_inner(KsArgs a, const uint64_t *d,
-                                                               int64_t ds, const uint64_t *ext,
-                                                               const uint64_t *key,
-                                                               uint64_t *acc) {
+__global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t *ext) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
     __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, LK = a.L + a.K;
-    const int item = blockIdx.y / LK, l = blockIdx.y - item * LK;
-    const ModConst mc = a.mc[l];
-    const uint64_t q = mc.q;
+    const int l = blockIdx.y % LK, jd = (blockIdx.y / LK) % a.dnum;
+    const int64_t item = blockIdx.y / (LK * a.dnum);
+    const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
+    if (l >= i0 && l < i1) return;  // the digit's own primes keep d itself
+    const uint64_t q = a.mc[l].q;
     const TwPair *tw = (const TwPair *)(a.tw + (int64_t)l * 4 * N);
     const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
-    const int64_t rofs = (int64_t)row * M;
-    uint64_t s0[8], s1[8];
+    uint64_t *x = ext + ((item * a.dnum + jd) * LK + l) * N + (int64_t)row * M;
+    uint64_t v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) s0[e] = s1[e] = 0;
+    for (int e = 0; e < 8; ++e) v[e] = x[Pass<LR>::first(j, e)];
+    fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
+    store8(x + 8 * j, v);
+}
+
+// Inner product with the key: acc[item][c][l] = sum_j e_j * key[j][c][l]
+// with e_j = ext[item][j][l] (< 32q) or, on digit j's own primes, d itself.
+// Keys are in Montgomery form, so the 128-bit sum needs one reduction.
+// Items vary fastest so a key limb stays in L2 while every item uses it.
+__global__ __launch_bounds__(256) void k_ks_mac(KsArgs a, KsSrc s, const uint64_t *ext,
+                                                const uint64_t *key, uint64_t *acc, int n) {
+    // grid: x = coefficient pairs, y = l * n + item
+    const int N = 1 << a.log2n, LK = a.L + a.K;
+    const int l = blockIdx.y / n;
+    const int64_t item = blockIdx.y - (int64_t)l * n;
+    const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (k >= N) return;
+    const ModConst mc = a.mc[l];
+    uint64_t h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
     for (int jd = 0; jd < a.dnum; ++jd) {
         const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
-        // key words of this digit, fetched before the transform
-        const uint64_t *k0 = key + ((int64_t)(2 * jd) * LK + l) * N + rofs;
-        const uint64_t *k1 = k0 + (int64_t)LK * N;
-        uint64_t w0[8], w1[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            w0[e] = k0[Pass<LR>::last(j, e)];
-            w1[e] = k1[Pass<LR>::last(j, e)];
-        }
-        uint64_t v[8];
+        ulonglong2 e;
         if (l >= i0 && l < i1) {
-            const uint64_t *src = d + item * ds + (int64_t)l * N + rofs;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = src[Pass<LR>::last(j, e)];
+            if (s.d) {
+                e = *(const ulonglong2 *)(s.d + item * s.ds + (int64_t)l * N + k);
+            } else {
+                const int64_t o = item * s.ts + ((int64_t)a.L + l) * N + k;
+                const ulonglong2 x = *(const ulonglong2 *)(s.ta + o), y = *(const ulonglong2 *)(s.tb + o);
+                e = make_ulonglong2(mul_mod(x.x, y.x, mc), mul_mod(x.y, y.y, mc));
+            }
         } else {
-            const uint64_t *src = ext + (((int64_t)item * a.dnum + jd) * LK + l) * N + rofs;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = src[Pass<LR>::first(j, e)];
-            fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
+            e = *(const ulonglong2 *)(ext + ((item * a.dnum + jd) * LK + l) * N + k);
         }
-        // v * (w * 2^64) * 2^-64 = v * w: one Montgomery reduction per
-        // product (v < 32q unreduced, so v w < q 2^64); sums kept in [0, q)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            uint64_t r = redc(__umul64hi(v[e], w0[e]), v[e] * w0[e], q, mc.qneg) + s0[e];
-            s0[e] = r >= q ? r - q : r;
-            r = redc(__umul64hi(v[e], w1[e]), v[e] * w1[e], q, mc.qneg) + s1[e];
-            s1[e] = r >= q ? r - q : r;
-        }
+        const ulonglong2 w0 = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd) * LK + l) * N + k));
+        const ulonglong2 w1 = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd + 1) * LK + l) * N + k));
+        uint64_t p;
+        p = e.x * w0.x; l0a += p; h0a += __umul64hi(e.x, w0.x) + (l0a < p);
+        p = e.y * w0.y; l0b += p; h0b += __umul64hi(e.y, w0.y) + (l0b < p);
+        p = e.x * w1.x; l1a += p; h1a += __umul64hi(e.x, w1.x) + (l1a < p);
+        p = e.y * w1.y; l1b += p; h1b += __umul64hi(e.y, w1.y) + (l1b < p);
     }
-    uint64_t *o0 = acc + ((int64_t)item * 2 * LK + l) * N + rofs;
+    uint64_t *o0 = acc + (item * 2 * LK + l) * N + k;
     uint64_t *o1 = o0 + (int64_t)LK * N;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int p = Pass<LR>::last(j, e);
-        o0[p] = s0[e];
-        o1[p] = s1[e];
-    }
+    *(ulonglong2 *)o0 = make_ulonglong2(redc(h0a, l0a, mc.q, mc.qneg), redc(h0b, l0b, mc.q, mc.qneg));
+    *(ulonglong2 *)o1 = make_ulonglong2(redc(h1a, l1a, mc.q, mc.qneg), redc(h1b, l1b, mc.q, mc.qneg));
 }
 
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
@@ -242,13 +289,14 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const u
                                                                const uint64_t *dh,
                                                                const uint64_t *add, int64_t add_is,
                                                                int64_t add_cs, int add_mask,
-                                                               uint64_t *out) {
+                                                               KsSrc s, uint64_t *out) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
     __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L, LK = L + a.K;
     const int ic = blockIdx.y / L, i = blockIdx.y - ic * L;
     const int item = ic >> 1, c = ic & 1;
-    const uint64_t q = a.mc[i].q;
+    const ModConst mc = a.mc[i];
+    const uint64_t q = mc.q;
     const TwPair *tw = (const TwPair *)(a.tw + (int64_t)i * 4 * N);
     const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
     const int64_t rofs = (int64_t)row * M;
@@ -258,11 +306,29 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const u
     const uint64_t *ad = has_add ? add + item * add_is + c * add_cs + (int64_t)i * N + rofs : nullptr;
     // operands of the epilogue, fetched before the transform
     uint64_t xa[8], xd[8];
+    const bool tensor = s.ta != nullptr;
+    const int64_t LN = (int64_t)L * N, toff = item * s.ts + (int64_t)i * N + rofs;
+    load8(xa, x + 8 * j);
+    if (tensor) {  // d0 = a0 b0, d1 = a0 b1 + a1 b0
+        uint64_t a0[8], b0[8];
+        load8(a0, s.ta + toff + 8 * j);
+        load8(b0, s.tb + toff + 8 * j);
+        if (c == 0) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int p = Pass<LR>::last(j, e);
-        xa[e] = x[p];
-        xd[e] = has_add ? ad[p] : 0;
+            for (int e = 0; e < 8; ++e) xd[e] = mul_mod(a0[e], b0[e], mc);
+        } else {
+            uint64_t a1[8], b1[8];
+            load8(a1, s.ta + toff + LN + 8 * j);
+            load8(b1, s.tb + toff + LN + 8 * j);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                xd[e] = add_mod(mul_mod(a0[e], b1[e], mc), mul_mod(a1[e], b0[e], mc), q);
+        }
+    } else if (has_add) {
+        load8(xd, ad + 8 * j);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xd[e] = 0;
     }
     uint64_t v[8];
 #pragma unroll
@@ -272,18 +338,17 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const u
     uint64_t *o = out + ((int64_t)ic * L + i) * N + rofs;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int p = Pass<LR>::last(j, e);
         // delta < 32q unreduced: (acc + 32q - delta) * P^-1, fully reduced
-        uint64_t r = mul_shoup(xa[e] + 32 * q - v[e], w, ws, q);
-        o[p] = add_mod(r, xd[e], q);
+        const uint64_t r = mul_shoup(xa[e] + 32 * q - v[e], w, ws, q);
+        v[e] = add_mod(r, xd[e], q);
     }
+    store8(o + 8 * j, v);
 }
 
 template <int LC, int LR>
-static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const uint64_t *d, int64_t ds,
-                            const uint64_t *key, uint64_t *out, const uint64_t *add, int64_t add_is,
-                            int64_t add_cs, int add_mask, int n, uint64_t *scratch,
-                            cudaStream_t st) {
+static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
+                            uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
+                            int add_mask, int n, uint64_t *scratch, cudaStream_t st) {
     const int64_t N = c.N, L = c.L, K = c.K, LK = L + K;
     uint64_t *z = scratch;
     uint64_t *ext = z + n * L * N;
@@ -292,7 +357,7 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const uint64_t *d, in
     const int gc = (int)((N >> LC) / (kNttTile >> LC)), gr = (int)((N >> LR) / (kNttTile >> LR));
     int r;
     r = prof_begin(c, "k_ks_intt_rows", st);
-    k_ks_intt_rows<LR><<<dim3(gr, n * L), kNttThreads, 0, st>>>(a, d, ds, z, L * N, (int)L, 0);
+    k_ks_intt_rows_src<LR><<<dim3(gr, n * L), kNttThreads, 0, st>>>(a, s, z);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_intt_cols", st);
     k_ks_intt_cols<LC><<<dim3(gc, n * L), kNttThreads, 0, st>>>(a, z, L * N, (int)L, 0, a.zc);
@@ -300,8 +365,11 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const uint64_t *d, in
     r = prof_begin(c, "k_ks_modup_cols", st);
     k_ks_modup_cols<LC><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
     prof_end(c, r, st);
-    r = prof_begin(c, "k_ks_rows_inner", st);
-    k_ks_rows_inner<LR><<<dim3(gr, n * LK), kNttThreads, 0, st>>>(a, d, ds, ext, key, acc);
+    r = prof_begin(c, "k_ks_rows_fwd", st);
+    k_ks_rows_fwd<LR><<<dim3(gr, n * c.dnum * LK), kNttThreads, 0, st>>>(a, ext);
+    prof_end(c, r, st);
+    r = prof_begin(c, "k_ks_mac", st);
+    k_ks_mac<<<dim3((unsigned)((N / 2 + 255) / 256), (unsigned)(n * LK)), 256, 0, st>>>(a, s, ext, key, acc, n);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_intt_rows", st);
     k_ks_intt_rows<LR><<<dim3(gr, n * 2 * K), kNttThreads, 0, st>>>(a, acc + L * N, LK * N,
@@ -317,7 +385,7 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const uint64_t *d, in
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_final", st);
     k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, add, add_is,
-                                                                      add_cs, add_mask, out);
+                                                                      add_cs, add_mask, s, out);
     prof_end(c, r, st);
     return cudaGetLastError();
 }
@@ -326,9 +394,20 @@ bool ks_fused_supported(const Ctx &c) {
     return c.log2n >= 11 && c.log2n <= 15 && c.alpha <= 4 && c.K <= 4;
 }
 
-cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
-                            uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
-                            int add_mask, size_t n, uint64_t *scratch, cudaStream_t st) {
+static cudaError_t ks_dispatch(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
+                               uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
+                               int add_mask, int m, uint64_t *scratch, cudaStream_t st) {
+    switch (c.log2n) {
+        case 15: return ks_fused<7, 8>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        case 14: return ks_fused<7, 7>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        case 13: return ks_fused<6, 7>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        case 12: return ks_fused<6, 6>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        case 11: return ks_fused<5, 6>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static KsArgs ks_args(const Ctx &c) {
     const hespmv_ctx *h = c.c;
     KsArgs a;
     a.mc = h->d.mc;
@@ -343,21 +422,40 @@ cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, c
     a.K = c.K;
     a.dnum = c.dnum;
     a.alpha = c.alpha;
-    // grid.y of the widest launch is n * 2 * max(L, K) (and n * (L+K)); keep it in range
-    const size_t per = 2 * (size_t)(c.L + c.K);
-    const size_t maxn = 65535 / per;
+    return a;
+}
+
+// grid.y of the widest launch is n * dnum * (L+K): items per launch
+static size_t ks_max_items(const Ctx &c) {
+    return 65535 / ((size_t)std::max(2, c.dnum) * (c.L + c.K));
+}
+
+cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
+                            uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
+                            int add_mask, size_t n, uint64_t *scratch, cudaStream_t st) {
+    const KsArgs a = ks_args(c);
+    const size_t maxn = ks_max_items(c);
     for (size_t i0 = 0; i0 < n; i0 += maxn) {
         const int m = (int)std::min(maxn, n - i0);
-        const uint64_t *ad = add ? add + i0 * add_is : nullptr;
-        cudaError_t e;
-        switch (c.log2n) {
-            case 15: e = ks_fused<7, 8>(c, a, d + i0 * d_stride, d_stride, key, out + i0 * 2 * c.L * c.N, ad, add_is, add_cs, add_mask, m, scratch, st); break;
-            case 14: e = ks_fused<7, 7>(c, a, d + i0 * d_stride, d_stride, key, out + i0 * 2 * c.L * c.N, ad, add_is, add_cs, add_mask, m, scratch, st); break;
-            case 13: e = ks_fused<6, 7>(c, a, d + i0 * d_stride, d_stride, key, out + i0 * 2 * c.L * c.N, ad, add_is, add_cs, add_mask, m, scratch, st); break;
-            case 12: e = ks_fused<6, 6>(c, a, d + i0 * d_stride, d_stride, key, out + i0 * 2 * c.L * c.N, ad, add_is, add_cs, add_mask, m, scratch, st); break;
-            case 11: e = ks_fused<5, 6>(c, a, d + i0 * d_stride, d_stride, key, out + i0 * 2 * c.L * c.N, ad, add_is, add_cs, add_mask, m, scratch, st); break;
-            default: return cudaErrorInvalidValue;
-        }
+        KsSrc s{d + i0 * d_stride, d_stride, nullptr, nullptr, 0};
+        cudaError_t e = ks_dispatch(c, a, s, key, out + i0 * 2 * c.L * c.N,
+                                    add ? add + i0 * add_is : nullptr, add_is, add_cs, add_mask, m,
+                                    scratch, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *B,
+                               const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
+                               cudaStream_t st) {
+    const KsArgs a = ks_args(c);
+    const int64_t CT = 2 * (int64_t)c.L * c.N;
+    const size_t maxn = ks_max_items(c);
+    for (size_t i0 = 0; i0 < n; i0 += maxn) {
+        const int m = (int)std::min(maxn, n - i0);
+        KsSrc s{nullptr, 0, A + i0 * CT, B + i0 * CT, CT};
+        cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, nullptr, 0, 0, 0, m, scratch, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -262,10 +262,12 @@ __global__ __launch_bounds__(kNttThreads) void k_fntt_rows(NttArgs a) {
         for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))];
         fwd_round<LOGM, 3 + R1, R2>(v, j, twb, tw, q);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) base[elem_pos<LOGM, 3 + R1, R2>(j, e)] = reduce_full(v[e], q, one_s);
+        for (int e = 0; e < 8; ++e) v[e] = reduce_full(v[e], q, one_s);
+        store8(base + 8 * j, v);  // = elem_pos<LOGM, 3 + R1, R2>(j, e)
     } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) base[elem_pos<LOGM, 3, R1>(j, e)] = reduce_full(v[e], q, one_s);
+        for (int e = 0; e < 8; ++e) v[e] = reduce_full(v[e], q, one_s);
+        store8(base + 8 * j, v);  // = elem_pos<LOGM, 3, R1>(j, e)
     }
 }
 
@@ -288,8 +290,7 @@ __global__ __launch_bounds__(kNttThreads) void k_intt_rows(NttArgs a) {
     const RowIdx<M> si{rr};
     uint64_t v[8];
     if constexpr (R2 > 0) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = base[elem_pos<LOGM, 3 + R1, R2>(j, e)];
+        load8(v, base + 8 * j);  // = elem_pos<LOGM, 3 + R1, R2>(j, e)
         inv_round<LOGM, 3 + R1, R2>(v, j, twb, itw, q);
 #pragma unroll
         for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))] = v[e];
@@ -297,8 +298,7 @@ __global__ __launch_bounds__(kNttThreads) void k_intt_rows(NttArgs a) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3, R1>(j, e))];
     } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = base[elem_pos<LOGM, 3, R1>(j, e)];
+        load8(v, base + 8 * j);  // = elem_pos<LOGM, 3, R1>(j, e)
     }
     inv_round<LOGM, 3, R1>(v, j, twb, itw, q);
     __syncthreads();

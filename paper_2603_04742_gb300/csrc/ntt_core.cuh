@@ -156,6 +156,23 @@ struct Sched {
 
 namespace hespmv {
 
+// In the last round of every pass, thread j holds the 8 consecutive
+// positions 8j .. 8j+7: row passes move them with four 16-byte accesses.
+__device__ __forceinline__ void load8(uint64_t (&v)[8], const uint64_t *p) {
+    const ulonglong2 *s = (const ulonglong2 *)p;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const ulonglong2 t = s[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ void store8(uint64_t *p, const uint64_t (&v)[8]) {
+    ulonglong2 *d = (ulonglong2 *)p;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+}
+
 // Positions of a thread's 8 values in the first and last forward rounds.
 template <int LOGM>
 struct Pass {
