@@ -38,12 +38,17 @@ CONFIGS = {
     "c4": "64 square matrices, n log-U[256,8192], density log-U[5e-4,2e-2], integers [-15,15]; "
           "BGV N=2^14, 5+1 primes, dnum 5, t=1146881; batched evaluation vs plain calls",
 }
-# dense 32-bit multiply-adds per SM per clock, SM count and maximum SM clock
-# of a GB300; a Shoup modular product needs 10 32x32-bit partial products
-IMAD_PER_SM_CLK = 64
+# ALU roofline of a 64-bit modular product: a Shoup product needs 10 32x32-bit
+# partial products (3 + 3 for two low halves, 4 for a high half), all on the
+# heavy multiply pipe, which completes 32 of them per clock per SM; 152 SMs at
+# the 2070 MHz maximum clock.  (A microbenchmark of independent Shoup chains
+# reaches 1.01 T/s with that pipe 94% busy.)
+IMAD_PER_SM_CLK = 32
 SMS = 152
 SM_MAX_MHZ = 2070.0
 IMAD_PER_MULMOD = 10
+KS_SOURCES = ["paper_2603_04742_gb300/csrc/ks.cu", "paper_2603_04742_gb300/csrc/ntt_core.cuh",
+              "paper_2603_04742_gb300/csrc/modarith.cuh"]
 
 
 def parse():
@@ -72,6 +77,36 @@ def load_workload(name):
         A.vals = synth.quantize(A.vals)
         x = synth.quantize(x)
     return A, x, synth.RING[name]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KS_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel, config):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic_%s.md" % config)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = [ln for ln in lines if ln.startswith("source hash:")]
+    if not src or src[0].split(":", 1)[1].strip() != kernel_source_hash():
+        return None
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel:
+            try:
+                return float(cells[1]) + float(cells[2])
+            except ValueError:
+                return None
+    return None
 
 
 def measured_peaks():
@@ -250,7 +285,7 @@ def time_steps(fn, stream, steps, barrier):
     return e0.elapsed_time(e1) / steps
 
 
-def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot):
+def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"):
     peaks, peak_kind = measured_peaks()
     kernels = {}
     total_ms = sum(v[1] for v in prof.values())
@@ -270,13 +305,15 @@ def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot):
     if t_alu >= t_hbm:
         ach = mm_launch / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tmulmod/s",
-                "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": top,
-                "peak_source": "derived: %d SMs x %d IMAD/clk x %.0f MHz / %d IMAD per mulmod"
-                               % (SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD)}
+                "frac": ach / (alu_peak / 1e12), "kernel": top,
+                "traffic": measured_traffic(top, config),
+                "peak_source": "derived: %d SMs x %d heavy-IMAD/clk x %.0f MHz / %d per Shoup "
+                               "mulmod" % (SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD)}
     else:
         ach = by_launch / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": top,
+                "frac": ach / peaks["hbm_gbs"], "traffic": measured_traffic(top, config),
+                "kernel": top,
                 "peak_source": "%s hbm_gbs" % peak_kind}
     roof["algorithmic_per_launch"] = {"mulmods": mm_launch, "bytes": by_launch}
     roof["mulmod_rate_measured_T"] = ctx.mulmod_rate(0) / 1e12
@@ -487,7 +524,7 @@ def main():
     n_chunks = sum(m.n_chunks for m in ms)
     n_ks = n_chunks + sum(m.n_keyswitch for m in ms)
     kernels, roof = roofline(ctx, prof, args.steps, ring, n_ks, n_chunks,
-                             sum(m.n_parts for m in ms), sum(m.n_rot for m in ms))
+                             sum(m.n_parts for m in ms), sum(m.n_rot for m in ms), args.config)
 
     cpu = None
     if not args.no_cpu_baseline:
