@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5"])
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--instances", type=int, default=64, help="c4: SpMVs per batched step")
@@ -396,10 +396,73 @@ def run_serving(args):
     return 0
 
 
+def run_sweep(args):
+    """Runtime vs nnz at N = 2^15 (the paper's Figure 8 reports a log-log
+    slope near 1 for its CPU implementation): uniform random 16384 x 16384
+    integer matrices with nnz from 2^10 to 2^22."""
+    import torch
+
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300 import synth
+    from paper_2603_04742_gb300.api import Context
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    logn, L, K, dnum, t = synth.RING["c5"]
+    ctx = Context(logn, L, K, dnum, t)
+    ctx.keygen(1)   # every power-of-two rotation key
+    stream = torch.cuda.current_stream()
+    g = np.random.default_rng(108)
+    pts = []
+    for e in range(10, 23, 2):
+        nnz = 1 << e
+        A = synth.uniform_positions(g, 16384, 16384, nnz, -15, 15)
+        x = g.integers(-15, 16, size=16384, dtype=np.int64)
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals, max_abs_x=15)
+        ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=e)
+        cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=100 + e)
+        y = ctx.spmv(m, ca, cx)
+        torch.cuda.synchronize()
+        ok = list(ctx.decrypt(m, y)) == list(A.matvec(x))
+
+        def step():
+            ctx.spmv(m, ca, cx, y=y, stream=stream)
+        for _ in range(3):
+            step()
+        ms = time_steps(step, stream, args.steps, lambda: None)
+        pa = ctx.encode_matrix_plain(m)
+        yp = ctx.spmv_ptmatrix(m, pa, cx)
+        torch.cuda.synchronize()
+        ok_p = list(ctx.decrypt(m, yp)) == list(A.matvec(x))
+
+        def step_p():
+            ctx.spmv_ptmatrix(m, pa, cx, y=yp, stream=stream)
+        for _ in range(3):
+            step_p()
+        ms_p = time_steps(step_p, stream, args.steps, lambda: None)
+        pts.append({"nnz": A.nnz, "chunks": m.n_chunks, "rotations": m.n_rot,
+                    "keyswitches": m.n_chunks + m.n_keyswitch, "ms": ms, "correct": bool(ok),
+                    "ms_plain_matrix": ms_p, "correct_plain_matrix": bool(ok_p)})
+        del ca, cx, y, m, pa, yp
+    lx = np.log([p_["nnz"] for p_ in pts])
+    ly = np.log([p_["ms"] for p_ in pts])
+    slope_all = float(np.polyfit(lx, ly, 1)[0])
+    big = [i for i, p_ in enumerate(pts) if p_["nnz"] >= 1 << 16]
+    slope_big = float(np.polyfit(lx[big], ly[big], 1)[0])
+    line = {"metric": "runtime vs nnz (Figure 8 sweep)", "unit": "ms per SpMV",
+            "config": {"workload": "uniform random 16384x16384 integer matrices, nnz 2^10..2^22; "
+                                   "BGV N=2^15, 8+2 primes, dnum 4, t=1179649, power-of-two keys"},
+            "points": pts, "loglog_slope_all": slope_all, "loglog_slope_nnz_ge_2^16": slope_big}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "sweep":
+        return run_sweep(args)
     if args.config == "c5":
         return run_serving(args)
     import torch
@@ -421,12 +484,10 @@ def main():
         if world > 1:
             dist.barrier()
 
+    from paper_2603_04742_gb300.dist import max_over_ranks as _max
+
     def max_over_ranks(v):
-        if world > 1:
-            tt = torch.tensor([v], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            return float(tt.item())
-        return v
+        return _max(v, dev)
 
     stream = torch.cuda.current_stream()
     batched = args.config == "c4"

@@ -202,6 +202,16 @@ int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const i
 int hespmv_spmv(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
                 const hespmv_ctbatch *X, hespmv_ctbatch **y, void *stream);
 
+/* Plaintext-matrix mode (the trust model of the Rhombus comparison in
+ * Section 5: the evaluator holds the matrix in the clear, only the vector is
+ * encrypted).  hespmv_encode_matrix_plain encodes the chunk values as trivial
+ * ciphertexts (m, 0) in the NTT domain (no randomness; keys not needed);
+ * hespmv_spmv_ptmatrix evaluates Algorithm 1 with HE-CMult in place of HE-Mult
+ * (no relinearisation), then Algorithm 4 as hespmv_spmv. */
+int hespmv_encode_matrix_plain(hespmv_ctx *ctx, const hespmv_cssc *m, hespmv_ctbatch **out);
+int hespmv_spmv_ptmatrix(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                         const hespmv_ctbatch *X, hespmv_ctbatch **y, void *stream);
+
 /* hespmv_spmv from host buffers: copies A_host and X_host (n_chunks
  * ciphertexts each) to the device, evaluates, copies the n_parts result
  * ciphertexts to y_host, and synchronises `stream`. */

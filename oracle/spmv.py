@@ -64,6 +64,14 @@ def cloud(orc: Oracle, chunks, ct_values, ct_vectors, policy="pow2"):
     return aggregation(orc, prods, [ch.h for ch in chunks], [ch.c for ch in chunks], policy)
 
 
+def cloud_plain_matrix(orc: Oracle, chunks, pt_values, ct_vectors, policy="pow2"):
+    """Algorithm 1 cloud lines when the evaluator holds the matrix in the
+    clear (the Rhombus trust model of Section 5): HE-CMult per chunk, then
+    Algorithm 4 unchanged."""
+    prods = [orc.cmult(x, pt) for pt, x in zip(pt_values, ct_vectors)]
+    return aggregation(orc, prods, [ch.h for ch in chunks], [ch.c for ch in chunks], policy)
+
+
 class SpmvPlan:
     """Client-side preparation: partitions, CSSC, chunks (Algorithms 5, 2)."""
 
@@ -89,6 +97,25 @@ def encrypt_vector(orc: Oracle, plan: SpmvPlan, x, seed: int):
     for k, v in enumerate(reorg):
         out.append(orc.encrypt(orc.encode(v), seed, k))
     return out
+
+
+def encode_matrix_plain(orc: Oracle, plan: SpmvPlan):
+    """Chunk values as plaintexts in the NTT domain over Q (no encryption)."""
+    return [orc.plaintext_ntt(ch.values) for ch in plan.chunks]
+
+
+def spmv_plain_matrix(orc: Oracle, plan: SpmvPlan, pt_values, ct_vectors, policy="pow2"):
+    res = []
+    k = 0
+    for part in plan.parts:
+        n = len(part.chunks)
+        if n == 0:
+            res.append(np.zeros((2, orc.p.L, orc.p.N), dtype=np.uint64))
+        else:
+            res.append(cloud_plain_matrix(orc, part.chunks, pt_values[k:k + n],
+                                          ct_vectors[k:k + n], policy))
+        k += n
+    return res
 
 
 def spmv(orc: Oracle, plan: SpmvPlan, ct_values, ct_vectors, policy="pow2"):

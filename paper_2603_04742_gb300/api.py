@@ -60,9 +60,12 @@ class Context:
     """Scheme parameters, tables and keys on one GPU (hespmv_create)."""
 
     def __init__(self, log2n, L, K, dnum, t, rot_policy="pow2", slots=0, device=0,
-                 torch_alloc=True, prime_bits=0):
+                 torch_alloc=True, prime_bits=0, allocator=None):
         self.lib = B.load()
-        self.allocator = TorchAllocator(device) if torch_alloc else None
+        if allocator is not None:
+            self.allocator = allocator
+        else:
+            self.allocator = TorchAllocator(device) if torch_alloc else None
         p = B.hespmv_params()
         p.log2n, p.L, p.K, p.dnum, p.t = log2n, L, K, dnum, t
         p.prime_bits = prime_bits
@@ -143,6 +146,17 @@ class Context:
     def spmv(self, m, A, X, y=None, stream=None):
         yh = c_void_p(y.h.value if y is not None else None)
         self.check(self.lib.hespmv_spmv(self.h, m.h, A.h, X.h, byref(yh), _stream_handle(stream)))
+        return y if y is not None else CtBatch(self, yh)
+
+    def encode_matrix_plain(self, m):
+        out = c_void_p()
+        self.check(self.lib.hespmv_encode_matrix_plain(self.h, m.h, byref(out)))
+        return CtBatch(self, out)
+
+    def spmv_ptmatrix(self, m, Aplain, X, y=None, stream=None):
+        yh = c_void_p(y.h.value if y is not None else None)
+        self.check(self.lib.hespmv_spmv_ptmatrix(self.h, m.h, Aplain.h, X.h, byref(yh),
+                                                 _stream_handle(stream)))
         return y if y is not None else CtBatch(self, yh)
 
     def spmv_batched(self, ms, As, Xs, ys=None, stream=None):

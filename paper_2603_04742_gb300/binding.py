@@ -74,6 +74,9 @@ SIGNATURES = {
     "hespmv_encrypt": (c_int, [c_void_p, c_void_p, c_int32, i64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_spmv": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p), c_void_p]),
     "hespmv_spmv_host": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),
+    "hespmv_encode_matrix_plain": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
+    "hespmv_spmv_ptmatrix": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p),
+                                     c_void_p]),
     "hespmv_spmv_batched": (c_int, [c_void_p, c_size_t, POINTER(c_void_p), POINTER(c_void_p),
                                     POINTER(c_void_p), POINTER(c_void_p), c_void_p]),
     "hespmv_decrypt": (c_int, [c_void_p, c_void_p, c_void_p, i64p]),

@@ -414,6 +414,7 @@ struct SpmvPrep {
     size_t total_chunks = 0, rot_chunks = 0, G = 1, GR = 1;
     RotPlan *rp = nullptr;
     size_t need_bytes = 0;
+    bool pt_matrix = false;  // matrix operand in the clear: HE-CMult, no key switch
 };
 
 // Per-matrix device state an evaluation reads: mask plaintexts (cached per
@@ -482,8 +483,16 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     const size_t G = pp.G, GR = pp.GR;
     const size_t prod_w = pp.total_chunks * CT;
     uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + G * 3 * LN;
-    // 1) HE-Mult of every chunk pair, G at a time across instances
-    {
+    // 1) HE-Mult of every chunk pair, G at a time across instances (HE-CMult
+    //    when the matrix is in the clear)
+    if (pp.pt_matrix) {
+        size_t k0 = 0;
+        for (size_t i = 0; i < n_inst; ++i) {
+            const size_t nk = ms[i]->plan.chunks.size();
+            CK(op_pt_ct_mul(c, A[i], X[i], prod + k0 * CT, nk, st));
+            k0 += nk;
+        }
+    } else {
         std::vector<std::pair<size_t, size_t>> all;  // (instance, chunk)
         all.reserve(pp.total_chunks);
         for (size_t i = 0; i < n_inst; ++i)
@@ -567,16 +576,18 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
 // graphs are disabled.
 int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
-              cudaStream_t st) {
+              cudaStream_t st, bool pt_matrix = false) {
     SpmvPrep pp;
     int rc = spmv_prepare(ctx, n_inst, ms, pp, st);
     if (rc) return rc;
+    pp.pt_matrix = pt_matrix;
     uint64_t *ws = workspace(ctx, pp.need_bytes);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     const bool profiling = ctx->prof && ctx->prof->on;
     if (!ctx->use_graphs || profiling) return spmv_enqueue(ctx, n_inst, ms, A, X, Y, pp, ws, st);
     std::vector<uint64_t> key;
     key.push_back((uint64_t)(uintptr_t)ws);
+    key.push_back(pt_matrix ? 1 : 0);
     for (size_t i = 0; i < n_inst; ++i) {
         key.push_back(ms[i]->uid);
         key.push_back((uint64_t)(uintptr_t)A[i]);
@@ -970,10 +981,10 @@ int hespmv_ctbatch_download(const hespmv_ctbatch *b, uint64_t *host, size_t n_ct
     return HESPMV_OK;
 }
 
-int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
-                   uint64_t seed, hespmv_ctbatch **out) {
+static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
+                        uint64_t seed, bool plain, hespmv_ctbatch **out) {
     if (!ctx || !m || !out) return HESPMV_E_INVALID;
-    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    if (!ctx->have_keys && !plain) FAIL(HESPMV_E_INVALID, "keygen first");
     if (which != HESPMV_MATRIX && which != HESPMV_VECTOR) FAIL(HESPMV_E_INVALID, "bad operand kind");
     if (which == HESPMV_VECTOR && !x && m->plan.cols > 0) FAIL(HESPMV_E_INVALID, "x is NULL");
     NEED_DEVICE(ctx);
@@ -994,12 +1005,13 @@ int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const i
         FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     }
     int64_t *dvals = (int64_t *)ws;
-    uint64_t *E = ws + G * half, *mq = E + G * N, *u = mq + G * LN, *e0 = u + G * LN,
-             *e1 = e0 + G * LN;
-    int64_t *coef = (int64_t *)(e1 + G * LN);
+    uint64_t *E = ws + G * half, *mq = E + G * N, *u = mq + G * LN;
+    int64_t *coef = (int64_t *)(u + 3 * G * LN);
     std::vector<int64_t> host(G * half);
     for (size_t k0 = 0; k0 < n; k0 += G) {
         const size_t gn = std::min(G, n - k0);
+        // u, e0, e1 back to back at this group's size: one transform of 3*gn items
+        uint64_t *e0 = u + gn * LN, *e1 = e0 + gn * LN;
         std::fill(host.begin(), host.end(), 0);
         for (size_t k = 0; k < gn; ++k) {
             const Chunk &ch = pl.chunks[k0 + k];
@@ -1019,6 +1031,19 @@ int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const i
         ok = ok && !launch_ntt(c, E, c.L + c.K, 1, (int)gn, N, true, 0);
         ok = ok && !op_lift(c, E, mq, gn, 0);
         ok = ok && !launch_ntt(c, mq, 0, (int)L, (int)gn, LN, false, 0);
+        if (plain) {  // trivial ciphertexts (m, 0): the plaintext itself
+            uint64_t *dst = b->data + k0 * 2 * LN;
+            for (size_t k = 0; ok && k < gn; ++k) {
+                ok = cudaMemcpyAsync(dst + k * 2 * LN, mq + k * LN, LN * 8, cudaMemcpyDeviceToDevice, 0) == cudaSuccess &&
+                     cudaMemsetAsync(dst + k * 2 * LN + LN, 0, LN * 8, 0) == cudaSuccess;
+            }
+            ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+            if (!ok) {
+                hespmv_ctbatch_free(b);
+                FAIL(HESPMV_E_CUDA, "plain encoding failed");
+            }
+            continue;
+        }
         ok = ok && !op_sample_signed(c, seed, sbase + 1, 4, kTernary, coef, gn, 0);
         ok = ok && !op_signed_to_limbs(c, coef, u, 0, (int)L, gn, 0);
         ok = ok && !op_sample_signed(c, seed, sbase + 2, 4, kCbd21, coef, gn, 0);
@@ -1035,6 +1060,15 @@ int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const i
     }
     *out = b;
     return HESPMV_OK;
+}
+
+int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
+                   uint64_t seed, hespmv_ctbatch **out) {
+    return encrypt_impl(ctx, m, which, x, seed, false, out);
+}
+
+int hespmv_encode_matrix_plain(hespmv_ctx *ctx, const hespmv_cssc *m, hespmv_ctbatch **out) {
+    return encrypt_impl(ctx, m, HESPMV_MATRIX, nullptr, 0, true, out);
 }
 
 int hespmv_spmv(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
@@ -1066,6 +1100,25 @@ int hespmv_spmv_batched(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         out[i] = y[i]->data;
     }
     return spmv_core(ctx, n, m, a.data(), x.data(), out.data(), (cudaStream_t)stream);
+}
+
+int hespmv_spmv_ptmatrix(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
+                         const hespmv_ctbatch *X, hespmv_ctbatch **y, void *stream) {
+    if (!ctx || !m || !A || !X || !y) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    DeviceGuard g(ctx->device);
+    const size_t nc = m->plan.chunks.size(), np = m->plan.parts.size();
+    if (A->n < nc || X->n < nc) FAIL(HESPMV_E_INVALID, "operand batches are smaller than the chunk count");
+    if (*y == nullptr) {
+        int rc = batch_new(ctx, np, y);
+        if (rc) return rc;
+    } else if ((*y)->n < np) {
+        FAIL(HESPMV_E_INVALID, "result batch is smaller than the partition count");
+    }
+    const uint64_t *a = A->data, *x = X->data;
+    uint64_t *out = (*y)->data;
+    return spmv_core(ctx, 1, &m, &a, &x, &out, (cudaStream_t)stream, true);
 }
 
 int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_host,

@@ -10,6 +10,9 @@ cudaError_t op_add(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t 
                    cudaStream_t st);   // n_polys polynomials of L limbs
 cudaError_t op_tensor(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
                       cudaStream_t st);
+// prod[i] = (a[i].c0 * x[i].c0, a[i].c0 * x[i].c1) for n pairs (plaintext a in normal form)
+cudaError_t op_pt_ct_mul(const Ctx &c, const uint64_t *a, const uint64_t *x, uint64_t *prod,
+                         size_t n, cudaStream_t st);
 // out = ct * pt (pt [L][N] in Montgomery form, shared by all n ciphertexts)
 cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint64_t *out, size_t n,
                      cudaStream_t st);

@@ -127,6 +127,19 @@ __global__ void k_cmult_acc(uint64_t *acc, const uint64_t *w, const uint64_t *pt
     }
 }
 
+// prod = (a0 * x0, a0 * x1): ciphertext x times the plaintext a0 (HE-CMult)
+__global__ void k_pt_ct_mul(const uint64_t *a, const uint64_t *x, uint64_t *prod, int64_t total,
+                            int log2n, int L, const ModConst *mc) {
+    const int64_t LN = (int64_t)L << log2n;
+    GRID_STRIDE(i, total) {  // total = n * L * N
+        const int64_t item = i / LN, r = i - item * LN;
+        const ModConst m = mc[(int)(r >> log2n)];
+        const uint64_t p = a[item * 2 * LN + r];
+        prod[item * 2 * LN + r] = mul_mod(p, x[item * 2 * LN + r], m);
+        prod[item * 2 * LN + LN + r] = mul_mod(p, x[item * 2 * LN + LN + r], m);
+    }
+}
+
 __global__ void k_permute(const uint64_t *in, uint64_t *out, const int32_t *perm, int64_t total,
                           int log2n) {
     GRID_STRIDE(i, total) {
@@ -436,6 +449,12 @@ cudaError_t op_tensor(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64
                       cudaStream_t st) {
     const int64_t total = (int64_t)n * c.L * c.N;
     LAUNCH(k_tensor, total, st, a, b, d, total, c.log2n, c.L, c.c->d.mc);
+}
+
+cudaError_t op_pt_ct_mul(const Ctx &c, const uint64_t *a, const uint64_t *x, uint64_t *prod,
+                         size_t n, cudaStream_t st) {
+    const int64_t total = (int64_t)n * c.L * c.N;
+    LAUNCH(k_pt_ct_mul, total, st, a, x, prod, total, c.log2n, c.L, c.c->d.mc);
 }
 
 cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint64_t *out, size_t n,

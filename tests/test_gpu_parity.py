@@ -219,6 +219,26 @@ def test_spmv_small_partitions_parity():
     assert list(out) == list(A.matvec(x)) == list(oout)
 
 
+@pytest.mark.parametrize("logn,rows,nnz,slots", [(6, 960, 9000, 32), (12, 640, 3000, 16)])
+def test_spmv_many_chunks_ragged_batches_parity(logn, rows, nnz, slots):
+    """More chunks than one batch of every stage holds (encryption 64, HE-Mult
+    32, totalSum rounds 64 ciphertexts), with a ragged last batch in each;
+    2^6 runs the unfused key switch, 2^12 the fused one."""
+    t = plain_modulus(1 << logn, 1 << 20)
+    A, x = synth.small_matrix(5 if logn == 6 else 6, rows, 64 if logn == 6 else 96, nnz, -9, 9)
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, 3, 1, 3, t, slots=slots)
+    orc = Oracle(Params(log2n=logn, L=3, K=1, dnum=3, t=t, slots=slots))
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    h, c, _ = m.chunks()
+    assert m.n_chunks > 64 and m.n_chunks % 64 and m.n_chunks % 32 and int((c > 1).sum()) > 64
+    steps = m.rotation_steps()
+    ctx.keygen(4, steps)
+    orc.keygen(4, sorted({g for k in steps for g in orc.rotation_elements(k)}))
+    m2, y, out, oout = run_spmv_pair(ctx, orc, A, x)
+    assert list(out) == list(A.matvec(x)) == list(oout)
+
+
 @pytest.mark.parametrize("policy", ["pow2", "exact"])
 def test_spmv_c1_parity(policy):
     logn, L, K, dnum, t = synth.RING["c1"]
@@ -341,3 +361,30 @@ def test_graph_replay_matches_eager():
     cx.upload(cx2.download())
     ctx.spmv(m, ca, cx, y=y)
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x2))
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_spmv_plain_matrix_parity(name):
+    """Plaintext-matrix mode: the trivial ciphertexts equal the oracle's
+    plaintexts, the result ciphertexts equal the oracle's, and decrypt = A.x."""
+    logn, L, K, dnum, t = synth.RING[name]
+    A, x = synth.workload(name)
+    from paper_2603_04742_gb300.api import Context
+    probe = Context(logn, L, K, dnum, t, device=-1, torch_alloc=False)
+    steps = probe.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals).rotation_steps()
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=2, steps=steps)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    pa = ctx.encode_matrix_plain(m)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    y = ctx.spmv_ptmatrix(m, pa, cx)
+    torch.cuda.synchronize()
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    pts = S.encode_matrix_plain(orc, plan)
+    gp = pa.download()
+    for k in range(len(pts)):
+        assert np.array_equal(gp[k][0], pts[k]) and not np.any(gp[k][1])
+    ores = S.spmv_plain_matrix(orc, plan, pts, S.encrypt_vector(orc, plan, x, 3))
+    gy = y.download()
+    for p_ in range(len(ores)):
+        assert np.array_equal(gy[p_], ores[p_])
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x))

@@ -143,3 +143,23 @@ def test_spmv_c1_end_to_end():
     assert list(y) == list(A.matvec(x))
     # remaining noise budget (bits) stays well above zero
     assert p.Q.bit_length() - 1 - orc.noise_bits(res[0]) > 20
+
+
+def test_spmv_plain_matrix_mode():
+    """Plaintext matrix times encrypted vector (HE-CMult per chunk) decrypts
+    to A.x, with one multiplicative level fewer than the ciphertext mode."""
+    A, x = synth.small_matrix(31, 60, 50, 300, -9, 9)
+    p = Params(log2n=6, L=3, K=1, dnum=3, t=12289)
+    orc = Oracle(p)
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, p.slots)
+    gels = set()
+    for ch in plan.chunks:
+        for k in S.rotation_steps(ch.c, ch.h):
+            gels.update(orc.rotation_elements(k))
+    orc.keygen(5, sorted(gels))
+    pts = S.encode_matrix_plain(orc, plan)
+    cx = S.encrypt_vector(orc, plan, x, 6)
+    orc.counts.clear()
+    res = S.spmv_plain_matrix(orc, plan, pts, cx)
+    assert list(S.decrypt_result(orc, plan, res)) == list(A.matvec(x))
+    assert orc.counts.get("mult", 0) == 0 and orc.counts["cmult"] == 2 * len(plan.chunks)
