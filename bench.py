@@ -54,7 +54,7 @@ KS_SOURCES = ["paper_2603_04742_gb300/csrc/ks.cu", "paper_2603_04742_gb300/csrc/
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep"])
@@ -132,10 +132,17 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        # the timed region starts once the sampler has written its first row
+        t0 = time.time()
+        while time.time() - t0 < 5 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:
@@ -283,6 +290,19 @@ def time_steps(fn, stream, steps, barrier):
     torch.cuda.synchronize()
     barrier()
     return e0.elapsed_time(e1) / steps
+
+
+def per_step_ms(fn, stream, n):
+    """Device time of each of n consecutive steps (one event between steps)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(n):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
 
 
 def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"):
@@ -529,6 +549,10 @@ def main():
     n_spmv = len(insts)
     nnz = sum(a.nnz for a, _ in insts)
     value = world * n_spmv * 1000.0 / ms_step
+    # step-time distribution (a separate pass, >= 50 steps)
+    dist_ms = np.asarray(per_step_ms(step, stream, max(50, args.steps)))
+    step_ms = {"median": float(np.median(dist_ms)), "p99": float(np.percentile(dist_ms, 99)),
+               "runs": int(dist_ms.size)}
 
     # per-kernel device times (second pass, kernels one by one)
     ctx.profile_enable(True)
@@ -616,6 +640,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": cfg,
         "nnz_per_s": value * nnz / n_spmv,
+        "step_ms": step_ms,
         "correct": bool(correct),
         "e2e": e2e,
         "gpu_launches": int(sum(v[0] for v in prof.values())),

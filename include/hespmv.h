@@ -64,6 +64,10 @@ extern "C" {
 #define HESPMV_VECTOR 1
 
 /* which key hespmv_key_export copies out */
+/* CSSC serialization kinds */
+#define HESPMV_SER_FULL 0  /* every array: VA, CI, CP, RM (Client A's own copy)              */
+#define HESPMV_SER_SHAPE 1 /* CP only: the chunk shapes the cloud needs (rList, cList)         */
+
 #define HESPMV_KEY_SECRET 0 /* s in the NTT domain over the L+K primes: [L+K][N]   */
 #define HESPMV_KEY_PUBLIC 1 /* (pk0, pk1): [2][L][N]                               */
 #define HESPMV_KEY_RELIN 2  /* relinearisation key: [dnum][2][L+K][N]              */
@@ -173,6 +177,22 @@ int hespmv_cssc_arrays(const hespmv_cssc *m, int32_t part, const int64_t **va, c
  * (ascending).  Writes at most cap entries; *n receives the total. */
 int hespmv_cssc_rotation_steps(const hespmv_cssc *m, int32_t *steps, size_t cap, size_t *n);
 
+/* Serialize a CSSC plan (Algorithm 1: what Client A keeps, or the chunk
+ * shapes it hands to the cloud).  Format, little-endian, fields 8-byte
+ * aligned: magic "HSCS", version, kind, s, rows, cols, nnz, n_parts, then
+ * per partition row0, rows, nnz_part, |CP|, CP[], and for HESPMV_SER_FULL
+ * VA[], CI[], RM[].  buf NULL: *len receives the size only; cap < size:
+ * HESPMV_E_INVALID with *len set.  A shape-only plan serializes only as
+ * HESPMV_SER_SHAPE.  Host only. */
+int hespmv_cssc_serialize(const hespmv_cssc *m, int32_t kind, void *buf, size_t cap, size_t *len);
+/* Rebuild a plan from hespmv_cssc_serialize output (chunks recomputed by
+ * Algorithm 2).  Every length, bound, permutation and ordering is checked
+ * before use: HESPMV_E_INVALID with a message on any inconsistency,
+ * including a chunk capacity s other than the context's.  A shape-only plan
+ * evaluates (spmv) but refuses encrypt, decrypt, colindex and arrays.  Host
+ * only.  Release with hespmv_cssc_free. */
+int hespmv_cssc_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hespmv_cssc **out);
+
 /* --------------------------------------------------------- ciphertext batch */
 
 int hespmv_ctbatch_create(hespmv_ctx *ctx, size_t n_ct, hespmv_ctbatch **out);
@@ -182,6 +202,16 @@ int hespmv_ctbatch_data(const hespmv_ctbatch *b, uint64_t **dev, size_t *n_ct);
 /* Host <-> device copies of n_ct whole ciphertexts, on `stream`. */
 int hespmv_ctbatch_upload(hespmv_ctbatch *b, const uint64_t *host, size_t n_ct, void *stream);
 int hespmv_ctbatch_download(const hespmv_ctbatch *b, uint64_t *host, size_t n_ct, void *stream);
+/* Serialize a batch for transfer between parties: magic "HSCT", version,
+ * log2 N, L, n_ct, a fingerprint of (N, q_0..q_{L-1}, t), then the n_ct
+ * ciphertexts [2][L][N] as little-endian u64.  buf NULL: *len receives the
+ * size only.  Synchronous (waits for the device copy). */
+int hespmv_ctbatch_serialize(const hespmv_ctbatch *b, void *buf, size_t cap, size_t *len);
+/* Load a serialized batch into a new device batch of this context.  Fails
+ * with HESPMV_E_INVALID if the stream is truncated or longer than its
+ * header says, comes from another ring, or holds a residue >= its prime.
+ * Synchronous. */
+int hespmv_ctbatch_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hespmv_ctbatch **out);
 
 /* Encode and encrypt one operand (Algorithm 1, Client A / Client B).
  * which = HESPMV_MATRIX: the chunk values; HESPMV_VECTOR: x (cols entries)

@@ -134,6 +134,20 @@ class Context:
     def encode_cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x=0):
         return Cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x)
 
+    def cssc_from_bytes(self, data):
+        """A plan from Cssc.serialize output (hespmv_cssc_deserialize)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        h = c_void_p()
+        self.check(self.lib.hespmv_cssc_deserialize(self.h, buf, len(data), byref(h)))
+        return Cssc.from_handle(self, h)
+
+    def ctbatch_from_bytes(self, data):
+        """A device batch from CtBatch.serialize output."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        h = c_void_p()
+        self.check(self.lib.hespmv_ctbatch_deserialize(self.h, buf, len(data), byref(h)))
+        return CtBatch(self, h)
+
     def encrypt(self, m, which, x=None, seed=0):
         out = c_void_p()
         xp = None
@@ -302,11 +316,30 @@ class Cssc:
         ctx.check(self.lib.hespmv_encode_cssc(ctx.h, rows, cols, int(rp[-1]) if len(rp) else 0,
                                               _i64p(rp), _i32p(ci), _i64p(va),
                                               c_int64(max_abs_x), byref(h)))
+        self._attach(h)
+
+    @classmethod
+    def from_handle(cls, ctx, h):
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self._attach(h)
+        return self
+
+    def _attach(self, h):
         self.h = h
         info = [c_int32(), c_int32(), c_int64(), c_int64(), c_int32(), c_int32(), c_int64()]
-        ctx.check(self.lib.hespmv_cssc_info(h, *[byref(v) for v in info]))
+        self.ctx.check(self.lib.hespmv_cssc_info(h, *[byref(v) for v in info]))
         (self.n_parts, self.n_chunks, self.n_rot, self.n_keyswitch, self.rows, self.cols,
          self.nnz) = [v.value for v in info]
+
+    def serialize(self, kind=B.HESPMV_SER_FULL):
+        """Bytes of hespmv_cssc_serialize (FULL: every array; SHAPE: chunk shapes only)."""
+        n = c_size_t()
+        self.ctx.check(self.lib.hespmv_cssc_serialize(self.h, kind, None, 0, byref(n)))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        self.ctx.check(self.lib.hespmv_cssc_serialize(self.h, kind, buf, n.value, byref(n)))
+        return buf.raw[:n.value]
 
     def chunks(self):
         n = self.n_chunks
@@ -381,6 +414,14 @@ class CtBatch:
         self.ctx.check(self.ctx.lib.hespmv_ctbatch_download(self.h, _u64p(out), self.n,
                                                             _stream_handle(stream)))
         return out.reshape(self.n, 2, self.ctx.L, self.ctx.N)
+
+    def serialize(self):
+        """Bytes of hespmv_ctbatch_serialize."""
+        n = c_size_t()
+        self.ctx.check(self.ctx.lib.hespmv_ctbatch_serialize(self.h, None, 0, byref(n)))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        self.ctx.check(self.ctx.lib.hespmv_ctbatch_serialize(self.h, buf, n.value, byref(n)))
+        return buf.raw[:n.value]
 
     def upload(self, host, stream=None):
         a = np.ascontiguousarray(host, dtype=np.uint64)

@@ -23,6 +23,8 @@ HESPMV_ROT_POW2 = 0
 HESPMV_ROT_EXACT = 1
 HESPMV_MATRIX = 0
 HESPMV_VECTOR = 1
+HESPMV_SER_FULL = 0
+HESPMV_SER_SHAPE = 1
 HESPMV_KEY_SECRET = 0
 HESPMV_KEY_PUBLIC = 1
 HESPMV_KEY_RELIN = 2
@@ -66,11 +68,15 @@ SIGNATURES = {
     "hespmv_cssc_arrays": (c_int, [c_void_p, c_int32, POINTER(i64p), POINTER(i32p), szp,
                                    POINTER(i64p), szp, POINTER(i32p), szp, i32p]),
     "hespmv_cssc_rotation_steps": (c_int, [c_void_p, i32p, c_size_t, szp]),
+    "hespmv_cssc_serialize": (c_int, [c_void_p, c_int32, c_void_p, c_size_t, szp]),
+    "hespmv_cssc_deserialize": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
     "hespmv_ctbatch_create": (c_int, [c_void_p, c_size_t, POINTER(c_void_p)]),
     "hespmv_ctbatch_free": (None, [c_void_p]),
     "hespmv_ctbatch_data": (c_int, [c_void_p, POINTER(u64p), szp]),
     "hespmv_ctbatch_upload": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_download": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
+    "hespmv_ctbatch_serialize": (c_int, [c_void_p, c_void_p, c_size_t, szp]),
+    "hespmv_ctbatch_deserialize": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
     "hespmv_encrypt": (c_int, [c_void_p, c_void_p, c_int32, i64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_spmv": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p), c_void_p]),
     "hespmv_spmv_host": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),

@@ -831,6 +831,24 @@ int hespmv_key_export(hespmv_ctx *ctx, int32_t which, uint32_t galois_elt, uint6
     return HESPMV_OK;
 }
 
+// rotation counts, distinct steps and the schedule-cache id of a new plan
+static void finish_cssc(hespmv_ctx *ctx, hespmv_cssc *m) {
+    std::set<int32_t> st;
+    std::vector<int32_t> steps;
+    std::vector<uint8_t> orig;
+    m->n_rot = m->n_ks = 0;
+    for (const Chunk &ch : m->plan.chunks) {
+        total_sum_steps(ch.h, ch.c, steps, orig);
+        m->n_rot += (int64_t)steps.size();
+        for (int32_t k : steps) {
+            st.insert(k);
+            m->n_ks += (int64_t)rotation_chain(ctx, k).size();
+        }
+    }
+    m->steps.assign(st.begin(), st.end());
+    m->uid = ctx->next_uid++;
+}
+
 int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
                        const int64_t *rowptr, const int32_t *colidx, const int64_t *vals,
                        int64_t max_abs_x, hespmv_cssc **out) {
@@ -861,19 +879,7 @@ int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
             }
         }
     }
-    std::set<int32_t> st;
-    std::vector<int32_t> steps;
-    std::vector<uint8_t> orig;
-    for (const Chunk &ch : m->plan.chunks) {
-        total_sum_steps(ch.h, ch.c, steps, orig);
-        m->n_rot += (int64_t)steps.size();
-        for (int32_t k : steps) {
-            st.insert(k);
-            m->n_ks += (int64_t)rotation_chain(ctx, k).size();
-        }
-    }
-    m->steps.assign(st.begin(), st.end());
-    m->uid = ctx->next_uid++;
+    finish_cssc(ctx, m);
     *out = m;
     return HESPMV_OK;
 }
@@ -912,7 +918,7 @@ int hespmv_cssc_chunks(const hespmv_cssc *m, int32_t *h, int32_t *c, int32_t *pa
 }
 
 int hespmv_cssc_colindex(const hespmv_cssc *m, const int32_t **ci, size_t *len) {
-    if (!m || !ci || !len) return HESPMV_E_INVALID;
+    if (!m || !ci || !len || m->shape_only) return HESPMV_E_INVALID;
     *ci = m->plan.slot_ci.data();
     *len = m->plan.slot_ci.size();
     return HESPMV_OK;
@@ -921,7 +927,8 @@ int hespmv_cssc_colindex(const hespmv_cssc *m, const int32_t **ci, size_t *len) 
 int hespmv_cssc_arrays(const hespmv_cssc *m, int32_t part, const int64_t **va, const int32_t **ci,
                        size_t *nnz_part, const int64_t **cp, size_t *cp_len, const int32_t **rm,
                        size_t *rm_len, int32_t *row0) {
-    if (!m || part < 0 || part >= (int32_t)m->plan.parts.size()) return HESPMV_E_INVALID;
+    if (!m || m->shape_only || part < 0 || part >= (int32_t)m->plan.parts.size())
+        return HESPMV_E_INVALID;
     const Partition &P = m->plan.parts[part];
     if (va) *va = P.va.data();
     if (ci) *ci = P.ci.data();
@@ -981,11 +988,247 @@ int hespmv_ctbatch_download(const hespmv_ctbatch *b, uint64_t *host, size_t n_ct
     return HESPMV_OK;
 }
 
+// ------------------------------------------------------------ serialization
+// Little-endian byte streams; every field is 8-byte aligned.  Readers check
+// each length against the bytes left before touching or allocating anything.
+}  // extern "C"
+
+namespace {
+
+const uint32_t kCsscMagic = 0x53435348u;  // "HSCS"
+const uint32_t kCtMagic = 0x54435348u;    // "HSCT"
+const uint32_t kSerVersion = 1;
+
+struct Writer {
+    uint8_t *p;
+    size_t cap, n = 0;
+    void put(const void *src, size_t bytes) {
+        if (p && n + bytes <= cap) std::memcpy(p + n, src, bytes);
+        n += bytes;
+    }
+    template <class T>
+    void val(T v) { put(&v, sizeof(T)); }
+    template <class T>
+    void arr(const std::vector<T> &v) {
+        put(v.data(), v.size() * sizeof(T));
+        const size_t pad = (8 - (v.size() * sizeof(T)) % 8) % 8;
+        const uint64_t zero = 0;
+        put(&zero, pad);
+    }
+};
+
+struct Reader {
+    const uint8_t *p;
+    size_t len, n = 0;
+    bool ok = true;
+    bool take(void *dst, size_t bytes) {
+        if (!ok || bytes > len - n) return ok = false;
+        std::memcpy(dst, p + n, bytes);
+        n += bytes;
+        return true;
+    }
+    template <class T>
+    bool val(T &v) { return take(&v, sizeof(T)); }
+    template <class T>
+    bool arr(std::vector<T> &v, uint64_t count) {
+        if (!ok || count > (len - n) / sizeof(T)) return ok = false;
+        v.resize(count);
+        if (!take(v.data(), count * sizeof(T))) return false;
+        const size_t pad = (8 - (count * sizeof(T)) % 8) % 8;
+        if (pad > len - n) return ok = false;
+        n += pad;
+        return true;
+    }
+};
+
+// FNV-1a over the ciphertext moduli and t: ciphertexts load only into a
+// context with the same ring
+uint64_t ring_fingerprint(const hespmv_ctx *ctx) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)ctx->h.log2n);
+    for (int l = 0; l < ctx->h.L; ++l) mix(ctx->h.q[l]);
+    mix(ctx->h.t);
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hespmv_cssc_serialize(const hespmv_cssc *m, int32_t kind, void *buf, size_t cap, size_t *len) {
+    if (!m || !len || (kind != HESPMV_SER_FULL && kind != HESPMV_SER_SHAPE)) return HESPMV_E_INVALID;
+    if (kind == HESPMV_SER_FULL && m->shape_only) return HESPMV_E_INVALID;
+    const Plan &pl = m->plan;
+    Writer w{(uint8_t *)buf, cap};
+    w.val(kCsscMagic);
+    w.val(kSerVersion);
+    w.val((uint32_t)kind);
+    w.val((uint32_t)pl.s);
+    w.val((int32_t)pl.rows);
+    w.val((int32_t)pl.cols);
+    w.val((int64_t)pl.nnz);
+    w.val((uint64_t)pl.parts.size());
+    for (const Partition &P : pl.parts) {
+        w.val((int32_t)P.row0);
+        w.val((int32_t)P.rows);
+        w.val((int64_t)P.va.size());
+        w.val((int64_t)P.cp.size());
+        w.arr(P.cp);
+        if (kind == HESPMV_SER_FULL) {
+            w.arr(P.va);
+            w.arr(P.ci);
+            w.arr(P.rm);
+        }
+    }
+    *len = w.n;
+    if (buf && cap < w.n) return HESPMV_E_INVALID;
+    return HESPMV_OK;
+}
+
+int hespmv_cssc_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hespmv_cssc **out) {
+    if (!ctx || !buf || !out || ctx->h.q.empty()) return HESPMV_E_INVALID;
+    *out = nullptr;
+    Reader r{(const uint8_t *)buf, len};
+    uint32_t magic = 0, ver = 0, kind = 0, s = 0;
+    int32_t rows = 0, cols = 0;
+    int64_t nnz = 0;
+    uint64_t n_parts = 0;
+    r.val(magic), r.val(ver), r.val(kind), r.val(s), r.val(rows), r.val(cols), r.val(nnz), r.val(n_parts);
+    if (!r.ok || magic != kCsscMagic || ver != kSerVersion) FAIL(HESPMV_E_INVALID, "not a CSSC stream");
+    if (kind != HESPMV_SER_FULL && kind != HESPMV_SER_SHAPE) FAIL(HESPMV_E_INVALID, "unknown CSSC kind");
+    if ((int32_t)s != ctx->h.slots) FAIL(HESPMV_E_INVALID, "CSSC chunk capacity differs from the context's");
+    if (rows < 0 || cols < 0 || nnz < 0) FAIL(HESPMV_E_INVALID, "negative CSSC size");
+    const uint64_t want_parts = rows ? ((uint64_t)rows + s - 1) / s : 0;
+    if (n_parts != want_parts) FAIL(HESPMV_E_INVALID, "partition count does not match rows");
+    const bool full = kind == HESPMV_SER_FULL;
+    hespmv_cssc *m = new hespmv_cssc();
+    m->ctx = ctx;
+    m->shape_only = !full;
+    Plan &pl = m->plan;
+    pl.rows = rows, pl.cols = cols, pl.nnz = nnz, pl.s = (int32_t)s;
+    std::string err;
+    int64_t total = 0;
+    for (uint64_t k = 0; k < n_parts && err.empty(); ++k) {
+        Partition P;
+        int64_t nnz_part = 0, cp_len = 0;
+        r.val(P.row0), r.val(P.rows), r.val(nnz_part), r.val(cp_len);
+        if (!r.ok) { err = "truncated"; break; }
+        if ((int64_t)P.row0 != (int64_t)k * s || P.rows != std::min<int64_t>(s, rows - (int64_t)k * s)) {
+            err = "partition bounds";
+            break;
+        }
+        if (nnz_part < 0 || cp_len < 1 || !r.arr(P.cp, (uint64_t)cp_len)) { err = "bad CP"; break; }
+        if (P.cp[0] != 0 || P.cp.back() != nnz_part) { err = "CP ends"; break; }
+        for (int64_t j = 0; j + 1 < cp_len && err.empty(); ++j) {
+            const int64_t h = P.cp[j + 1] - P.cp[j];
+            if (h < 1 || h > P.rows) err = "column height out of range";
+            else if (j > 0 && h > P.cp[j] - P.cp[j - 1]) err = "column heights increase";
+        }
+        if (!err.empty()) break;
+        total += nnz_part;
+        if (full) {
+            if (!r.arr(P.va, (uint64_t)nnz_part) || !r.arr(P.ci, (uint64_t)nnz_part) ||
+                !r.arr(P.rm, (uint64_t)P.rows)) {
+                err = "truncated";
+                break;
+            }
+            std::vector<uint8_t> seen(P.rows, 0);
+            for (int32_t v : P.rm) {
+                if (v < 0 || v >= P.rows || seen[v]) { err = "RM is not a permutation"; break; }
+                seen[v] = 1;
+            }
+            // sorted row p holds CI[CP[j] + p] for the columns j taller than p;
+            // a CSR row's columns ascend strictly
+            for (int64_t j = 0; j + 1 < cp_len && err.empty(); ++j)
+                for (int64_t p = 0; p < P.cp[j + 1] - P.cp[j]; ++p) {
+                    const int32_t c = P.ci[P.cp[j] + p];
+                    if (c < 0 || c >= cols) { err = "column index out of range"; break; }
+                    if (j > 0 && c <= P.ci[P.cp[j - 1] + p]) { err = "row columns not ascending"; break; }
+                }
+        } else {
+            P.va.assign((size_t)nnz_part, 0);
+            P.ci.assign((size_t)nnz_part, -1);
+        }
+        pl.parts.push_back(std::move(P));
+    }
+    if (err.empty() && (total != nnz || r.n != len)) err = "length mismatch";
+    if (!err.empty()) {
+        delete m;
+        FAIL(HESPMV_E_INVALID, "CSSC stream: " + err);
+    }
+    chunk_plan(pl);
+    finish_cssc(ctx, m);
+    *out = m;
+    return HESPMV_OK;
+}
+
+int hespmv_ctbatch_serialize(const hespmv_ctbatch *b, void *buf, size_t cap, size_t *len) {
+    if (!b || !len) return HESPMV_E_INVALID;
+    hespmv_ctx *ctx = b->ctx;
+    const size_t words = b->n * 2 * (size_t)ctx->h.L * ctx->h.N;
+    const size_t head = 4 * 4 + 2 * 8;
+    *len = head + words * 8;
+    if (!buf) return HESPMV_OK;
+    if (cap < *len) FAIL(HESPMV_E_INVALID, "buffer too small");
+    Writer w{(uint8_t *)buf, cap};
+    w.val(kCtMagic);
+    w.val(kSerVersion);
+    w.val((uint32_t)ctx->h.log2n);
+    w.val((uint32_t)ctx->h.L);
+    w.val((uint64_t)b->n);
+    w.val(ring_fingerprint(ctx));
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpy((uint8_t *)buf + head, b->data, words * 8, cudaMemcpyDeviceToHost));
+    return HESPMV_OK;
+}
+
+int hespmv_ctbatch_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hespmv_ctbatch **out) {
+    if (!ctx || !buf || !out) return HESPMV_E_INVALID;
+    *out = nullptr;
+    NEED_DEVICE(ctx);
+    Reader r{(const uint8_t *)buf, len};
+    uint32_t magic = 0, ver = 0, log2n = 0, L = 0;
+    uint64_t n = 0, fp = 0;
+    r.val(magic), r.val(ver), r.val(log2n), r.val(L), r.val(n), r.val(fp);
+    if (!r.ok || magic != kCtMagic || ver != kSerVersion) FAIL(HESPMV_E_INVALID, "not a ciphertext stream");
+    if ((int)log2n != ctx->h.log2n || (int)L != ctx->h.L || fp != ring_fingerprint(ctx))
+        FAIL(HESPMV_E_INVALID, "ciphertexts belong to another ring");
+    const size_t N = ctx->h.N, per_ct = 2 * (size_t)L * N;
+    if (n > (len - r.n) / 8 / per_ct || r.n + n * per_ct * 8 != len)
+        FAIL(HESPMV_E_INVALID, "ciphertext stream length mismatch");
+    const uint8_t *src = (const uint8_t *)buf + r.n;
+    for (size_t i = 0; i < n * 2 * L; ++i) {  // every residue reduced mod its prime
+        const uint64_t q = ctx->h.q[i % L];
+        for (size_t k = 0; k < N; ++k) {
+            uint64_t v;
+            std::memcpy(&v, src + (i * N + k) * 8, 8);
+            if (v >= q) FAIL(HESPMV_E_INVALID, "residue not reduced mod q");
+        }
+    }
+    DeviceGuard g(ctx->device);
+    hespmv_ctbatch *b = nullptr;
+    int rc = batch_new(ctx, n, &b);
+    if (rc) return rc;
+    if (n && cudaMemcpy(b->data, src, n * per_ct * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        hespmv_ctbatch_free(b);
+        FAIL(HESPMV_E_CUDA, "ciphertext upload failed");
+    }
+    *out = b;
+    return HESPMV_OK;
+}
+
 static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
                         uint64_t seed, bool plain, hespmv_ctbatch **out) {
     if (!ctx || !m || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys && !plain) FAIL(HESPMV_E_INVALID, "keygen first");
     if (which != HESPMV_MATRIX && which != HESPMV_VECTOR) FAIL(HESPMV_E_INVALID, "bad operand kind");
+    if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no values or column indices");
     if (which == HESPMV_VECTOR && !x && m->plan.cols > 0) FAIL(HESPMV_E_INVALID, "x is NULL");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
@@ -1184,6 +1427,7 @@ int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *
                    int64_t *out_rows) {
     if (!ctx || !m || !y || (!out_rows && m->plan.rows)) return HESPMV_E_INVALID;
     if (y->n < m->plan.parts.size()) FAIL(HESPMV_E_INVALID, "result batch too small");
+    if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no row map");
     const uint64_t t = ctx->h.t;
     std::vector<uint64_t> slots(ctx->h.N);
     for (size_t p = 0; p < m->plan.parts.size(); ++p) {

@@ -75,6 +75,13 @@ static void chunk_partition(Partition &P, int32_t part_index, int32_t s, Plan &p
     P.n_chunks = (int32_t)plan.chunks.size() - P.chunk0;
 }
 
+void chunk_plan(Plan &plan) {
+    plan.chunks.clear();
+    plan.slot_vals.clear();
+    plan.slot_ci.clear();
+    for (size_t k = 0; k < plan.parts.size(); ++k) chunk_partition(plan.parts[k], (int32_t)k, plan.s, plan);
+}
+
 std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *rowptr,
                        const int32_t *colidx, const int64_t *vals, int32_t s, Plan &plan) {
     if (rows < 0 || cols < 0 || nnz < 0 || s < 1) return "negative size";

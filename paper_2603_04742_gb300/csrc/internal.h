@@ -103,6 +103,8 @@ struct Plan {
 // Returns empty string on success.
 std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *rowptr,
                        const int32_t *colidx, const int64_t *vals, int32_t s, Plan &plan);
+// Chunks (Algorithm 2) of every partition whose CP, VA and CI are set.
+void chunk_plan(Plan &plan);
 // totalSum rotation amounts of a chunk (r rows, c columns) in order; flags
 // tell whether the step rotates the running sum (doubling) or the original.
 void total_sum_steps(int32_t r, int32_t c, std::vector<int32_t> &steps,
@@ -201,6 +203,7 @@ struct hespmv_cssc {
     const uint64_t **d_masks = nullptr;  // device: mask plaintext of each chunk
     uint64_t uid = 0;                    // unique per context (schedule cache key)
     bool prepared = false;               // masks, mask table, permutations resident
+    bool shape_only = false;             // chunk shapes without values, indices, RM
 };
 
 struct hespmv_ctbatch {
