@@ -5,17 +5,18 @@
 //   out_c = (sum_j ModUp_j(d) * key_j,c  -  delta_c) * P^-1  (+ addend),
 //   delta_c = t * Conv_{P->Q}([x_c * t^-1]_P),  x_c the P-limbs of the sum:
 //  1. inverse NTT of d, row pass                         (d -> dc)
-//     (with HE-Mult fused in, d = a1 * b1 is formed here, in step 4 and the
-//     addend (a0 b0, a0 b1 + a1 b0) in step 7: no tensor in memory)
+//     (with HE-Mult fused in, d = a1 * b1 is formed here and in step 4, and
+//     the addend (a0 b0, a0 b1 + a1 b0) in step 4: no tensor in memory)
 //  2. inverse NTT column pass, N^-1 * Qhat^-1 folded in  (dc -> z)
 //  3. ModUp + forward column pass: one CTA raises a digit's z columns to
 //     every other prime and transforms them                 (z -> ext)
 //  4. forward row pass of the raised limbs, in place             (ext)
 //     and the inner product with the key: the digit's own primes use d
-//     directly; 128-bit sums, one Montgomery reduction           (-> acc)
+//     directly; the addend enters on the Q primes times P; 128-bit sums,
+//     one Montgomery reduction                                     (-> acc)
 //  5. inverse NTT of acc's P limbs, t^-1 * Phat^-1 * N^-1 folded in (-> y)
 //  6. ModDown conversion (t folded in) + forward column pass   (y -> dh)
-//  7. forward row pass of delta + (acc - delta) * P^-1 + addend  (-> out)
+//  7. forward row pass of delta, (acc - delta) * P^-1            (-> out)
 // Scratch per item (words): L*N (dc, z) + dnum*(L+K)*N (ext) + 2*(L+K)*N
 // (acc) + 2*L*N (dh).
 #include "kernels.h"
@@ -31,6 +32,7 @@ struct KsArgs {
     const uint64_t *modup_mod; // [dnum][alpha][L+K][2]
     const uint64_t *phat_t;    // [K][L][2]  Phat_k * t mod q_i
     const uint64_t *pinv;      // [L][2]
+    const uint64_t *pmont;     // [L]     P * 2^64 mod q_i
     int log2n, L, K, dnum, alpha;
 };
 
@@ -44,11 +46,13 @@ struct KsSrc {
     int64_t ts;
 };
 
-__device__ __forceinline__ uint64_t src_d2(const KsSrc &s, const ModConst &mc, int64_t item,
-                                           int64_t off, int64_t LN) {
-    if (s.d) return s.d[item * s.ds + off];
-    return mul_mod(s.ta[item * s.ts + LN + off], s.tb[item * s.ts + LN + off], mc);
-}
+// Addend of the key switch's output: component c (add_mask bit c) of
+// add + item * is + c * cs, [L][N] each.
+struct KsAdd {
+    const uint64_t *p;
+    int64_t is, cs;
+    int mask;
+};
 
 __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
     const uint64_t m = lo * qneg;
@@ -199,8 +203,15 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t 
 // Inner product with the key: acc[item][c][l] = sum_j e_j * key[j][c][l]
 // with e_j = ext[item][j][l] (< 32q) or, on digit j's own primes, d itself.
 // Keys are in Montgomery form, so the 128-bit sum needs one reduction.
+// On the Q primes the addend y_c of the output, times P, joins the sum
+// (P * 2^64 mod q as its factor): (acc + P y - delta) * P^-1 = (acc - delta)
+// * P^-1 + y exactly, and P y vanishes on the P primes that ModDown reads.
+// With HE-Mult fused (s.ta), y = (a0 b0, a0 b1 + a1 b0) and d = a1 b1.
 // Items vary fastest so a key limb stays in L2 while every item uses it.
-__global__ __launch_bounds__(256) void k_ks_mac(KsArgs a, KsSrc s, const uint64_t *ext,
+// DN > 0: dnum known at compile time, every digit's loads issued before the
+// first product; DN = 0: any dnum, one digit at a time.
+template <int DN>
+__global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc s, KsAdd ad, const uint64_t *ext,
                                                 const uint64_t *key, uint64_t *acc, int n) {
     // grid: x = coefficient pairs, y = l * n + item
     const int N = 1 << a.log2n, LK = a.L + a.K;
@@ -209,28 +220,58 @@ __global__ __launch_bounds__(256) void k_ks_mac(KsArgs a, KsSrc s, const uint64_
     const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (k >= N) return;
     const ModConst mc = a.mc[l];
+    constexpr int B = DN > 0 ? DN : 1;
+    const int dnum = DN > 0 ? DN : a.dnum;
     uint64_t h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
-    for (int jd = 0; jd < a.dnum; ++jd) {
-        const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
-        ulonglong2 e;
-        if (l >= i0 && l < i1) {
-            if (s.d) {
-                e = *(const ulonglong2 *)(s.d + item * s.ds + (int64_t)l * N + k);
-            } else {
-                const int64_t o = item * s.ts + ((int64_t)a.L + l) * N + k;
-                const ulonglong2 x = *(const ulonglong2 *)(s.ta + o), y = *(const ulonglong2 *)(s.tb + o);
-                e = make_ulonglong2(mul_mod(x.x, y.x, mc), mul_mod(x.y, y.y, mc));
-            }
+    // addend terms (Q primes only) and, fused, d = a1 b1
+    ulonglong2 own = make_ulonglong2(0, 0);
+    if (l < a.L) {
+        ulonglong2 y0 = make_ulonglong2(0, 0), y1 = make_ulonglong2(0, 0);
+        if (s.ta) {
+            const int64_t o = item * s.ts + (int64_t)l * N + k, LN = (int64_t)a.L * N;
+            const ulonglong2 a0 = *(const ulonglong2 *)(s.ta + o), b0 = *(const ulonglong2 *)(s.tb + o);
+            const ulonglong2 a1 = *(const ulonglong2 *)(s.ta + o + LN);
+            const ulonglong2 b1 = *(const ulonglong2 *)(s.tb + o + LN);
+            own = make_ulonglong2(mul_mod(a1.x, b1.x, mc), mul_mod(a1.y, b1.y, mc));
+            y0 = make_ulonglong2(mul_mod(a0.x, b0.x, mc), mul_mod(a0.y, b0.y, mc));
+            y1 = make_ulonglong2(add_mod(mul_mod(a0.x, b1.x, mc), mul_mod(a1.x, b0.x, mc), mc.q),
+                                 add_mod(mul_mod(a0.y, b1.y, mc), mul_mod(a1.y, b0.y, mc), mc.q));
         } else {
-            e = *(const ulonglong2 *)(ext + ((item * a.dnum + jd) * LK + l) * N + k);
+            own = *(const ulonglong2 *)(s.d + item * s.ds + (int64_t)l * N + k);
+            if (ad.p) {
+                const uint64_t *base = ad.p + item * ad.is + (int64_t)l * N + k;
+                if (ad.mask & 1) y0 = *(const ulonglong2 *)base;
+                if (ad.mask & 2) y1 = *(const ulonglong2 *)(base + ad.cs);
+            }
         }
-        const ulonglong2 w0 = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd) * LK + l) * N + k));
-        const ulonglong2 w1 = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd + 1) * LK + l) * N + k));
+        const uint64_t pm = a.pmont[l];
         uint64_t p;
-        p = e.x * w0.x; l0a += p; h0a += __umul64hi(e.x, w0.x) + (l0a < p);
-        p = e.y * w0.y; l0b += p; h0b += __umul64hi(e.y, w0.y) + (l0b < p);
-        p = e.x * w1.x; l1a += p; h1a += __umul64hi(e.x, w1.x) + (l1a < p);
-        p = e.y * w1.y; l1b += p; h1b += __umul64hi(e.y, w1.y) + (l1b < p);
+        p = y0.x * pm; l0a += p; h0a += __umul64hi(y0.x, pm) + (l0a < p);
+        p = y0.y * pm; l0b += p; h0b += __umul64hi(y0.y, pm) + (l0b < p);
+        p = y1.x * pm; l1a += p; h1a += __umul64hi(y1.x, pm) + (l1a < p);
+        p = y1.y * pm; l1b += p; h1b += __umul64hi(y1.y, pm) + (l1b < p);
+    }
+    for (int j0 = 0; j0 < dnum; j0 += B) {
+        ulonglong2 e[B], w0[B], w1[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int jd = j0 + u;
+            const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
+            w0[u] = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd) * LK + l) * N + k));
+            w1[u] = __ldg((const ulonglong2 *)(key + ((int64_t)(2 * jd + 1) * LK + l) * N + k));
+            if (l >= i0 && l < i1)
+                e[u] = own;
+            else
+                e[u] = *(const ulonglong2 *)(ext + ((item * dnum + jd) * LK + l) * N + k);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            uint64_t p;
+            p = e[u].x * w0[u].x; l0a += p; h0a += __umul64hi(e[u].x, w0[u].x) + (l0a < p);
+            p = e[u].y * w0[u].y; l0b += p; h0b += __umul64hi(e[u].y, w0[u].y) + (l0b < p);
+            p = e[u].x * w1[u].x; l1a += p; h1a += __umul64hi(e[u].x, w1[u].x) + (l1a < p);
+            p = e[u].y * w1[u].y; l1b += p; h1b += __umul64hi(e[u].y, w1[u].y) + (l1b < p);
+        }
     }
     uint64_t *o0 = acc + (item * 2 * LK + l) * N + k;
     uint64_t *o1 = o0 + (int64_t)LK * N;
@@ -283,66 +324,30 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_moddown_cols(KsArgs a, const
     }
 }
 
-// Forward row pass of delta, then out = (acc - delta) * P^-1 (+ addend).
+// Forward row pass of delta, then out = (acc - delta) * P^-1 (the addend is
+// already in acc, times P).
 template <int LR>
 __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
-                                                               const uint64_t *dh,
-                                                               const uint64_t *add, int64_t add_is,
-                                                               int64_t add_cs, int add_mask,
-                                                               KsSrc s, uint64_t *out) {
+                                                               const uint64_t *dh, uint64_t *out) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
     __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L, LK = L + a.K;
-    const int ic = blockIdx.y / L, i = blockIdx.y - ic * L;
-    const int item = ic >> 1, c = ic & 1;
-    const ModConst mc = a.mc[i];
-    const uint64_t q = mc.q;
+    const int ic = blockIdx.y / L, i = blockIdx.y - ic * L;  // ic = item * 2 + component
+    const uint64_t q = a.mc[i].q;
     const TwPair *tw = (const TwPair *)(a.tw + (int64_t)i * 4 * N);
     const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
     const int64_t rofs = (int64_t)row * M;
     const uint64_t *src = dh + ((int64_t)ic * L + i) * N + rofs;
-    const uint64_t *x = acc + ((int64_t)ic * LK + i) * N + rofs;
-    const bool has_add = add && ((add_mask >> c) & 1);
-    const uint64_t *ad = has_add ? add + item * add_is + c * add_cs + (int64_t)i * N + rofs : nullptr;
-    // operands of the epilogue, fetched before the transform
-    uint64_t xa[8], xd[8];
-    const bool tensor = s.ta != nullptr;
-    const int64_t LN = (int64_t)L * N, toff = item * s.ts + (int64_t)i * N + rofs;
-    load8(xa, x + 8 * j);
-    if (tensor) {  // d0 = a0 b0, d1 = a0 b1 + a1 b0
-        uint64_t a0[8], b0[8];
-        load8(a0, s.ta + toff + 8 * j);
-        load8(b0, s.tb + toff + 8 * j);
-        if (c == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) xd[e] = mul_mod(a0[e], b0[e], mc);
-        } else {
-            uint64_t a1[8], b1[8];
-            load8(a1, s.ta + toff + LN + 8 * j);
-            load8(b1, s.tb + toff + LN + 8 * j);
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                xd[e] = add_mod(mul_mod(a0[e], b1[e], mc), mul_mod(a1[e], b0[e], mc), q);
-        }
-    } else if (has_add) {
-        load8(xd, ad + 8 * j);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) xd[e] = 0;
-    }
-    uint64_t v[8];
+    uint64_t xa[8], v[8];
+    load8(xa, acc + ((int64_t)ic * LK + i) * N + rofs + 8 * j);  // fetched before the transform
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = src[Pass<LR>::first(j, e)];
     fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
     const uint64_t w = a.pinv[2 * i], ws = a.pinv[2 * i + 1];
-    uint64_t *o = out + ((int64_t)ic * L + i) * N + rofs;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        // delta < 32q unreduced: (acc + 32q - delta) * P^-1, fully reduced
-        const uint64_t r = mul_shoup(xa[e] + 32 * q - v[e], w, ws, q);
-        v[e] = add_mod(r, xd[e], q);
-    }
-    store8(o + 8 * j, v);
+    for (int e = 0; e < 8; ++e)  // delta < 32q unreduced: (acc + 32q - delta) * P^-1, fully reduced
+        v[e] = mul_shoup(xa[e] + 32 * q - v[e], w, ws, q);
+    store8(out + ((int64_t)ic * L + i) * N + rofs + 8 * j, v);
 }
 
 template <int LC, int LR>
@@ -369,7 +374,17 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     k_ks_rows_fwd<LR><<<dim3(gr, n * c.dnum * LK), kNttThreads, 0, st>>>(a, ext);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_mac", st);
-    k_ks_mac<<<dim3((unsigned)((N / 2 + 255) / 256), (unsigned)(n * LK)), 256, 0, st>>>(a, s, ext, key, acc, n);
+    {
+        const dim3 g((unsigned)((N / 2 + 255) / 256), (unsigned)(n * LK));
+        const KsAdd ad{add, add_is, add_cs, add_mask};
+        switch (c.dnum) {
+            case 2: k_ks_mac<2><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 3: k_ks_mac<3><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 4: k_ks_mac<4><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 5: k_ks_mac<5><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            default: k_ks_mac<0><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+        }
+    }
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_intt_rows", st);
     k_ks_intt_rows<LR><<<dim3(gr, n * 2 * K), kNttThreads, 0, st>>>(a, acc + L * N, LK * N,
@@ -384,8 +399,7 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     k_ks_moddown_cols<LC><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_final", st);
-    k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, add, add_is,
-                                                                      add_cs, add_mask, s, out);
+    k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, out);
     prof_end(c, r, st);
     return cudaGetLastError();
 }
@@ -417,6 +431,7 @@ static KsArgs ks_args(const Ctx &c) {
     a.modup_mod = h->d.modup_mod;
     a.phat_t = h->d.md_phat_t;
     a.pinv = h->d.md_pinv;
+    a.pmont = h->d.p_mont;
     a.log2n = c.log2n;
     a.L = c.L;
     a.K = c.K;
