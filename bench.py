@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--instances", type=int, default=64, help="c4: SpMVs per batched step")
     ap.add_argument("--pool", type=int, default=32, help="c5: distinct instances")
     ap.add_argument("--requests", type=int, default=10000, help="c5: Poisson requests")
@@ -534,6 +535,12 @@ def main():
     As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 1000 * rank + i) for i, m in enumerate(ms)]
     Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=xx, seed=3 + 1000 * rank + i)
           for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
+    # schedule autotuning (batch sizes, NTT split; results are unchanged)
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = ctx.autotune(ms, As, Xs, reps=3)
+        tune["seconds"] = time.perf_counter() - t0
     if batched:
         ys = ctx.spmv_batched(ms, As, Xs)
 
@@ -660,6 +667,7 @@ def main():
         "clocks": clk,
         "kernels": kernels,
     }
+    line["autotune"] = tune
     line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -358,6 +358,40 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
 int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt,
                              uint64_t *out, size_t n, void *stream);
 
+/* ------------------------------------------------------------ autotuning */
+
+/* Schedule of an evaluation.  None of these changes a result bit: they set
+ * how many ciphertexts share one launch of each stage and how the NTTs of
+ * the fused key switch are split into their column and row passes. */
+typedef struct hespmv_tuning {
+    int32_t mult_batch; /* HE-Mult stage: ciphertexts per fused key switch (0: 32)        */
+    int32_t rot_batch;  /* totalSum: ciphertexts per batched rotation round
+                           (0: 32 at N = 2^15, else 64)                                  */
+    int32_t ntt_split;  /* fused key switch NTT split: 0 = default, 1 = alternative
+                           (N = 2^LC x 2^LR with LC and LR exchanged or shifted by one)  */
+    int32_t reserved;
+    double ms;          /* hespmv_autotune: device time of one evaluation             */
+} hespmv_tuning;
+
+/* Apply a schedule (e.g. one cached from an earlier hespmv_autotune).  Waits
+ * for the device and drops captured graphs.  HESPMV_E_INVALID for negative
+ * or huge batch sizes or a split the ring does not offer. */
+int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t);
+int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t);
+
+/* Autotuner: times the evaluation of the given SpMVs (as hespmv_spmv_batched
+ * would run them, into its own result buffers, on its own stream) under
+ * candidate schedules -- each NTT split, then HE-Mult batches 1, 2, 4, ...
+ * up to 128, then rotation round widths 4, 8, ... up to 512 (capped by the
+ * chunk counts) -- by coordinate descent from the
+ * default, `reps` timed evaluations after one warm-up each, skipping any
+ * whose workspace would not fit in free device memory.  Applies the fastest
+ * and returns it in *best; tried[0 .. min(cap, *n_tried)) lists every
+ * setting timed (effective batch sizes; ms = -1: skipped).  Synchronous. */
+int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
+                    const hespmv_ctbatch *const *A, const hespmv_ctbatch *const *X, int32_t reps,
+                    hespmv_tuning *best, hespmv_tuning *tried, size_t cap, size_t *n_tried);
+
 /* Evaluations (hespmv_spmv, hespmv_spmv_batched, hespmv_spmv_host) are
  * recorded once into a CUDA graph per set of matrices, buffers and workspace
  * and replayed afterwards (one launch per evaluation).  enable = 0 makes

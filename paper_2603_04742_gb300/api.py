@@ -87,6 +87,7 @@ class Context:
             raise B.HespmvError(rc, msg)
         self.N = 1 << log2n
         self.L, self.K, self.dnum, self.t = L, K, dnum, t
+        self.device = device
 
     def close(self):
         if getattr(self, "h", None):
@@ -197,6 +198,67 @@ class Context:
     def decrypt_slots(self, b, index=0):
         out = np.zeros(self.N, dtype=np.uint64)
         self.check(self.lib.hespmv_decrypt_slots(self.h, b.h, index, _u64p(out)))
+        return out
+
+    # ---- schedule tuning ----
+    def set_tuning(self, mult_batch=0, rot_batch=0, ntt_split=0):
+        t = B.hespmv_tuning(mult_batch, rot_batch, ntt_split, 0, 0.0)
+        self.check(self.lib.hespmv_set_tuning(self.h, byref(t)))
+
+    def get_tuning(self):
+        t = B.hespmv_tuning()
+        self.check(self.lib.hespmv_get_tuning(self.h, byref(t)))
+        return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch, "ntt_split": t.ntt_split}
+
+    def tuning_key(self, ms):
+        """Cache key of a workload: device, ring and the stage sizes that the
+        schedule depends on (chunks, rotation chunks, instances)."""
+        import torch
+        name = torch.cuda.get_device_name(self.device) if self.device >= 0 else "host"
+        chunks = sum(m.n_chunks for m in ms)
+        rot = sum(int((m.chunks()[1] > 1).sum()) for m in ms)
+        return "%s|N=%d|L=%d|K=%d|dnum=%d|inst=%d|chunks=%d|rot=%d" % (
+            name, self.N, self.L, self.K, self.dnum, len(ms), chunks, rot)
+
+    def autotune(self, ms, As, Xs, reps=3, cache=None):
+        """Time candidate schedules on these SpMVs (hespmv_autotune), apply the
+        fastest and return {"best": ..., "tried": [...], "cached": bool}.
+        With `cache` (a JSON file path) a result stored under the same
+        tuning_key is applied without timing, and new results are stored."""
+        import json
+        import os
+        key = self.tuning_key(ms)
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                b = table[key]["best"]
+                self.set_tuning(b["mult_batch"], b["rot_batch"], b["ntt_split"])
+                return {"best": b, "tried": table[key].get("tried", []), "cached": True}
+        n = len(ms)
+        arr = c_void_p * n
+        mh = arr(*[m.h for m in ms])
+        ah = arr(*[a.h for a in As])
+        xh = arr(*[x.h for x in Xs])
+        best = B.hespmv_tuning()
+        cap = 64
+        tried = (B.hespmv_tuning * cap)()
+        nt = c_size_t()
+        self.check(self.lib.hespmv_autotune(self.h, n, mh, ah, xh, reps, byref(best), tried, cap,
+                                            byref(nt)))
+
+        def as_dict(t):
+            return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch,
+                    "ntt_split": t.ntt_split, "ms": t.ms}
+        out = {"best": as_dict(best), "tried": [as_dict(tried[i]) for i in range(min(cap, nt.value))],
+               "cached": False}
+        if cache:
+            table[key] = {"best": out["best"], "tried": out["tried"]}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
         return out
 
     def set_graphs(self, on=True):

@@ -44,6 +44,11 @@ class hespmv_params(ctypes.Structure):
                 ("free", FREE_FN), ("alloc_user", c_void_p)]
 
 
+class hespmv_tuning(ctypes.Structure):
+    _fields_ = [("mult_batch", c_int32), ("rot_batch", c_int32), ("ntt_split", c_int32),
+                ("reserved", c_int32), ("ms", ctypes.c_double)]
+
+
 u64p = POINTER(c_uint64)
 i64p = POINTER(c_int64)
 i32p = POINTER(c_int32)
@@ -76,6 +81,11 @@ SIGNATURES = {
     "hespmv_ctbatch_upload": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_download": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_serialize": (c_int, [c_void_p, c_void_p, c_size_t, szp]),
+    "hespmv_set_tuning": (c_int, [c_void_p, POINTER(hespmv_tuning)]),
+    "hespmv_get_tuning": (c_int, [c_void_p, POINTER(hespmv_tuning)]),
+    "hespmv_autotune": (c_int, [c_void_p, c_size_t, POINTER(c_void_p), POINTER(c_void_p),
+                                POINTER(c_void_p), c_int32, POINTER(hespmv_tuning),
+                                POINTER(hespmv_tuning), c_size_t, szp]),
     "hespmv_ctbatch_deserialize": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
     "hespmv_encrypt": (c_int, [c_void_p, c_void_p, c_int32, i64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_spmv": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p), c_void_p]),

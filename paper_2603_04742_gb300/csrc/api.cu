@@ -440,12 +440,13 @@ int prepare_matrix(hespmv_ctx *ctx, const hespmv_cssc *cm, cudaStream_t st) {
 }
 
 // batch sizes and workspace bytes of an evaluation over the given chunk counts
-void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, size_t tune_G, SpmvPrep &pp) {
+void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &pp) {
+    const size_t tune_G = c.c->tune_G, tune_GR = c.c->tune_GR;
     const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
     pp.total_chunks = total_chunks;
     pp.rot_chunks = rot_chunks;
     pp.G = std::max<size_t>(1, std::min<size_t>(total_chunks, tune_G ? tune_G : 32));
-    pp.GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, c.N >= (1 << 15) ? 32 : 64));
+    pp.GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, tune_GR ? tune_GR : c.N >= (1 << 15) ? 32 : 64));
     const size_t prod_w = total_chunks * CT;
     const size_t mult_w = pp.G * 3 * LN + ks_words(c, pp.G);
     const size_t rot_w = rot_chunks ? 4 * pp.GR * CT + ks_words(c, pp.GR) : 0;
@@ -464,7 +465,7 @@ int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, S
         total += ms[i]->plan.chunks.size();
         for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
     }
-    spmv_sizes(c, total, rot, ctx->tune_G, pp);
+    spmv_sizes(c, total, rot, pp);
     pp.rp = nullptr;
     if (rot) {
         pp.rp = rotation_plan(ctx, n_inst, ms, (int)pp.GR);
@@ -1563,6 +1564,190 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
     return HESPMV_OK;
 }
 
+// ------------------------------------------------------------ autotuning
+}  // extern "C"
+
+namespace {
+
+void drop_graphs(hespmv_ctx *ctx) {
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+struct TuneState {
+    size_t G, GR;
+    int split;
+};
+
+void apply_tuning(hespmv_ctx *ctx, const TuneState &s) {
+    if (ctx->tune_G != s.G || ctx->tune_GR != s.GR || ctx->ks_split != s.split) drop_graphs(ctx);
+    ctx->tune_G = s.G;
+    ctx->tune_GR = s.GR;
+    ctx->ks_split = s.split;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t) {
+    if (!ctx || !t) return HESPMV_E_INVALID;
+    if (t->mult_batch < 0 || t->rot_batch < 0 || t->mult_batch > 4096 || t->rot_batch > 4096)
+        FAIL(HESPMV_E_INVALID, "batch sizes must be in [0, 4096]");
+    if (t->ntt_split < 0 || t->ntt_split >= ks_split_variants(view(ctx)))
+        FAIL(HESPMV_E_INVALID, "no such NTT split for this ring");
+    if (ctx->device >= 0) {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        apply_tuning(ctx, {(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split});
+    } else {
+        apply_tuning(ctx, {(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split});
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t) {
+    if (!ctx || !t) return HESPMV_E_INVALID;
+    *t = hespmv_tuning{};
+    t->mult_batch = (int32_t)ctx->tune_G;
+    t->rot_batch = (int32_t)ctx->tune_GR;
+    t->ntt_split = ctx->ks_split;
+    t->ms = 0;
+    return HESPMV_OK;
+}
+
+int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
+                    const hespmv_ctbatch *const *A, const hespmv_ctbatch *const *X, int32_t reps,
+                    hespmv_tuning *best, hespmv_tuning *tried, size_t cap, size_t *n_tried) {
+    if (!ctx || !n || !m || !A || !X || !best || reps < 1) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    std::vector<const uint64_t *> a(n), x(n);
+    std::vector<uint64_t *> out(n);
+    std::vector<hespmv_ctbatch *> ys(n, nullptr);
+    size_t total = 0, rot = 0;
+    auto release = [&]() {
+        for (hespmv_ctbatch *y : ys) hespmv_ctbatch_free(y);
+    };
+    for (size_t i = 0; i < n; ++i) {
+        if (!m[i] || !A[i] || !X[i]) {
+            release();
+            FAIL(HESPMV_E_INVALID, "null handle");
+        }
+        const size_t nc = m[i]->plan.chunks.size();
+        if (A[i]->n < nc || X[i]->n < nc) {
+            release();
+            FAIL(HESPMV_E_INVALID, "operand batches are smaller than the chunk count");
+        }
+        int rc = batch_new(ctx, m[i]->plan.parts.size(), &ys[i]);
+        if (rc) {
+            release();
+            return rc;
+        }
+        a[i] = A[i]->data;
+        x[i] = X[i]->data;
+        out[i] = ys[i]->data;
+        total += nc;
+        for (const Chunk &ch : m[i]->plan.chunks) rot += ch.c > 1;
+    }
+    const TuneState orig{ctx->tune_G, ctx->tune_GR, ctx->ks_split};
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    std::vector<hespmv_tuning> log;
+    std::string err;
+    int err_rc = HESPMV_OK;
+    // time one setting; returns ms, or -1 when its workspace would not fit
+    auto measure = [&](const TuneState &s) -> double {
+        apply_tuning(ctx, s);
+        SpmvPrep pp;
+        spmv_sizes(c, total, rot, pp);
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        hespmv_tuning rec{};
+        rec.mult_batch = (int32_t)pp.G;
+        rec.rot_batch = (int32_t)pp.GR;
+        rec.ntt_split = s.split;
+        if (pp.need_bytes > ctx->ws_bytes && pp.need_bytes - ctx->ws_bytes > free_b / 10 * 9) {
+            rec.ms = -1;
+            log.push_back(rec);
+            return -1;
+        }
+        int rc = spmv_core(ctx, n, m, a.data(), x.data(), out.data(), st);  // warm-up / capture
+        if (rc == HESPMV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = HESPMV_E_CUDA;
+        if (rc == HESPMV_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = HESPMV_E_CUDA;
+        for (int32_t r = 0; rc == HESPMV_OK && r < reps; ++r)
+            rc = spmv_core(ctx, n, m, a.data(), x.data(), out.data(), st);
+        float ms = 0;
+        if (rc == HESPMV_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = HESPMV_E_CUDA;
+        if (rc != HESPMV_OK) {
+            err_rc = rc;
+            err = ctx->err.empty() ? "evaluation failed while tuning" : ctx->err;
+            return -2;
+        }
+        rec.ms = ms / reps;
+        log.push_back(rec);
+        return rec.ms;
+    };
+    TuneState cur{0, 0, 0}, bestS = cur;
+    double best_ms = ok ? measure(cur) : -2;
+    if (best_ms < 0 && err_rc == HESPMV_OK && ok) {
+        err_rc = HESPMV_E_NOMEM;
+        err = "the default schedule does not fit in device memory";
+    }
+    if (!ok && err_rc == HESPMV_OK) {
+        err_rc = HESPMV_E_CUDA;
+        err = "stream/event creation failed";
+    }
+    auto consider = [&](const TuneState &s) {
+        if (err_rc != HESPMV_OK) return;
+        const double t = measure(s);
+        if (t >= 0 && t < best_ms) {
+            best_ms = t;
+            bestS = s;
+        }
+    };
+    // coordinate descent: NTT split, then the HE-Mult batch, then the rotation round width
+    for (int v = 1; v < ks_split_variants(c); ++v) consider({bestS.G, bestS.GR, v});
+    {
+        std::vector<size_t> gs;
+        for (size_t v = 1; v < 128 && v < total; v *= 2) gs.push_back(v);
+        gs.push_back(std::min<size_t>(total, 128));
+        const TuneState base = bestS;
+        for (size_t v : gs) consider({v, base.GR, base.split});
+    }
+    if (rot > 0) {
+        std::vector<size_t> grs;
+        for (size_t v = 4; v < 512 && v < rot; v *= 2) grs.push_back(v);
+        grs.push_back(std::min<size_t>(rot, 512));
+        const TuneState base = bestS;
+        for (size_t v : grs) consider({base.G, v, base.split});
+    }
+    if (st) cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    release();
+    if (err_rc != HESPMV_OK) {
+        apply_tuning(ctx, orig);
+        FAIL(err_rc, err);
+    }
+    apply_tuning(ctx, bestS);
+    best->mult_batch = (int32_t)bestS.G;
+    best->rot_batch = (int32_t)bestS.GR;
+    best->ntt_split = bestS.split;
+    best->reserved = 0;
+    best->ms = best_ms;
+    if (n_tried) *n_tried = log.size();
+    for (size_t i = 0; tried && i < log.size() && i < cap; ++i) tried[i] = log[i];
+    return HESPMV_OK;
+}
+
 int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable) {
     if (!ctx) return HESPMV_E_INVALID;
     ctx->use_graphs = enable != 0;
@@ -1740,7 +1925,7 @@ namespace {
 
 const size_t kServeIdxCap = 1 << 20;  // schedule entries per slot (4 MiB)
 
-size_t slot_need(const Ctx &c, const std::vector<ServeReq> &reqs, size_t tune_G) {
+size_t slot_need(const Ctx &c, const std::vector<ServeReq> &reqs) {
     size_t total = 0, rot = 0, drop = 0;
     for (const ServeReq &r : reqs) {
         total += r.m->plan.chunks.size();
@@ -1748,7 +1933,7 @@ size_t slot_need(const Ctx &c, const std::vector<ServeReq> &reqs, size_t tune_G)
         if (!r.y) drop += r.m->plan.parts.size();
     }
     SpmvPrep pp;
-    spmv_sizes(c, total, rot, tune_G, pp);
+    spmv_sizes(c, total, rot, pp);
     return pp.need_bytes + drop * 2 * (size_t)c.L * c.N * 8;
 }
 
@@ -1770,7 +1955,7 @@ int serve_launch(hespmv_server *s, ServeSlot &sl, std::vector<ServeReq> &batch) 
         for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
     }
     SpmvPrep pp;
-    spmv_sizes(c, total, rot, ctx->tune_G, pp);
+    spmv_sizes(c, total, rot, pp);
     uint64_t *dropbuf = sl.ws + pp.need_bytes / 8;
     for (size_t i = 0; i < n; ++i) {
         if (batch[i].y) {
@@ -1836,7 +2021,7 @@ void serve_loop(hespmv_server *s) {
                 std::lock_guard<std::mutex> lock(s->mu);
                 while (!s->queue.empty() && (int32_t)batch.size() < s->max_batch) {
                     batch.push_back(s->queue.front());
-                    if (slot_need(c, batch, ctx->tune_G) > sl.cap) {
+                    if (slot_need(c, batch) > sl.cap) {
                         batch.pop_back();
                         break;
                     }
@@ -1948,7 +2133,7 @@ int hespmv_server_submit(hespmv_server *s, const hespmv_cssc *m, const hespmv_ct
     r.y = y ? y->data : nullptr;
     const Ctx c = view(ctx);
     std::vector<ServeReq> one{r};
-    if (slot_need(c, one, ctx->tune_G) > s->slots[0].cap) {
+    if (slot_need(c, one) > s->slots[0].cap) {
         std::lock_guard<std::mutex> lock(s->mu);
         ++s->rejected;
         ctx->err = "request needs more device memory than a serving slot holds";

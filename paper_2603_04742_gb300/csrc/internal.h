@@ -192,7 +192,10 @@ struct hespmv_ctx {
     bool use_graphs = true;
     std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;
-    size_t tune_G = 0;  // HE-Mult batch size (0: default)
+    // schedule choices (0: default); results do not depend on them
+    size_t tune_G = 0;   // HE-Mult batch: ciphertexts per fused key switch
+    size_t tune_GR = 0;  // totalSum round width: ciphertexts per rotation round
+    int ks_split = 0;    // fused key switch: NTT split variant (column/row pass sizes)
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;
@@ -220,8 +223,9 @@ namespace hespmv {
 struct Ctx {
     const hespmv_ctx *c;
     int N, L, K, dnum, alpha, log2n;
+    int ks_split;
 };
 inline Ctx view(const hespmv_ctx *c) {
-    return Ctx{c, c->h.N, c->h.L, c->h.K, c->h.dnum, c->h.alpha, c->h.log2n};
+    return Ctx{c, c->h.N, c->h.L, c->h.K, c->h.dnum, c->h.alpha, c->h.log2n, c->ks_split};
 }
 }  // namespace hespmv

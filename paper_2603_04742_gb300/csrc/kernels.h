@@ -53,6 +53,8 @@ cudaError_t op_moddown_final(const Ctx &c, const uint64_t *acc, const uint64_t *
 
 // fused hybrid key switch (ks.cu), keys in Montgomery form
 bool ks_fused_supported(const Ctx &c);
+// number of NTT split variants the fused key switch offers for this ring
+int ks_split_variants(const Ctx &c);
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);

@@ -408,18 +408,25 @@ bool ks_fused_supported(const Ctx &c) {
     return c.log2n >= 11 && c.log2n <= 15 && c.alpha <= 4 && c.K <= 4;
 }
 
+// NTT split of the two passes, N = 2^LC (column pass) x 2^LR (row pass):
+// variant 0 is the default, variant 1 the alternative the autotuner tries.
 static cudaError_t ks_dispatch(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
                                uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                                int add_mask, int m, uint64_t *scratch, cudaStream_t st) {
+#define KS_CALL(LC, LR) ks_fused<LC, LR>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st)
+    const bool alt = c.ks_split == 1;
     switch (c.log2n) {
-        case 15: return ks_fused<7, 8>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
-        case 14: return ks_fused<7, 7>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
-        case 13: return ks_fused<6, 7>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
-        case 12: return ks_fused<6, 6>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
-        case 11: return ks_fused<5, 6>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st);
+        case 15: return alt ? KS_CALL(8, 7) : KS_CALL(7, 8);
+        case 14: return alt ? KS_CALL(6, 8) : KS_CALL(7, 7);
+        case 13: return alt ? KS_CALL(7, 6) : KS_CALL(6, 7);
+        case 12: return alt ? KS_CALL(5, 7) : KS_CALL(6, 6);
+        case 11: return alt ? KS_CALL(6, 5) : KS_CALL(5, 6);
         default: return cudaErrorInvalidValue;
     }
+#undef KS_CALL
 }
+
+int ks_split_variants(const Ctx &c) { return ks_fused_supported(c) ? 2 : 1; }
 
 static KsArgs ks_args(const Ctx &c) {
     const hespmv_ctx *h = c.c;
