@@ -34,6 +34,7 @@ def csr_to_cssc(rows, rowptr, colidx, vals) -> CSSC:
     Lmax = max(nnz_row) if rows else 0
     # stable sort by descending nnz: ties keep ascending row order
     RM = sorted(range(rows), key=lambda i: (-nnz_row[i], i))
+    real = np.asarray(vals).dtype.kind == "f"   # real values (CKKS) or integers
     V, C = [], []
     CP = [0] * (Lmax + 1)
     for j in range(Lmax):
@@ -42,10 +43,10 @@ def csr_to_cssc(rows, rowptr, colidx, vals) -> CSSC:
             i = RM[p]
             if j < nnz_row[i]:
                 k = rowptr[i] + j
-                V.append(int(vals[k]))
+                V.append(float(vals[k]) if real else int(vals[k]))
                 C.append(int(colidx[k]))
     CP[Lmax] = len(V)
-    return CSSC(np.array(V, dtype=np.int64), np.array(C, dtype=np.int64),
+    return CSSC(np.array(V, dtype=np.float64 if real else np.int64), np.array(C, dtype=np.int64),
                 np.array(CP, dtype=np.int64), np.array(RM, dtype=np.int64), rows)
 
 
@@ -69,7 +70,7 @@ def generate_chunks(cssc: CSSC, s: int) -> List[Chunk]:
         while i < nC and h * (i - start + 1) <= s:
             i += 1
         c = i - start
-        vals = np.zeros(h * c, dtype=np.int64)
+        vals = np.zeros(h * c, dtype=cssc.VA.dtype)
         cis = np.full(h * c, -1, dtype=np.int64)
         for qcol in range(c):
             col = start + qcol
@@ -83,7 +84,8 @@ def generate_chunks(cssc: CSSC, s: int) -> List[Chunk]:
 def reorg_vector(v, chunks: List[Chunk]) -> List[np.ndarray]:
     out = []
     for ch in chunks:
-        one = np.zeros(len(ch.colidx), dtype=np.int64)
+        one = np.zeros(len(ch.colidx), dtype=np.float64 if np.asarray(v).dtype.kind == "f"
+                       else np.int64)
         for k, idx in enumerate(ch.colidx):
             if idx >= 0:
                 one[k] = v[idx]

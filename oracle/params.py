@@ -97,7 +97,12 @@ def bitrev(x: int, bits: int) -> int:
 
 @dataclass
 class Params:
-    """A BGV-RNS parameter set (Q primes, P primes, digits, plaintext t)."""
+    """An RNS parameter set (Q primes, P primes, digits, plaintext t).
+
+    scheme "bgv": integer slots mod t.  scheme "ckks": real slots at scale
+    2^scale_bits; t is then 1 in every formula (keys, encryption, ModDown),
+    which turns the BGV error terms t*e into e and the key-switching
+    correction into the plain ModDown of CKKS."""
     log2n: int
     L: int
     K: int
@@ -108,15 +113,26 @@ class Params:
     q: List[int] = field(default_factory=list)   # L + K moduli, Q first
     psi: List[int] = field(default_factory=list)
     zeta: int = 0           # primitive 2N-th root mod t
+    scheme: str = "bgv"
+    scale_bits: int = 40    # CKKS: matrix and vector scale
+    mask_scale_bits: int = 30  # CKKS: scale of the 0/1 masks
 
     def __post_init__(self):
         N = self.N
         if self.slots == 0:
             self.slots = N // 2
         assert 1 <= self.slots <= N // 2
-        assert (self.t - 1) % (2 * N) == 0 and is_prime(self.t)
+        if self.scheme == "ckks":
+            self.t = 1
+            self.zeta = 1
+        else:
+            assert self.scheme == "bgv"
+            assert (self.t - 1) % (2 * N) == 0 and is_prime(self.t)
         self.alpha = -(-self.L // self.dnum)
         assert -(-self.L // self.alpha) == self.dnum, "every digit must be non-empty"
+        # CKKS adds the key-switching noise (about N * Q_j / P) to the message
+        # itself, so P must cover a digit: K >= alpha primes of equal size
+        assert self.scheme != "ckks" or self.K >= self.alpha, "CKKS needs K >= alpha"
         if not self.q:
             self.q = ntt_primes(N, self.bits, self.L + self.K)
         if not self.psi:

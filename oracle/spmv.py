@@ -142,3 +142,16 @@ def decrypt_result(orc: Oracle, plan: SpmvPlan, results):
             v = int(slots[idx])
             out[part.row0 + int(rm)] = v - t if 2 * v > t else v
     return out
+
+
+def decrypt_result_real(orc, plan: SpmvPlan, results):
+    """CKKS: decrypt, decode at the product scale (matrix x vector x mask)
+    and undo the row permutation."""
+    p = orc.p
+    total_bits = 2 * p.scale_bits + p.mask_scale_bits
+    out = np.zeros(plan.rows, dtype=np.float64)
+    for part, ct in zip(plan.parts, results):
+        z = orc.decode_ct(ct, len(part.cssc.RM), total_bits)
+        for idx, rm in enumerate(part.cssc.RM):
+            out[part.row0 + int(rm)] = z[idx]
+    return out
