@@ -90,7 +90,21 @@ typedef struct hespmv_params {
     hespmv_alloc_fn alloc; /* optional device allocator (NULL: cudaMalloc)     */
     hespmv_free_fn free;   /* its matching free                                 */
     void *alloc_user;      /* passed back to alloc/free                         */
+    int32_t scheme;        /* HESPMV_SCHEME_BGV (0, integers mod t) or
+                              HESPMV_SCHEME_CKKS (real values; t must be 0)     */
+    int32_t scale_bits;    /* CKKS: matrix and vector scale 2^scale_bits, 10..60 */
+    int32_t mask_scale_bits; /* CKKS: scale of the 0/1 masks, 1..60            */
+    int32_t reserved;
 } hespmv_params;
+
+/* Schemes.  CKKS (the approximate scheme the paper names as the alternative
+ * for real values, Section 6) runs the same circuit: every key, encryption
+ * and key switch is the BGV one with t = 1 (errors e instead of t*e, plain
+ * ModDown), no rescaling (all L primes throughout), and a SpMV result
+ * carries scale 2^(2 scale_bits + mask_scale_bits).  It needs K >= alpha so
+ * that P covers a key-switching digit. */
+#define HESPMV_SCHEME_BGV 0
+#define HESPMV_SCHEME_CKKS 1
 
 typedef struct hespmv_ctx hespmv_ctx;         /* scheme, tables, keys, workspace */
 typedef struct hespmv_cssc hespmv_cssc;       /* CSSC + partitions + chunk plan */
@@ -142,7 +156,9 @@ int hespmv_key_export(hespmv_ctx *ctx, int32_t which, uint32_t galois_elt, uint6
  * Lmax+1), partition it into blocks of at most s rows (Section 4.7) and cut
  * each block into chunks (Algorithm 2, padded-area capacity h*c <= s).
  * rowptr[rows+1], colidx[nnz] strictly ascending within each row, values
- * vals[nnz] (integers; fixed-point values are quantised by the caller).
+ * vals[nnz] (integers; fixed-point values are quantised by the caller; NULL
+ * records the pattern only, for CKKS contexts, whose values are given to
+ * hespmv_encrypt_real).
  * max_abs_x > 0 declares |x_j| <= max_abs_x; if any row could then reach
  * t/2 the call fails with HESPMV_E_RANGE.  max_abs_x <= 0 skips the check.
  * Host only (no device work).  Release with hespmv_cssc_free. */
@@ -221,6 +237,26 @@ int hespmv_ctbatch_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hes
 int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
                    uint64_t seed, hespmv_ctbatch **out);
 
+/* CKKS contexts: encode and encrypt real values (Client A: the matrix values
+ * in the CSR order given to hespmv_encode_cssc, nnz entries; Client B: x,
+ * cols entries), each chunk's slots encoded at 2^scale_bits (the inverse
+ * canonical embedding, rounded half away from zero; see hespmv_ckks_encode)
+ * and encrypted as hespmv_encrypt does.  HESPMV_E_RANGE if a coefficient
+ * would reach 2^62.  Plans read back by hespmv_cssc_deserialize lack the
+ * CSR positions and refuse the matrix.  Synchronous. */
+int hespmv_encrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const double *values,
+                        uint64_t seed, hespmv_ctbatch **out);
+/* CKKS plaintext-matrix mode: the matrix chunks encoded, not encrypted. */
+int hespmv_encode_matrix_plain_real(hespmv_ctx *ctx, const hespmv_cssc *m, const double *vals,
+                                    hespmv_ctbatch **out);
+/* CKKS encoding of n <= N/2 real slot values at 2^scale_bits: slot j is the
+ * evaluation at zeta^(5^j), zeta = exp(i pi / N), and
+ *   coef[k] = round(2^scale_bits * (2/N) * sum_j z_j cos(pi k 5^j / N)),
+ * k < N, rounded half away from zero (double-double arithmetic: the exact
+ * rounding).  Host only; HESPMV_E_RANGE beyond 2^62. */
+int hespmv_ckks_encode(hespmv_ctx *ctx, const double *z, size_t n, int32_t scale_bits,
+                       int64_t *coef);
+
 /* ------------------------------------------------------------ evaluation */
 
 /* The cloud lines of Algorithm 1 with Aggregation (Algorithm 4): for every
@@ -265,6 +301,15 @@ int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *
 
 /* Decrypt ciphertext `index` of a batch to its N slot values in [0, t):
  * row 0 slots 0..N/2-1 then row 1. Synchronous. */
+/* CKKS: decrypt (exact CRT of [c0 + c1 s]_Q, centred), decode the N/2 slots
+ * and divide by 2^scale_bits.  hespmv_decrypt_real un-permutes the rows of
+ * a SpMV result, whose scale is 2^(2 scale_bits + mask_scale_bits).
+ * Synchronous. */
+int hespmv_decrypt_real_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
+                              int32_t scale_bits, double *slots_out);
+int hespmv_decrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
+                        double *out_rows);
+
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out);
 

@@ -22,6 +22,10 @@ def _i64p(a):
     return a.ctypes.data_as(B.i64p)
 
 
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
 def _i32p(a):
     return a.ctypes.data_as(B.i32p)
 
@@ -60,7 +64,8 @@ class Context:
     """Scheme parameters, tables and keys on one GPU (hespmv_create)."""
 
     def __init__(self, log2n, L, K, dnum, t, rot_policy="pow2", slots=0, device=0,
-                 torch_alloc=True, prime_bits=0, allocator=None):
+                 torch_alloc=True, prime_bits=0, allocator=None, scheme="bgv", scale_bits=40,
+                 mask_scale_bits=30):
         self.lib = B.load()
         if allocator is not None:
             self.allocator = allocator
@@ -72,6 +77,8 @@ class Context:
         p.rot_policy = B.HESPMV_ROT_EXACT if rot_policy == "exact" else B.HESPMV_ROT_POW2
         p.slots = slots
         p.device = device
+        p.scheme = B.HESPMV_SCHEME_CKKS if scheme == "ckks" else B.HESPMV_SCHEME_BGV
+        p.scale_bits, p.mask_scale_bits = scale_bits, mask_scale_bits
         if self.allocator is not None:
             p.alloc = self.allocator.alloc_fn
             p.free = self.allocator.free_fn
@@ -88,6 +95,8 @@ class Context:
         self.N = 1 << log2n
         self.L, self.K, self.dnum, self.t = L, K, dnum, t
         self.device = device
+        self.scheme = scheme
+        self.scale_bits, self.mask_scale_bits = scale_bits, mask_scale_bits
 
     def close(self):
         if getattr(self, "h", None):
@@ -157,6 +166,36 @@ class Context:
             xp = _i64p(xa)
         self.check(self.lib.hespmv_encrypt(self.h, m.h, which, xp, c_uint64(seed), byref(out)))
         return CtBatch(self, out)
+
+    # ---- CKKS ----
+    def encrypt_real(self, m, which, values, seed=0):
+        out = c_void_p()
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self.check(self.lib.hespmv_encrypt_real(self.h, m.h, which, _f64p(v), c_uint64(seed),
+                                                byref(out)))
+        return CtBatch(self, out)
+
+    def encode_matrix_plain_real(self, m, vals):
+        out = c_void_p()
+        v = np.ascontiguousarray(vals, dtype=np.float64)
+        self.check(self.lib.hespmv_encode_matrix_plain_real(self.h, m.h, _f64p(v), byref(out)))
+        return CtBatch(self, out)
+
+    def ckks_encode(self, z, scale_bits):
+        zz = np.ascontiguousarray(z, dtype=np.float64)
+        out = np.zeros(self.N, dtype=np.int64)
+        self.check(self.lib.hespmv_ckks_encode(self.h, _f64p(zz), len(zz), scale_bits, _i64p(out)))
+        return out
+
+    def decrypt_real(self, m, y):
+        out = np.zeros(m.rows, dtype=np.float64)
+        self.check(self.lib.hespmv_decrypt_real(self.h, m.h, y.h, _f64p(out)))
+        return out
+
+    def decrypt_real_slots(self, b, index, scale_bits):
+        out = np.zeros(self.N // 2, dtype=np.float64)
+        self.check(self.lib.hespmv_decrypt_real_slots(self.h, b.h, index, scale_bits, _f64p(out)))
+        return out
 
     def spmv(self, m, A, X, y=None, stream=None):
         yh = c_void_p(y.h.value if y is not None else None)
@@ -373,10 +412,13 @@ class Cssc:
         self.lib = ctx.lib
         rp = np.ascontiguousarray(rowptr, dtype=np.int64)
         ci = np.ascontiguousarray(colidx, dtype=np.int32)
-        va = np.ascontiguousarray(vals, dtype=np.int64)
+        # real values (CKKS) are given to encrypt_real: the plan records positions only
+        real = vals is None or np.asarray(vals).dtype.kind == "f"
+        va = None if real else np.ascontiguousarray(vals, dtype=np.int64)
         h = c_void_p()
         ctx.check(self.lib.hespmv_encode_cssc(ctx.h, rows, cols, int(rp[-1]) if len(rp) else 0,
-                                              _i64p(rp), _i32p(ci), _i64p(va),
+                                              _i64p(rp), _i32p(ci),
+                                              _i64p(va) if va is not None else None,
                                               c_int64(max_abs_x), byref(h)))
         self._attach(h)
 

@@ -23,6 +23,8 @@ HESPMV_ROT_POW2 = 0
 HESPMV_ROT_EXACT = 1
 HESPMV_MATRIX = 0
 HESPMV_VECTOR = 1
+HESPMV_SCHEME_BGV = 0
+HESPMV_SCHEME_CKKS = 1
 HESPMV_SER_FULL = 0
 HESPMV_SER_SHAPE = 1
 HESPMV_KEY_SECRET = 0
@@ -41,7 +43,8 @@ class hespmv_params(ctypes.Structure):
     _fields_ = [("log2n", c_int32), ("L", c_int32), ("K", c_int32), ("dnum", c_int32),
                 ("t", c_uint64), ("prime_bits", c_int32), ("rot_policy", c_int32),
                 ("slots", c_int32), ("device", c_int32), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_user", c_void_p)]
+                ("free", FREE_FN), ("alloc_user", c_void_p), ("scheme", c_int32),
+                ("scale_bits", c_int32), ("mask_scale_bits", c_int32), ("reserved", c_int32)]
 
 
 class hespmv_tuning(ctypes.Structure):
@@ -53,6 +56,7 @@ u64p = POINTER(c_uint64)
 i64p = POINTER(c_int64)
 i32p = POINTER(c_int32)
 szp = POINTER(c_size_t)
+f64p = POINTER(ctypes.c_double)
 
 # name -> (restype, argtypes); mirrors include/hespmv.h
 SIGNATURES = {
@@ -81,6 +85,11 @@ SIGNATURES = {
     "hespmv_ctbatch_upload": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_download": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_serialize": (c_int, [c_void_p, c_void_p, c_size_t, szp]),
+    "hespmv_encrypt_real": (c_int, [c_void_p, c_void_p, c_int32, f64p, c_uint64, POINTER(c_void_p)]),
+    "hespmv_encode_matrix_plain_real": (c_int, [c_void_p, c_void_p, f64p, POINTER(c_void_p)]),
+    "hespmv_ckks_encode": (c_int, [c_void_p, f64p, c_size_t, c_int32, i64p]),
+    "hespmv_decrypt_real_slots": (c_int, [c_void_p, c_void_p, c_size_t, c_int32, f64p]),
+    "hespmv_decrypt_real": (c_int, [c_void_p, c_void_p, c_void_p, f64p]),
     "hespmv_set_tuning": (c_int, [c_void_p, POINTER(hespmv_tuning)]),
     "hespmv_get_tuning": (c_int, [c_void_p, POINTER(hespmv_tuning)]),
     "hespmv_autotune": (c_int, [c_void_p, c_size_t, POINTER(c_void_p), POINTER(c_void_p),

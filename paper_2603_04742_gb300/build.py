@@ -57,7 +57,10 @@ def build(verbose=False, force=False):
             cmd = [nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                                    "-Xptxas", "-v" if verbose else "-O3", "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", os.path.join(cuda, "include"),
+            # no contraction into FMA: host floating point gives the same bits on
+            # every CPU (the CKKS encoder's double-double arithmetic relies on it)
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
+                   "-I", os.path.join(cuda, "include"),
                    "-c", src, "-o", obj]
         jobs.append(cmd)
 

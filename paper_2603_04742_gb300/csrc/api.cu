@@ -203,6 +203,12 @@ int check_ctx(hespmv_ctx *ctx) { return ctx ? HESPMV_OK : HESPMV_E_INVALID; }
 // device buffers handed to the key switch are read with 16-byte vector loads
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
+// CKKS encoder tables of the context, made on first use
+CkksCodec *get_codec(hespmv_ctx *ctx) {
+    if (!ctx->codec) ctx->codec = ckks_codec(ctx->h.log2n);
+    return ctx->codec;
+}
+
 const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
     auto it = ctx->masks.find(r);
     if (it != ctx->masks.end()) return it->second;
@@ -214,14 +220,29 @@ const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
         dev_free(ctx, tmp);
         return nullptr;
     }
-    std::vector<int64_t> ones(N / 2, 0);
-    for (int j = 0; j < r && j < N / 2; ++j) ones[j] = 1;
-    int64_t *dvals = (int64_t *)tmp;
-    uint64_t *E = (uint64_t *)tmp + N;  // words [N, 2N) of tmp
-    bool ok = cudaMemcpyAsync(dvals, ones.data(), (N / 2) * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    ok = ok && op_scatter_slots(c, dvals, N / 2, E, 1, st) == cudaSuccess;
-    ok = ok && launch_ntt(c, E, c.L + c.K, 1, 1, N, true, st) == cudaSuccess;
-    ok = ok && op_lift(c, E, m, 1, st) == cudaSuccess;
+    bool ok;
+    if (ctx->h.scheme == HESPMV_SCHEME_CKKS) {
+        // r ones at the mask scale, encoded on the host, lifted over Q
+        std::vector<double> ones(N / 2, 0.0);
+        for (int j = 0; j < r && j < N / 2; ++j) ones[j] = 1.0;
+        std::vector<int64_t> coef(N);
+        CkksCodec *codec = get_codec(ctx);
+        ok = codec && ckks_encode(*codec, ones.data(), N / 2, ctx->h.mask_scale_bits, coef.data()).empty();
+        int64_t *dcoef = (int64_t *)tmp;
+        ok = ok && cudaMemcpyAsync(dcoef, coef.data(), N * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        ok = ok && op_signed_to_limbs(c, dcoef, m, 0, c.L, 1, st) == cudaSuccess;
+        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;  // coef is host memory
+    } else {
+        std::vector<int64_t> ones(N / 2, 0);
+        for (int j = 0; j < r && j < N / 2; ++j) ones[j] = 1;
+        int64_t *dvals = (int64_t *)tmp;
+        uint64_t *E = (uint64_t *)tmp + N;  // words [N, 2N) of tmp
+        ok = cudaMemcpyAsync(dvals, ones.data(), (N / 2) * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        ok = ok && op_scatter_slots(c, dvals, N / 2, E, 1, st) == cudaSuccess;
+        ok = ok && launch_ntt(c, E, c.L + c.K, 1, 1, N, true, st) == cudaSuccess;
+        ok = ok && op_lift(c, E, m, 1, st) == cudaSuccess;
+        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;  // `ones` is host memory
+    }
     ok = ok && launch_ntt(c, m, 0, c.L, 1, (int64_t)c.L * N, false, st) == cudaSuccess;
     // Montgomery form: mask products then need one reduction per sum
     ok = ok && op_to_mont_limbs(c, m, 0, c.L, 1, st) == cudaSuccess;
@@ -678,6 +699,8 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
 
 void hespmv_destroy(hespmv_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->codec) ckks_codec_free(ctx->codec);
+    if (ctx->crt) crt_real_free(ctx->crt);
     if (ctx->device < 0) {
         delete ctx;
         return;
@@ -863,7 +886,7 @@ int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
         delete m;
         FAIL(HESPMV_E_INVALID, "malformed CSR: " + err);
     }
-    if (max_abs_x > 0) {
+    if (max_abs_x > 0 && vals && ctx->h.scheme == HESPMV_SCHEME_BGV) {
         typedef unsigned __int128 u128;
         const u128 half_t = (u128)ctx->h.t;
         for (int32_t i = 0; i < rows; ++i) {
@@ -1056,6 +1079,9 @@ uint64_t ring_fingerprint(const hespmv_ctx *ctx) {
     mix((uint64_t)ctx->h.log2n);
     for (int l = 0; l < ctx->h.L; ++l) mix(ctx->h.q[l]);
     mix(ctx->h.t);
+    mix((uint64_t)ctx->h.scheme);
+    mix((uint64_t)ctx->h.scale_bits);
+    mix((uint64_t)ctx->h.mask_scale_bits);
     return h;
 }
 
@@ -1225,13 +1251,24 @@ int hespmv_ctbatch_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hes
     return HESPMV_OK;
 }
 
+// Encode and encrypt (or, plain, only encode) the chunks of one operand.
+// BGV: integer values (matrix values from the plan, or x); CKKS: real values
+// `real` (the matrix's CSR values, or x) encoded at 2^scale_bits.
 static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
-                        uint64_t seed, bool plain, hespmv_ctbatch **out) {
+                        const double *real, uint64_t seed, bool plain, hespmv_ctbatch **out) {
     if (!ctx || !m || !out) return HESPMV_E_INVALID;
+    const bool ckks = ctx->h.scheme == HESPMV_SCHEME_CKKS;
     if (!ctx->have_keys && !plain) FAIL(HESPMV_E_INVALID, "keygen first");
     if (which != HESPMV_MATRIX && which != HESPMV_VECTOR) FAIL(HESPMV_E_INVALID, "bad operand kind");
     if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no values or column indices");
-    if (which == HESPMV_VECTOR && !x && m->plan.cols > 0) FAIL(HESPMV_E_INVALID, "x is NULL");
+    if (ckks != (real != nullptr))
+        FAIL(HESPMV_E_INVALID, ckks ? "a CKKS context encrypts real values (hespmv_encrypt_real)"
+                                    : "a BGV context encrypts integers (hespmv_encrypt)");
+    if (!ckks && which == HESPMV_VECTOR && !x && m->plan.cols > 0) FAIL(HESPMV_E_INVALID, "x is NULL");
+    if (!ckks && which == HESPMV_MATRIX && !m->plan.has_values)
+        FAIL(HESPMV_E_INVALID, "the CSSC was built without values");
+    if (ckks && which == HESPMV_MATRIX && m->plan.nnz > 0 && !m->plan.has_src)
+        FAIL(HESPMV_E_INVALID, "the CSSC does not map slots to CSR positions (deserialized plan)");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
@@ -1252,7 +1289,9 @@ static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, co
     int64_t *dvals = (int64_t *)ws;
     uint64_t *E = ws + G * half, *mq = E + G * N, *u = mq + G * LN;
     int64_t *coef = (int64_t *)(u + 3 * G * LN);
-    std::vector<int64_t> host(G * half);
+    std::vector<int64_t> host(G * (ckks ? N : half));
+    std::vector<double> zs(ckks ? half : 0);
+    CkksCodec *codec = ckks ? get_codec(ctx) : nullptr;
     for (size_t k0 = 0; k0 < n; k0 += G) {
         const size_t gn = std::min(G, n - k0);
         // u, e0, e1 back to back at this group's size: one transform of 3*gn items
@@ -1261,6 +1300,19 @@ static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, co
         for (size_t k = 0; k < gn; ++k) {
             const Chunk &ch = pl.chunks[k0 + k];
             const int64_t cnt = (int64_t)ch.h * ch.c;
+            if (ckks) {  // slot values, then the chunk's N coefficients
+                for (int64_t s = 0; s < cnt; ++s) {
+                    const int64_t at = which == HESPMV_MATRIX ? pl.slot_src[ch.slot0 + s]
+                                                              : pl.slot_ci[ch.slot0 + s];
+                    zs[s] = at >= 0 ? real[at] : 0.0;
+                }
+                const std::string e = ckks_encode(*codec, zs.data(), cnt, ctx->h.scale_bits, &host[k * N]);
+                if (!e.empty()) {
+                    hespmv_ctbatch_free(b);
+                    FAIL(HESPMV_E_RANGE, "CKKS encoding: " + e);
+                }
+                continue;
+            }
             for (int64_t s = 0; s < cnt; ++s) {
                 if (which == HESPMV_MATRIX) {
                     host[k * half + s] = pl.slot_vals[ch.slot0 + s];
@@ -1271,10 +1323,16 @@ static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, co
             }
         }
         const uint64_t sbase = kEncBase + 4 * (uint64_t)k0;
-        bool ok = cudaMemcpy(dvals, host.data(), gn * half * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-        ok = ok && !op_scatter_slots(c, dvals, half, E, gn, 0);
-        ok = ok && !launch_ntt(c, E, c.L + c.K, 1, (int)gn, N, true, 0);
-        ok = ok && !op_lift(c, E, mq, gn, 0);
+        bool ok;
+        if (ckks) {  // coefficients (in E's words) -> residues over Q
+            ok = cudaMemcpy(E, host.data(), gn * N * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+            ok = ok && !op_signed_to_limbs(c, (const int64_t *)E, mq, 0, (int)L, gn, 0);
+        } else {
+            ok = cudaMemcpy(dvals, host.data(), gn * half * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+            ok = ok && !op_scatter_slots(c, dvals, half, E, gn, 0);
+            ok = ok && !launch_ntt(c, E, c.L + c.K, 1, (int)gn, N, true, 0);
+            ok = ok && !op_lift(c, E, mq, gn, 0);
+        }
         ok = ok && !launch_ntt(c, mq, 0, (int)L, (int)gn, LN, false, 0);
         if (plain) {  // trivial ciphertexts (m, 0): the plaintext itself
             uint64_t *dst = b->data + k0 * 2 * LN;
@@ -1309,11 +1367,26 @@ static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, co
 
 int hespmv_encrypt(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
                    uint64_t seed, hespmv_ctbatch **out) {
-    return encrypt_impl(ctx, m, which, x, seed, false, out);
+    return encrypt_impl(ctx, m, which, x, nullptr, seed, false, out);
 }
 
 int hespmv_encode_matrix_plain(hespmv_ctx *ctx, const hespmv_cssc *m, hespmv_ctbatch **out) {
-    return encrypt_impl(ctx, m, HESPMV_MATRIX, nullptr, 0, true, out);
+    return encrypt_impl(ctx, m, HESPMV_MATRIX, nullptr, nullptr, 0, true, out);
+}
+
+int hespmv_encrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const double *values,
+                        uint64_t seed, hespmv_ctbatch **out) {
+    if (ctx && m && !values && (which == HESPMV_VECTOR ? m->plan.cols : m->plan.nnz) > 0)
+        FAIL(HESPMV_E_INVALID, "values is NULL");
+    static const double none = 0.0;
+    return encrypt_impl(ctx, m, which, nullptr, values ? values : &none, seed, false, out);
+}
+
+int hespmv_encode_matrix_plain_real(hespmv_ctx *ctx, const hespmv_cssc *m, const double *vals,
+                                    hespmv_ctbatch **out) {
+    if (ctx && m && !vals && m->plan.nnz > 0) FAIL(HESPMV_E_INVALID, "vals is NULL");
+    static const double none = 0.0;
+    return encrypt_impl(ctx, m, HESPMV_MATRIX, nullptr, vals ? vals : &none, 0, true, out);
 }
 
 int hespmv_spmv(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *A,
@@ -1408,6 +1481,7 @@ int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_ho
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out) {
     if (!ctx || !b || !slots_out || index >= b->n) return HESPMV_E_INVALID;
+    if (ctx->h.scheme != HESPMV_SCHEME_BGV) FAIL(HESPMV_E_INVALID, "CKKS: hespmv_decrypt_real_slots");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
@@ -1425,9 +1499,58 @@ int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
     return HESPMV_OK;
 }
 
+int hespmv_decrypt_real_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
+                              int32_t scale_bits, double *slots_out) {
+    if (!ctx || !b || !slots_out || index >= b->n || scale_bits < 0 || scale_bits > 1000)
+        return HESPMV_E_INVALID;
+    if (ctx->h.scheme != HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "not a CKKS context");
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int64_t N = c.N, LN = (int64_t)c.L * N;
+    uint64_t *x = workspace(ctx, LN * 8);
+    if (!x) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    CK(op_dec_phase(c, b->data + index * 2 * LN, ctx->sk, x, 0));
+    CK(launch_ntt(c, x, 0, c.L, 1, LN, true, 0));
+    std::vector<uint64_t> res(LN);
+    CK(cudaMemcpy(res.data(), x, LN * 8, cudaMemcpyDeviceToHost));
+    if (!ctx->crt) ctx->crt = crt_real(ctx->h.q.data(), c.L);
+    std::vector<double> coef(N);
+    crt_to_double(*ctx->crt, res.data(), (int)N, coef.data());
+    ckks_decode(*get_codec(ctx), coef.data(), N / 2, std::ldexp(1.0, -scale_bits), slots_out);
+    return HESPMV_OK;
+}
+
+int hespmv_decrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
+                        double *out_rows) {
+    if (!ctx || !m || !y || (!out_rows && m->plan.rows)) return HESPMV_E_INVALID;
+    if (y->n < m->plan.parts.size()) FAIL(HESPMV_E_INVALID, "result batch too small");
+    if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no row map");
+    const int total = 2 * ctx->h.scale_bits + ctx->h.mask_scale_bits;
+    std::vector<double> slots(ctx->h.N / 2);
+    for (size_t p = 0; p < m->plan.parts.size(); ++p) {
+        int rc = hespmv_decrypt_real_slots(ctx, y, p, total, slots.data());
+        if (rc) return rc;
+        const Partition &P = m->plan.parts[p];
+        for (int32_t idx = 0; idx < P.rows; ++idx) out_rows[P.row0 + P.rm[idx]] = slots[idx];
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_ckks_encode(hespmv_ctx *ctx, const double *z, size_t n, int32_t scale_bits, int64_t *coef) {
+    if (!ctx || (!z && n) || !coef || ctx->h.q.empty()) return HESPMV_E_INVALID;
+    if (n > (size_t)ctx->h.N / 2) FAIL(HESPMV_E_INVALID, "more values than N/2 slots");
+    if (scale_bits < 0 || scale_bits > 62) FAIL(HESPMV_E_INVALID, "scale_bits must be in [0, 62]");
+    const std::string e = ckks_encode(*get_codec(ctx), z, n, scale_bits, coef);
+    if (!e.empty()) FAIL(HESPMV_E_RANGE, e);
+    return HESPMV_OK;
+}
+
 int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
                    int64_t *out_rows) {
     if (!ctx || !m || !y || (!out_rows && m->plan.rows)) return HESPMV_E_INVALID;
+    if (ctx->h.scheme != HESPMV_SCHEME_BGV) FAIL(HESPMV_E_INVALID, "CKKS results: hespmv_decrypt_real");
     if (y->n < m->plan.parts.size()) FAIL(HESPMV_E_INVALID, "result batch too small");
     if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no row map");
     const uint64_t t = ctx->h.t;

@@ -28,6 +28,7 @@ static void to_cssc(int32_t r0, int32_t r1, const int64_t *rowptr, const int32_t
     // number of sorted rows longer than j = height of aligned column j
     const int64_t nnz = rowptr[r1] - rowptr[r0];
     P.va.resize(nnz);
+    P.src.resize(nnz);
     P.ci.resize(nnz);
     P.cp.assign(lmax + 1, 0);
     std::vector<int64_t> height(lmax, 0);
@@ -39,7 +40,8 @@ static void to_cssc(int32_t r0, int32_t r1, const int64_t *rowptr, const int32_t
         const int32_t i = P.rm[p];
         const int64_t base = rowptr[r0 + i];
         for (int64_t j = 0; j < len[i]; ++j) {
-            P.va[P.cp[j] + p] = vals[base + j];
+            P.va[P.cp[j] + p] = vals ? vals[base + j] : 0;
+            P.src[P.cp[j] + p] = base + j;
             P.ci[P.cp[j] + p] = colidx[base + j];
         }
     }
@@ -62,12 +64,14 @@ static void chunk_partition(Partition &P, int32_t part_index, int32_t s, Plan &p
         ch.slot0 = (int64_t)plan.slot_vals.size();
         plan.slot_vals.resize(ch.slot0 + h * ch.c, 0);
         plan.slot_ci.resize(ch.slot0 + h * ch.c, -1);
+        plan.slot_src.resize(ch.slot0 + h * ch.c, -1);
         for (int32_t qc = 0; qc < ch.c; ++qc) {
             const int64_t col = start + qc;
             const int64_t n = P.cp[col + 1] - P.cp[col];
             for (int64_t p = 0; p < n; ++p) {
                 plan.slot_vals[ch.slot0 + qc * h + p] = P.va[P.cp[col] + p];
                 plan.slot_ci[ch.slot0 + qc * h + p] = P.ci[P.cp[col] + p];
+                if (!P.src.empty()) plan.slot_src[ch.slot0 + qc * h + p] = P.src[P.cp[col] + p];
             }
         }
         plan.chunks.push_back(ch);
@@ -79,6 +83,7 @@ void chunk_plan(Plan &plan) {
     plan.chunks.clear();
     plan.slot_vals.clear();
     plan.slot_ci.clear();
+    plan.slot_src.clear();
     for (size_t k = 0; k < plan.parts.size(); ++k) chunk_partition(plan.parts[k], (int32_t)k, plan.s, plan);
 }
 
@@ -86,7 +91,7 @@ std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *r
                        const int32_t *colidx, const int64_t *vals, int32_t s, Plan &plan) {
     if (rows < 0 || cols < 0 || nnz < 0 || s < 1) return "negative size";
     if (rows > 0 && !rowptr) return "rowptr is NULL";
-    if (nnz > 0 && (!colidx || !vals)) return "colidx/vals is NULL";
+    if (nnz > 0 && !colidx) return "colidx is NULL";
     if (rows > 0 && (rowptr[0] != 0 || rowptr[rows] != nnz)) return "rowptr[0] != 0 or rowptr[rows] != nnz";
     for (int32_t i = 0; i < rows; ++i) {
         if (rowptr[i + 1] < rowptr[i]) return "rowptr not non-decreasing";
@@ -97,6 +102,8 @@ std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *r
         }
     }
     plan = Plan();
+    plan.has_values = vals != nullptr || nnz == 0;
+    plan.has_src = true;
     plan.rows = rows;
     plan.cols = cols;
     plan.nnz = nnz;

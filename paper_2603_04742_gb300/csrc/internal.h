@@ -17,7 +17,8 @@ constexpr int kMaxPrimes = 21;  // L + K + 1 (t) <= 16 + 4 + 1
 // Host-side parameter tables (built once per context, then uploaded).
 struct HostTables {
     int log2n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, slots = 0;
-    uint64_t t = 0;
+    int scheme = 0, scale_bits = 0, mask_scale_bits = 0;  // CKKS: scales 2^bits
+    uint64_t t = 0;  // plaintext modulus (BGV); 1 for CKKS (its formulas' t)
     std::vector<uint64_t> q;     // L + K + 1 moduli: Q, then P, then t
     std::vector<uint64_t> psi;   // primitive 2N-th roots (index L+K: zeta for t)
     std::vector<ModConst> mc;    // per modulus
@@ -88,6 +89,7 @@ struct Chunk {
 struct Partition {
     int32_t row0 = 0, rows = 0;
     std::vector<int64_t> va;   // CSSC value array
+    std::vector<int64_t> src;  // CSR position of each CSSC entry (real values)
     std::vector<int32_t> ci;   // CSSC column indices
     std::vector<int64_t> cp;   // Lmax + 1
     std::vector<int32_t> rm;   // local row of sorted row p
@@ -101,6 +103,9 @@ struct Plan {
     std::vector<Chunk> chunks;
     std::vector<int64_t> slot_vals;   // concatenated chunk slot values
     std::vector<int32_t> slot_ci;     // concatenated chunk slot column indices
+    std::vector<int64_t> slot_src;    // CSR position of each slot value, -1 = padding
+    bool has_values = true;           // integer values given (else positions only)
+    bool has_src = false;             // slot_src filled (plans built from a CSR)
 };
 
 // Returns empty string on success.
@@ -108,6 +113,21 @@ std::string build_plan(int32_t rows, int32_t cols, int64_t nnz, const int64_t *r
                        const int32_t *colidx, const int64_t *vals, int32_t s, Plan &plan);
 // Chunks (Algorithm 2) of every partition whose CP, VA and CI are set.
 void chunk_plan(Plan &plan);
+
+// CKKS encoding of real slot values (host, double-double; ckks_host.cpp)
+struct CkksCodec;
+CkksCodec *ckks_codec(int log2n);
+void ckks_codec_free(CkksCodec *c);
+// n <= N/2 values -> N integer coefficients at scale 2^scale_bits; "" or an error
+std::string ckks_encode(const CkksCodec &C, const double *z, size_t n, int scale_bits,
+                        int64_t *coef);
+// N real coefficients -> the first n slot values times inv_scale
+void ckks_decode(const CkksCodec &C, const double *coef, size_t n, double inv_scale, double *z);
+// centred [x]_Q of residues x [L][N] as doubles (exact CRT, then rounding)
+struct CrtReal;
+CrtReal *crt_real(const uint64_t *q, int L);
+void crt_real_free(CrtReal *c);
+void crt_to_double(const CrtReal &c, const uint64_t *x, int N, double *out);
 // totalSum rotation amounts of a chunk (r rows, c columns) in order; flags
 // tell whether the step rotates the running sum (doubling) or the original.
 void total_sum_steps(int32_t r, int32_t c, std::vector<int32_t> &steps,
@@ -199,6 +219,9 @@ struct hespmv_ctx {
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;
+    // CKKS encoder tables and CRT constants (host, made on first use)
+    hespmv::CkksCodec *codec = nullptr;
+    hespmv::CrtReal *crt = nullptr;
 };
 
 struct hespmv_cssc {

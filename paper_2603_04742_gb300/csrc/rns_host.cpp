@@ -95,20 +95,36 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
     h.slots = p.slots ? p.slots : h.N / 2;
     if (h.slots < 1 || h.slots > h.N / 2) { err = "slots must be in [1, N/2]"; return false; }
     const uint64_t N = (uint64_t)h.N, twoN = 2 * N;
-    h.t = p.t;
-    if (p.t < 3 || p.t >= (1ull << 50) || p.t % twoN != 1 || !prime64(p.t)) {
+    const bool ckks = p.scheme == HESPMV_SCHEME_CKKS;
+    if (p.scheme != HESPMV_SCHEME_BGV && !ckks) { err = "unknown scheme"; return false; }
+    h.scheme = p.scheme;
+    if (ckks) {
+        if (p.t != 0) { err = "CKKS takes no plaintext modulus (t = 0)"; return false; }
+        if (p.scale_bits < 10 || p.scale_bits > 60 || p.mask_scale_bits < 1 || p.mask_scale_bits > 60) {
+            err = "CKKS scales: scale_bits in [10, 60], mask_scale_bits in [1, 60]";
+            return false;
+        }
+        if (p.K < h.alpha) { err = "CKKS needs K >= alpha (P must cover a key-switching digit)"; return false; }
+        h.scale_bits = p.scale_bits;
+        h.mask_scale_bits = p.mask_scale_bits;
+    } else if (p.t < 3 || p.t >= (1ull << 50) || p.t % twoN != 1 || !prime64(p.t)) {
         err = "t must be a prime below 2^50 with t = 1 mod 2N";
         return false;
     }
+    // the t of every key, encryption and key-switching formula
+    const uint64_t tk = ckks ? 1 : p.t;
+    h.t = tk;
     // ciphertext primes: descending from the largest q < 2^bits, q = 1 mod 2N
     h.q.clear();
     uint64_t cand = (((1ull << bits) - 2) / twoN) * twoN + 1;
-    while ((int)h.q.size() < p.L + p.K) {
+    while ((int)h.q.size() < p.L + p.K + (ckks ? 1 : 0)) {
         if (cand < twoN) { err = "not enough NTT primes"; return false; }
         if (prime64(cand) && cand != p.t) h.q.push_back(cand);
         cand -= twoN;
     }
-    h.q.push_back(p.t);
+    // last table entry: t (BGV plaintext NTT); CKKS has no plaintext modulus
+    // and keeps the next NTT prime there, unused
+    if (!ckks) h.q.push_back(p.t);
     const int M = p.L + p.K + 1;
     h.psi.resize(M);
     h.mc.resize(M);
@@ -184,7 +200,7 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         uint64_t phat = 1;
         for (int o = 0; o < K; ++o)
             if (o != k) phat = mulm(phat, h.q[L + o] % pk, pk);
-        const uint64_t v = mulm(invm(p.t % pk, pk), invm(phat, pk), pk);
+        const uint64_t v = mulm(invm(tk % pk, pk), invm(phat, pk), pk);
         h.md_pk[k * 2] = v;
         h.md_pk[k * 2 + 1] = shoup(v, pk);
         for (int i = 0; i < L; ++i) {
@@ -206,12 +222,14 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         const uint64_t pinv = invm(P, qi);
         h.md_pinv[i * 2] = pinv;
         h.md_pinv[i * 2 + 1] = shoup(pinv, qi);
-        h.md_t[i * 2] = p.t % qi;
-        h.md_t[i * 2 + 1] = shoup(p.t % qi, qi);
+        h.md_t[i * 2] = tk % qi;
+        h.md_t[i * 2 + 1] = shoup(tk % qi, qi);
     }
     // decryption CRT constants
     h.dec.assign((size_t)L * 4 + 2, 0);
     h.dec_inv_q.assign(L, 0.0);
+    // (Qhat_i^-1 mod q_i; BGV also Qhat_i mod t and Q mod t)
+    const uint64_t tt = ckks ? h.q[LK] : p.t;  // CKKS: harmless stand-in, unused
     uint64_t Qt = 1;
     for (int i = 0; i < L; ++i) {
         const uint64_t qi = h.q[i];
@@ -219,20 +237,20 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         for (int o = 0; o < L; ++o)
             if (o != i) {
                 prod = mulm(prod, h.q[o] % qi, qi);
-                prod_t = mulm(prod_t, h.q[o] % p.t, p.t);
+                prod_t = mulm(prod_t, h.q[o] % tt, tt);
             }
         const uint64_t inv = invm(prod, qi);
         h.dec[i * 4 + 0] = inv;
         h.dec[i * 4 + 1] = shoup(inv, qi);
         h.dec[i * 4 + 2] = prod_t;
-        h.dec[i * 4 + 3] = shoup(prod_t, p.t);
+        h.dec[i * 4 + 3] = shoup(prod_t, tt);
         h.dec_inv_q[i] = 1.0 / (double)qi;
-        Qt = mulm(Qt, qi % p.t, p.t);
+        Qt = mulm(Qt, qi % tt, tt);
     }
     h.dec[(size_t)L * 4] = Qt;
-    h.dec[(size_t)L * 4 + 1] = shoup(Qt, p.t);
+    h.dec[(size_t)L * 4 + 1] = shoup(Qt, tt);
     h.t_mod.resize(LK);
-    for (int l = 0; l < LK; ++l) h.t_mod[l] = p.t % h.q[l];
+    for (int l = 0; l < LK; ++l) h.t_mod[l] = tk % h.q[l];
     // fused key-switching constants
     h.ks_zc.assign((size_t)L * 4, 0);
     for (int i = 0; i < L; ++i) {
@@ -255,7 +273,7 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         h.ks_yc[k * 4 + 3] = shoup(c1, pk);
         for (int i = 0; i < L; ++i) {
             const uint64_t qi = h.q[i];
-            const uint64_t w = mulm(h.md_phat[((size_t)k * L + i) * 2], p.t % qi, qi);
+            const uint64_t w = mulm(h.md_phat[((size_t)k * L + i) * 2], tk % qi, qi);
             h.md_phat_t[((size_t)k * L + i) * 2] = w;
             h.md_phat_t[((size_t)k * L + i) * 2 + 1] = shoup(w, qi);
         }
