@@ -118,7 +118,7 @@ class Oracle:
     # -------------------------------------------------------------- keygen
     def keygen(self, seed, galois_elements=()):
         p = self.p
-        N, L, K, t = p.N, p.L, p.K, p.t
+        N, L, K, t = p.N, p.L, p.K, p.t_ks
         all_limbs = range(L + K)
         s = rng.ternary(seed, rng.S_SECRET, N)
         self.s_coef = s
@@ -151,7 +151,7 @@ class Oracle:
     def make_ksk(self, seed, kid, sp):
         """Key switching key from s' (NTT over Q u P) to s: [dnum][2][L+K][N]."""
         p = self.p
-        N, L, K, t = p.N, p.L, p.K, p.t
+        N, L, K, t = p.N, p.L, p.K, p.t_ks
         key = np.empty((p.dnum, 2, L + K, N), dtype=np.uint64)
         for j in range(p.dnum):
             a = rng.uniform_limbs(seed, rng.ksk_a_stream(kid, j), p.q, N)
@@ -167,7 +167,7 @@ class Oracle:
     # ------------------------------------------------- encryption/decryption
     def encrypt(self, m_coef, seed, ct_index):
         p = self.p
-        N, L, t = p.N, p.L, p.t
+        N, L, t = p.N, p.L, p.t_ks
         u = self.ntt_signed(rng.ternary(seed, rng.enc_stream(ct_index, 1), N), range(L))
         e0 = self.ntt_signed(rng.cbd21(seed, rng.enc_stream(ct_index, 2), N), range(L))
         e1 = self.ntt_signed(rng.cbd21(seed, rng.enc_stream(ct_index, 3), N), range(L))
@@ -257,7 +257,7 @@ class Oracle:
         """Hybrid key switch of d (NTT over Q) with `key` -> (ks0, ks1) over Q."""
         self._count("keyswitch")
         p = self.p
-        N, L, K, t = p.N, p.L, p.K, p.t
+        N, L, K, t = p.N, p.L, p.K, p.t_ks
         q = p.q
         d_coef = np.array([self.intt(d[i], i) for i in range(L)])
         acc = np.zeros((2, L + K, N), dtype=np.uint64)

@@ -126,13 +126,15 @@ class Params:
             self.t = 1
             self.zeta = 1
         else:
-            assert self.scheme == "bgv"
+            assert self.scheme in ("bgv", "bfv")
             assert (self.t - 1) % (2 * N) == 0 and is_prime(self.t)
         self.alpha = -(-self.L // self.dnum)
         assert -(-self.L // self.alpha) == self.dnum, "every digit must be non-empty"
         # CKKS adds the key-switching noise (about N * Q_j / P) to the message
         # itself, so P must cover a digit: K >= alpha primes of equal size
         assert self.scheme != "ckks" or self.K >= self.alpha, "CKKS needs K >= alpha"
+        # BFV holds the message at Q/t: the same holds for its key switches
+        assert self.scheme != "bfv" or self.K >= self.alpha, "BFV needs K >= alpha"
         if not self.q:
             self.q = ntt_primes(N, self.bits, self.L + self.K)
         if not self.psi:
@@ -143,6 +145,12 @@ class Params:
     @property
     def N(self) -> int:
         return 1 << self.log2n
+
+    @property
+    def t_ks(self) -> int:
+        """The t of the key, encryption and key-switching formulas: t for
+        BGV (errors t*e, ModDown with the t-correction), 1 for BFV and CKKS."""
+        return self.t if self.scheme == "bgv" else 1
 
     @property
     def Q(self) -> int:
