@@ -90,8 +90,9 @@ typedef struct hespmv_params {
     hespmv_alloc_fn alloc; /* optional device allocator (NULL: cudaMalloc)     */
     hespmv_free_fn free;   /* its matching free                                 */
     void *alloc_user;      /* passed back to alloc/free                         */
-    int32_t scheme;        /* HESPMV_SCHEME_BGV (0, integers mod t) or
-                              HESPMV_SCHEME_CKKS (real values; t must be 0)     */
+    int32_t scheme;        /* HESPMV_SCHEME_BGV (0, integers mod t),
+                              HESPMV_SCHEME_CKKS (real values; t must be 0) or
+                              HESPMV_SCHEME_BFV (integers mod t)                */
     int32_t scale_bits;    /* CKKS: matrix and vector scale 2^scale_bits, 10..60 */
     int32_t mask_scale_bits; /* CKKS: scale of the 0/1 masks, 1..60            */
     int32_t reserved;
@@ -105,6 +106,11 @@ typedef struct hespmv_params {
  * that P covers a key-switching digit. */
 #define HESPMV_SCHEME_BGV 0
 #define HESPMV_SCHEME_CKKS 1
+/* BFV (the paper's scheme, Section 5): the BGV slots and keys with t = 1 in
+ * their formulas, the message at Delta = floor(Q/t), and HE-Mult as defined:
+ * d' = [round(t d / Q)]_Q for the integer tensor d of the centred inputs,
+ * computed exactly in an auxiliary basis B > 2 t N Q.  Needs K >= alpha. */
+#define HESPMV_SCHEME_BFV 2
 
 typedef struct hespmv_ctx hespmv_ctx;         /* scheme, tables, keys, workspace */
 typedef struct hespmv_cssc hespmv_cssc;       /* CSSC + partitions + chunk plan */

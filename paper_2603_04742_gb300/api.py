@@ -77,7 +77,8 @@ class Context:
         p.rot_policy = B.HESPMV_ROT_EXACT if rot_policy == "exact" else B.HESPMV_ROT_POW2
         p.slots = slots
         p.device = device
-        p.scheme = B.HESPMV_SCHEME_CKKS if scheme == "ckks" else B.HESPMV_SCHEME_BGV
+        p.scheme = {"bgv": B.HESPMV_SCHEME_BGV, "ckks": B.HESPMV_SCHEME_CKKS,
+                    "bfv": B.HESPMV_SCHEME_BFV}[scheme]
         p.scale_bits, p.mask_scale_bits = scale_bits, mask_scale_bits
         if self.allocator is not None:
             p.alloc = self.allocator.alloc_fn

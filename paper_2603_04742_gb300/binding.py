@@ -25,6 +25,7 @@ HESPMV_MATRIX = 0
 HESPMV_VECTOR = 1
 HESPMV_SCHEME_BGV = 0
 HESPMV_SCHEME_CKKS = 1
+HESPMV_SCHEME_BFV = 2
 HESPMV_SER_FULL = 0
 HESPMV_SER_SHAPE = 1
 HESPMV_KEY_SECRET = 0

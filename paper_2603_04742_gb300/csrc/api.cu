@@ -209,6 +209,17 @@ CkksCodec *get_codec(hespmv_ctx *ctx) {
     return ctx->codec;
 }
 
+// HE-Mult tensor of n ciphertext pairs -> d [n][3][L][N]: BGV's limb-wise
+// products, or BFV's exact scale and round (scratch: tensor_scratch_words)
+size_t tensor_scratch_words(const Ctx &c, size_t n) {
+    return c.c->h.scheme == HESPMV_SCHEME_BFV ? bfv_tensor_words(c, n) : 0;
+}
+cudaError_t tensor_n(const Ctx &c, const uint64_t *a, const uint64_t *b, uint64_t *d, size_t n,
+                     uint64_t *scratch, cudaStream_t st) {
+    if (c.c->h.scheme == HESPMV_SCHEME_BFV) return bfv_tensor(c, a, b, d, n, scratch, st);
+    return op_tensor(c, a, b, d, n, st);
+}
+
 const uint64_t *mask_plaintext(hespmv_ctx *ctx, int32_t r, cudaStream_t st) {
     auto it = ctx->masks.find(r);
     if (it != ctx->masks.end()) return it->second;
@@ -469,7 +480,7 @@ void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &
     pp.G = std::max<size_t>(1, std::min<size_t>(total_chunks, tune_G ? tune_G : 32));
     pp.GR = std::max<size_t>(1, std::min<size_t>(rot_chunks, tune_GR ? tune_GR : c.N >= (1 << 15) ? 32 : 64));
     const size_t prod_w = total_chunks * CT;
-    const size_t mult_w = pp.G * 3 * LN + ks_words(c, pp.G);
+    const size_t mult_w = pp.G * 3 * LN + std::max(ks_words(c, pp.G), tensor_scratch_words(c, pp.G));
     const size_t rot_w = rot_chunks ? 4 * pp.GR * CT + ks_words(c, pp.GR) : 0;
     pp.need_bytes = (prod_w + std::max(mult_w, rot_w)) * 8;
 }
@@ -522,7 +533,8 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         for (size_t g0 = 0; g0 < all.size(); g0 += G) {
             const size_t gn = std::min(G, all.size() - g0);
             const size_t i = all[g0].first, k = all[g0].second;
-            if (ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
+            const bool bgv = ctx->h.scheme != HESPMV_SCHEME_BFV;  // BGV and CKKS tensors are limb-wise
+            if (bgv && ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
                 // one matrix's consecutive chunks: tensor product fused into the key switch
                 CK(relin_tensor_fused(c, A[i] + k * CT, X[i] + k * CT, ctx->rlk, prod + g0 * CT, gn,
                                       scr, st));
@@ -533,7 +545,7 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                 const size_t ii = all[g0 + s].first, kk = all[g0 + s].second;
                 size_t run = 1;
                 while (s + run < gn && all[g0 + s + run].first == ii) ++run;
-                CK(op_tensor(c, A[ii] + kk * CT, X[ii] + kk * CT, dbuf + s * 3 * LN, run, st));
+                CK(tensor_n(c, A[ii] + kk * CT, X[ii] + kk * CT, dbuf + s * 3 * LN, run, scr, st));
                 s += run;
             }
             CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + g0 * CT, dbuf, 3 * LN, LN, 3,
@@ -688,6 +700,8 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
               upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod) &&
               upload(ctx, d.ks_zc, h.ks_zc) && upload(ctx, d.ks_yc, h.ks_yc) &&
               upload(ctx, d.md_phat_t, h.md_phat_t);
+    if (ok && h.scheme == HESPMV_SCHEME_BFV)
+        ok = upload(ctx, d.bfv_delta, h.bfv_delta) && upload(ctx, d.bfv_const, h.bfv_const);
     if (!ok) {
         ctx->err = "table upload failed";
         *out = ctx;
@@ -886,7 +900,7 @@ int hespmv_encode_cssc(hespmv_ctx *ctx, int32_t rows, int32_t cols, int64_t nnz,
         delete m;
         FAIL(HESPMV_E_INVALID, "malformed CSR: " + err);
     }
-    if (max_abs_x > 0 && vals && ctx->h.scheme == HESPMV_SCHEME_BGV) {
+    if (max_abs_x > 0 && vals && ctx->h.scheme != HESPMV_SCHEME_CKKS) {
         typedef unsigned __int128 u128;
         const u128 half_t = (u128)ctx->h.t;
         for (int32_t i = 0; i < rows; ++i) {
@@ -1331,7 +1345,12 @@ static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, co
             ok = cudaMemcpy(dvals, host.data(), gn * half * 8, cudaMemcpyHostToDevice) == cudaSuccess;
             ok = ok && !op_scatter_slots(c, dvals, half, E, gn, 0);
             ok = ok && !launch_ntt(c, E, c.L + c.K, 1, (int)gn, N, true, 0);
-            ok = ok && !op_lift(c, E, mq, gn, 0);
+            // BFV puts the message at Delta = floor(Q/t); plaintexts that only
+            // multiply (the plain matrix) keep the centred lift
+            if (ctx->h.scheme == HESPMV_SCHEME_BFV && !plain)
+                ok = ok && !op_bfv_delta(c, E, mq, gn, 0);
+            else
+                ok = ok && !op_lift(c, E, mq, gn, 0);
         }
         ok = ok && !launch_ntt(c, mq, 0, (int)L, (int)gn, LN, false, 0);
         if (plain) {  // trivial ciphertexts (m, 0): the plaintext itself
@@ -1481,7 +1500,7 @@ int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_ho
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out) {
     if (!ctx || !b || !slots_out || index >= b->n) return HESPMV_E_INVALID;
-    if (ctx->h.scheme != HESPMV_SCHEME_BGV) FAIL(HESPMV_E_INVALID, "CKKS: hespmv_decrypt_real_slots");
+    if (ctx->h.scheme == HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "CKKS: hespmv_decrypt_real_slots");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
@@ -1492,7 +1511,15 @@ int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
     uint64_t *x = ws, *msg = x + LN, *slots = msg + N;
     CK(op_dec_phase(c, b->data + index * 2 * LN, ctx->sk, x, 0));
     CK(launch_ntt(c, x, 0, c.L, 1, LN, true, 0));
-    CK(op_crt_to_t(c, x, msg, 0));
+    if (ctx->h.scheme == HESPMV_SCHEME_BFV) {
+        // m = round(t [x]_Q / Q) mod t, exactly, on the host (client side)
+        std::vector<uint64_t> res(LN), m(N);
+        CK(cudaMemcpy(res.data(), x, LN * 8, cudaMemcpyDeviceToHost));
+        bfv_decrypt_coef(ctx->h, res.data(), m.data());
+        CK(cudaMemcpy(msg, m.data(), N * 8, cudaMemcpyHostToDevice));
+    } else {
+        CK(op_crt_to_t(c, x, msg, 0));
+    }
     CK(launch_ntt(c, msg, c.L + c.K, 1, 1, N, false, 0));
     CK(op_gather_slots(c, msg, slots, 0));
     CK(cudaMemcpy(slots_out, slots, N * 8, cudaMemcpyDeviceToHost));
@@ -1550,7 +1577,7 @@ int hespmv_ckks_encode(hespmv_ctx *ctx, const double *z, size_t n, int32_t scale
 int hespmv_decrypt(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
                    int64_t *out_rows) {
     if (!ctx || !m || !y || (!out_rows && m->plan.rows)) return HESPMV_E_INVALID;
-    if (ctx->h.scheme != HESPMV_SCHEME_BGV) FAIL(HESPMV_E_INVALID, "CKKS results: hespmv_decrypt_real");
+    if (ctx->h.scheme == HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "CKKS results: hespmv_decrypt_real");
     if (y->n < m->plan.parts.size()) FAIL(HESPMV_E_INVALID, "result batch too small");
     if (m->shape_only) FAIL(HESPMV_E_INVALID, "a shape-only CSSC has no row map");
     const uint64_t t = ctx->h.t;
@@ -1605,7 +1632,13 @@ int hespmv_he_tensor(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint
     if (!ctx || !a || !b || !d) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
-    CK(op_tensor(view(ctx), a, b, d, n, (cudaStream_t)stream));
+    const Ctx c = view(ctx);
+    uint64_t *scr = nullptr;
+    if (const size_t w = tensor_scratch_words(c, n)) {
+        scr = workspace(ctx, w * 8);
+        if (!scr) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    }
+    CK(tensor_n(c, a, b, d, n, scr, (cudaStream_t)stream));
     return HESPMV_OK;
 }
 
@@ -1633,10 +1666,10 @@ int hespmv_he_mult(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N;
-    uint64_t *ws = workspace(ctx, (n * 3 * LN + ks_words(c, n)) * 8);
+    uint64_t *ws = workspace(ctx, (n * 3 * LN + std::max(ks_words(c, n), tensor_scratch_words(c, n))) * 8);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     cudaStream_t st = (cudaStream_t)stream;
-    CK(op_tensor(c, a, b, ws, n, st));
+    CK(tensor_n(c, a, b, ws, n, ws + n * 3 * LN, st));
     CK(keyswitch_n(c, ws + 2 * LN, 3 * LN, ctx->rlk, out, ws, 3 * LN, LN, 3, n, ws + n * 3 * LN, st));
     return HESPMV_OK;
 }

@@ -18,6 +18,12 @@ constexpr int kMaxPrimes = 21;  // L + K + 1 (t) <= 16 + 4 + 1
 struct HostTables {
     int log2n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, slots = 0;
     int scheme = 0, scale_bits = 0, mask_scale_bits = 0;  // CKKS: scales 2^bits
+    // BFV: auxiliary basis B = table entries [iB, iB + nB); multi-word
+    // constants of exact Chinese remaindering over Q (wq words) and B (wb)
+    int nB = 0, iB = 0, wq = 0, wb = 0;
+    std::vector<uint64_t> bfv_delta;   // [L][2] floor(Q/t) mod q_i, Shoup pair
+    std::vector<uint64_t> bfv_const;   // packed, see BfvLayout
+    uint64_t bfv_qinv_t = 0;           // Q^-1 mod t (decryption)
     uint64_t t = 0;  // plaintext modulus (BGV); 1 for CKKS (its formulas' t)
     std::vector<uint64_t> q;     // L + K + 1 moduli: Q, then P, then t
     std::vector<uint64_t> psi;   // primitive 2N-th roots (index L+K: zeta for t)
@@ -72,9 +78,21 @@ struct DevTables {
     uint64_t *ks_zc = nullptr;
     uint64_t *ks_yc = nullptr;
     uint64_t *md_phat_t = nullptr;
+    uint64_t *bfv_delta = nullptr;
+    uint64_t *bfv_const = nullptr;
 };
 
 bool build_tables(const hespmv_params &p, HostTables &h, std::string &err);
+
+// Offsets (words) of the BFV constants in HostTables::bfv_const
+struct BfvLayout {
+    int64_t qhat, Q, Qhalf, qhat_inv, bhat, B, Bhalf, bhat_inv, pow_b, pow_q, qinv_b, t_b, t_q, size;
+};
+BfvLayout bfv_layout(const HostTables &h);
+bool bfv_tables(const hespmv_params &p, HostTables &h, std::string &err);
+// BFV decryption of phase residues x [L][N] (coefficient domain):
+// m = round(t [x]_Q / Q) mod t, exactly
+void bfv_decrypt_coef(const HostTables &h, const uint64_t *x, uint64_t *m);
 
 // Host-side bit reversal, primality and roots (used by the table builder).
 uint32_t host_bitrev(uint32_t x, int bits);

@@ -53,6 +53,13 @@ cudaError_t op_moddown_final(const Ctx &c, const uint64_t *acc, const uint64_t *
 
 // fused hybrid key switch (ks.cu), keys in Montgomery form
 bool ks_fused_supported(const Ctx &c);
+// BFV HE-Mult tensor (exact scale and round), n ciphertext pairs in the
+// NTT domain -> out [n][3][L][N] (NTT domain); scratch of bfv_tensor_words(n)
+size_t bfv_tensor_words(const Ctx &c, size_t n);
+cudaError_t bfv_tensor(const Ctx &c, const uint64_t *A, const uint64_t *B, uint64_t *out, size_t n,
+                       uint64_t *scratch, cudaStream_t st);
+// BFV message lift: coefficients m in [0, t) -> Delta * m over Q, [n][L][N]
+cudaError_t op_bfv_delta(const Ctx &c, const uint64_t *m, uint64_t *out, size_t n, cudaStream_t st);
 // number of NTT split variants the fused key switch offers for this ring
 int ks_split_variants(const Ctx &c);
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,

@@ -1,6 +1,7 @@
 // Host construction of the RNS parameter tables: prime search, roots of
 // unity, twiddle tables (with Shoup companions) and the base-conversion
 // constants of hybrid key switching.
+#include <cmath>
 #include <cstring>
 
 #include "internal.h"
@@ -95,8 +96,9 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
     h.slots = p.slots ? p.slots : h.N / 2;
     if (h.slots < 1 || h.slots > h.N / 2) { err = "slots must be in [1, N/2]"; return false; }
     const uint64_t N = (uint64_t)h.N, twoN = 2 * N;
-    const bool ckks = p.scheme == HESPMV_SCHEME_CKKS;
-    if (p.scheme != HESPMV_SCHEME_BGV && !ckks) { err = "unknown scheme"; return false; }
+    const bool ckks = p.scheme == HESPMV_SCHEME_CKKS, bfv = p.scheme == HESPMV_SCHEME_BFV;
+    if (p.scheme != HESPMV_SCHEME_BGV && !ckks && !bfv) { err = "unknown scheme"; return false; }
+    if (bfv && p.K < h.alpha) { err = "BFV needs K >= alpha (P must cover a key-switching digit)"; return false; }
     h.scheme = p.scheme;
     if (ckks) {
         if (p.t != 0) { err = "CKKS takes no plaintext modulus (t = 0)"; return false; }
@@ -111,9 +113,9 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         err = "t must be a prime below 2^50 with t = 1 mod 2N";
         return false;
     }
-    // the t of every key, encryption and key-switching formula
-    const uint64_t tk = ckks ? 1 : p.t;
-    h.t = tk;
+    // the t of every key, encryption and key-switching formula (BGV only: t e)
+    const uint64_t tk = (ckks || bfv) ? 1 : p.t;
+    h.t = ckks ? 1 : p.t;  // plaintext modulus (none for CKKS)
     // ciphertext primes: descending from the largest q < 2^bits, q = 1 mod 2N
     h.q.clear();
     uint64_t cand = (((1ull << bits) - 2) / twoN) * twoN + 1;
@@ -125,7 +127,25 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
     // last table entry: t (BGV plaintext NTT); CKKS has no plaintext modulus
     // and keeps the next NTT prime there, unused
     if (!ckks) h.q.push_back(p.t);
-    const int M = p.L + p.K + 1;
+    if (bfv) {
+        // auxiliary basis B for the exact HE-Mult: B > 2 t N Q bounds both the
+        // integer tensor (|d| <= N Q^2 / 2 needs Q B > N Q^2) and its scaled
+        // and rounded value (|z| <= t N Q / 2 + 1)
+        double need = std::log2((double)p.t) + p.log2n + 2.0;
+        for (int i = 0; i < p.L; ++i) need += std::log2((double)h.q[i]);
+        h.iB = (int)h.q.size();
+        double have = 0;
+        while (have < need) {
+            if (cand < twoN) { err = "not enough NTT primes for the BFV auxiliary basis"; return false; }
+            if (prime64(cand) && cand != p.t) {
+                h.q.push_back(cand);
+                have += std::log2((double)cand);
+            }
+            cand -= twoN;
+        }
+        h.nB = (int)h.q.size() - h.iB;
+    }
+    const int M = (int)h.q.size();
     h.psi.resize(M);
     h.mc.resize(M);
     h.tw.assign((size_t)M * 4 * N, 0);
@@ -278,6 +298,7 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
             h.md_phat_t[((size_t)k * L + i) * 2 + 1] = shoup(w, qi);
         }
     }
+    if (bfv && !bfv_tables(p, h, err)) return false;
     // batching slot positions
     h.slot_idx.resize(N);
     uint64_t e = 1;

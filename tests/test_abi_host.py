@@ -177,3 +177,13 @@ def test_autotune_needs_a_device():
     with pytest.raises(B.HespmvError) as e:
         ctx.autotune([], [], [])
     assert e.value.code == B.HESPMV_E_INVALID
+
+
+def test_bfv_context_tables():
+    from oracle.params import ntt_primes
+    logn, L, K, dnum, t = synth.RING["c3"]
+    ctx = Context(logn, L, K, dnum, t, device=-1, torch_alloc=False, scheme="bfv")
+    q, psi, zeta = ctx.moduli()
+    assert q == ntt_primes(1 << logn, 50, L + K)
+    with pytest.raises(B.HespmvError):        # K < alpha
+        Context(6, 4, 1, 2, 12289, device=-1, torch_alloc=False, scheme="bfv")
