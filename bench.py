@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--scheme", default="bgv", choices=["bgv", "bfv", "ckks"],
+                    help="bgv (default), bfv (the paper's scheme, exact HE-Mult) or ckks "
+                         "(float64 values at scale 2^40, no fixed point)")
     ap.add_argument("--instances", type=int, default=64, help="c4: SpMVs per batched step")
     ap.add_argument("--pool", type=int, default=32, help="c5: distinct instances")
     ap.add_argument("--requests", type=int, default=10000, help="c5: Poisson requests")
@@ -524,17 +527,32 @@ def main():
     if batched:
         insts = synth.workload("c4", count=args.instances)
         ring = synth.RING["c4"]
+    elif args.scheme == "ckks":
+        A, x = synth.workload(args.config)        # float64 values as generated
+        if A.vals.dtype.kind != "f":
+            g = np.random.default_rng(7)
+            A.vals = g.uniform(-1, 1, A.nnz)
+            x = g.uniform(-1, 1, A.cols)
+        ring = synth.RING[args.config]
+        insts = [(A, x)]
     else:
         A, x, ring = load_workload(args.config)
         insts = [(A, x)]
     logn, L, K, dnum, t = ring
     ct_words = 2 * L * (1 << logn)
-    ctx = Context(logn, L, K, dnum, t, device=local)
+    ckks = args.scheme == "ckks"
+    ctx = Context(logn, L, K, dnum, 0 if ckks else t, device=local, scheme=args.scheme)
     ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in insts]
     ctx.keygen(1 + rank, sorted({s for m in ms for s in m.rotation_steps()}))
-    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 1000 * rank + i) for i, m in enumerate(ms)]
-    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=xx, seed=3 + 1000 * rank + i)
-          for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
+    if ckks:
+        As = [ctx.encrypt_real(m, B.HESPMV_MATRIX, a.vals, seed=2 + 1000 * rank + i)
+              for i, (m, (a, _)) in enumerate(zip(ms, insts))]
+        Xs = [ctx.encrypt_real(m, B.HESPMV_VECTOR, xx, seed=3 + 1000 * rank + i)
+              for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
+    else:
+        As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + 1000 * rank + i) for i, m in enumerate(ms)]
+        Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=xx, seed=3 + 1000 * rank + i)
+              for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
     # schedule autotuning (batch sizes, NTT split; results are unchanged)
     tune = None
     if not args.no_autotune:
@@ -552,8 +570,13 @@ def main():
         def step():
             ctx.spmv(ms[0], As[0], Xs[0], y=ys[0], stream=stream)
     torch.cuda.synchronize()
-    correct = all(list(ctx.decrypt(m, y)) == list(a.matvec(xx))
-                  for m, y, (a, xx) in zip(ms, ys, insts))
+    if ckks:   # 1e-3 relative in the max norm
+        correct = all(np.max(np.abs(ctx.decrypt_real(m, y) - a.matvec(xx)))
+                      <= 1e-3 * max(1.0, np.max(np.abs(a.matvec(xx))))
+                      for m, y, (a, xx) in zip(ms, ys, insts))
+    else:
+        correct = all(list(ctx.decrypt(m, y)) == list(a.matvec(xx))
+                      for m, y, (a, xx) in zip(ms, ys, insts))
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -628,7 +651,7 @@ def main():
                              sum(m.n_parts for m in ms), sum(m.n_rot for m in ms), args.config)
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.scheme == "bgv":
         A0, x0 = insts[0]
         sample = 8 if args.config in ("c3",) else 10 ** 9
         smp = OracleSample(A0, x0, ring, sample)
@@ -643,7 +666,13 @@ def main():
                          "scaled to one SpMV%s" % (n_s, n_total, dt,
                                                    " of the batch by chunk count" if batched else "")}
 
-    cfg = {"workload": CONFIGS[args.config], "instances": n_spmv, "chunks": n_chunks,
+    workload = CONFIGS[args.config]
+    if args.scheme == "bfv":
+        workload = workload.replace("BGV", "BFV (exact HE-Mult)")
+    elif args.scheme == "ckks":
+        workload = workload.replace("fixed point 2^15; ", "float64 values; ").replace(
+            "BGV", "CKKS scale 2^40, masks 2^30").split(", t=")[0]
+    cfg = {"workload": workload, "scheme": args.scheme, "instances": n_spmv, "chunks": n_chunks,
            "partitions": sum(m.n_parts for m in ms), "rotations": sum(m.n_rot for m in ms),
            "keyswitches": n_ks,
            "l2": "inputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * n_chunks * ct_words * 8 / 1e6),
