@@ -32,83 +32,131 @@ struct BfvArgs {
     uint64_t t;
 };
 
-// acc[0..W) = centred sum_i y_i * hat_i mod M (residues res[i * stride])
-__device__ void crt_centred(uint64_t *acc, const uint64_t *res, int64_t stride, int n, int W,
-                            const ModConst *mc, const uint64_t *hat, const uint64_t *hat_inv,
-                            const uint64_t *M, const uint64_t *Mhalf, const uint64_t *tq) {
-    for (int w = 0; w < W; ++w) acc[w] = 0;
+// Word counts: WT > 0 fixes the width at compile time (loops unroll, values
+// stay in registers); WT = 0 takes the runtime width w <= kMaxW.
+template <int WT>
+struct Wd {
+    static constexpr int cap = WT > 0 ? WT : kMaxW;
+    __device__ static __forceinline__ int of(int w) { return WT > 0 ? WT : w; }
+};
+
+// acc[0..W) += h[0..W) * y
+template <int WT>
+__device__ __forceinline__ void mw_addmul(uint64_t *acc, const uint64_t *h, uint64_t y, int w) {
+    const int W = Wd<WT>::of(w);
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < Wd<WT>::cap; ++k) {
+        if (k >= W) break;
+        const uint64_t lo = h[k] * y, hi = __umul64hi(h[k], y);
+        uint64_t s = acc[k] + lo;
+        uint64_t c1 = s < lo;
+        s += carry;
+        c1 += s < carry;
+        acc[k] = s;
+        carry = hi + c1;
+    }
+}
+
+// acc (below n M) -> its centred residue mod M, two's complement
+template <int WT>
+__device__ __forceinline__ void reduce_centre(uint64_t *acc, int n, int w, const uint64_t *M,
+                                              const uint64_t *Mhalf) {
+    const int W = Wd<WT>::of(w);
+    for (int it = 0; it < n; ++it) {
+        bool ge = true;
+#pragma unroll
+        for (int k = Wd<WT>::cap - 1; k >= 0; --k) {
+            if (k >= W) continue;
+            if (acc[k] != M[k]) {
+                ge = acc[k] > M[k];
+                break;
+            }
+        }
+        if (!ge) break;
+        uint64_t br = 0;
+#pragma unroll
+        for (int k = 0; k < Wd<WT>::cap; ++k) {
+            if (k >= W) break;
+            const uint64_t d = acc[k] - M[k] - br;
+            br = (acc[k] < M[k] || (acc[k] == M[k] && br)) ? 1 : 0;
+            acc[k] = d;
+        }
+    }
+    bool gt = false;  // acc > Mhalf
+#pragma unroll
+    for (int k = Wd<WT>::cap - 1; k >= 0; --k) {
+        if (k >= W) continue;
+        if (acc[k] != Mhalf[k]) {
+            gt = acc[k] > Mhalf[k];
+            break;
+        }
+    }
+    if (gt) {
+        uint64_t br = 0;
+#pragma unroll
+        for (int k = 0; k < Wd<WT>::cap; ++k) {
+            if (k >= W) break;
+            const uint64_t d = acc[k] - M[k] - br;
+            br = (acc[k] < M[k] || (acc[k] == M[k] && br)) ? 1 : 0;
+            acc[k] = d;
+        }
+    }
+}
+
+// acc[0..W) = centred sum_i [x_i hat_i^-1] hat_i mod M for residues
+// x_i = res[i * stride] (times t first when tq is given)
+template <int WT>
+__device__ __forceinline__ void crt_centred(uint64_t *acc, const uint64_t *res, int64_t stride, int n,
+                                            int w, const ModConst *mc, const uint64_t *hat,
+                                            const uint64_t *hat_inv, const uint64_t *M,
+                                            const uint64_t *Mhalf, const uint64_t *tq) {
+    const int W = Wd<WT>::of(w);
+#pragma unroll
+    for (int k = 0; k < Wd<WT>::cap; ++k)
+        if (k < W) acc[k] = 0;
     for (int i = 0; i < n; ++i) {
         const uint64_t q = mc[i].q;
         uint64_t x = res[(int64_t)i * stride];
         if (tq) x = mul_shoup(x, tq[2 * i], tq[2 * i + 1], q);     // t * x mod q
         const uint64_t y = mul_shoup(x, hat_inv[2 * i], hat_inv[2 * i + 1], q);
-        const uint64_t *h = hat + (int64_t)i * W;
-        uint64_t carry = 0;
-        for (int w = 0; w < W; ++w) {
-            const uint64_t lo = h[w] * y, hi = __umul64hi(h[w], y);
-            uint64_t s = acc[w] + lo;
-            uint64_t c1 = s < lo;
-            s += carry;
-            c1 += s < carry;
-            acc[w] = s;
-            carry = hi + c1;
-        }
+        mw_addmul<WT>(acc, hat + (int64_t)i * W, y, w);
     }
-    // reduce below M (the sum is below n M), then centre
-    for (int it = 0; it < n; ++it) {
-        bool ge = true;
-        for (int w = W - 1; w >= 0; --w)
-            if (acc[w] != M[w]) {
-                ge = acc[w] > M[w];
-                break;
-            }
-        if (!ge) break;
-        uint64_t br = 0;
-        for (int w = 0; w < W; ++w) {
-            const uint64_t d = acc[w] - M[w] - br;
-            br = (acc[w] < M[w] || (acc[w] == M[w] && br)) ? 1 : 0;
-            acc[w] = d;
-        }
-    }
-    bool gt = false;  // acc > Mhalf
-    for (int w = W - 1; w >= 0; --w)
-        if (acc[w] != Mhalf[w]) {
-            gt = acc[w] > Mhalf[w];
-            break;
-        }
-    if (gt) {
-        uint64_t br = 0;
-        for (int w = 0; w < W; ++w) {
-            const uint64_t d = acc[w] - M[w] - br;
-            br = (acc[w] < M[w] || (acc[w] == M[w] && br)) ? 1 : 0;
-            acc[w] = d;
-        }
-    }
+    reduce_centre<WT>(acc, n, w, M, Mhalf);
 }
 
-// two's complement W-word value mod p; pw[k] = 2^(64 k) mod p for k <= W
-__device__ uint64_t mod_word(const uint64_t *a, int W, const ModConst &m, const uint64_t *pw) {
-    uint64_t r = 0;
-    for (int w = 0; w < W; ++w) {
-        const uint64_t aw = barrett_reduce(0, a[w], m.q, m.mu, m.k);
-        r = add_mod(r, mul_mod(aw, pw[w], m), m.q);
+// two's complement W-word value mod q; pw[2k], pw[2k+1] = 2^(64 k) mod q and
+// its Shoup companion, k <= W: one lazy Shoup product per word (< 2q each,
+// the sum stays below 2^64), one full reduction at the end
+template <int WT>
+__device__ __forceinline__ uint64_t mod_word(const uint64_t *a, int w, const ModConst &m,
+                                             const uint64_t *pw) {
+    const int W = Wd<WT>::of(w);
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < Wd<WT>::cap; ++k) {
+        if (k >= W) break;
+        s += mul_shoup_lazy(a[k], pw[2 * k], pw[2 * k + 1], m.q);
     }
-    if ((int64_t)a[W - 1] < 0) r = sub_mod(r, pw[W], m.q);  // minus 2^(64 W)
+    uint64_t r = mul_shoup(s, 1, m.one_s, m.q);
+    if ((int64_t)a[W - 1] < 0) r = sub_mod(r, pw[2 * W], m.q);  // minus 2^(64 W)
     return r;
 }
 
 // 2: centred extension of the four input polynomials to B
+template <int WQ>
 __global__ void k_bfv_extend(BfvArgs a, const uint64_t *coef, uint64_t *ext, int64_t total) {
     const int64_t N = 1LL << a.log2n, LN = (int64_t)a.L * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t poly = i >> a.log2n, k = i & (N - 1);  // poly = item * 4 + p
-        uint64_t x[kMaxW];
-        crt_centred(x, coef + poly * LN + k, N, a.L, a.wq, a.mc, a.k + a.o.qhat, a.k + a.o.qhat_inv,
-                    a.k + a.o.Q, a.k + a.o.Qhalf, nullptr);
+        uint64_t x[Wd<WQ>::cap];
+        crt_centred<WQ>(x, coef + poly * LN + k, N, a.L, a.wq, a.mc, a.k + a.o.qhat, a.k + a.o.qhat_inv,
+                        a.k + a.o.Q, a.k + a.o.Qhalf, nullptr);
         uint64_t *out = ext + poly * (int64_t)a.nB * N + k;
         for (int j = 0; j < a.nB; ++j)
-            out[(int64_t)j * N] = mod_word(x, a.wq, a.mc[a.iB + j], a.k + a.o.pow_b + (int64_t)j * (a.wq + 1));
+            out[(int64_t)j * N] = mod_word<WQ>(x, a.wq, a.mc[a.iB + j],
+                                               a.k + a.o.pow_b + (int64_t)j * 2 * (a.wq + 1));
     }
 }
 
@@ -142,32 +190,38 @@ __global__ void k_bfv_tensor(BfvArgs a, const uint64_t *A, const uint64_t *Bc, c
 }
 
 // 4: scale and round, coefficient domain: d [n][3][L + nB][N] -> z [n][3][L][N]
+template <int WQ, int WB>
 __global__ void k_bfv_scale(BfvArgs a, const uint64_t *d, uint64_t *z, int64_t total) {
     const int64_t N = 1LL << a.log2n, LB = a.L + a.nB;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t comp = i >> a.log2n, k = i & (N - 1);  // comp = item * 3 + c
         const uint64_t *dq = d + comp * LB * N + k, *db = dq + (int64_t)a.L * N;
-        uint64_t r[kMaxW];
+        uint64_t r[Wd<WQ>::cap];
         // r = [t d]_Q, centred
-        crt_centred(r, dq, N, a.L, a.wq, a.mc, a.k + a.o.qhat, a.k + a.o.qhat_inv, a.k + a.o.Q,
-                    a.k + a.o.Qhalf, a.k + a.o.t_q);
-        // z mod b_j = (t d_j - r) Q^-1, kept in place of d's B residues (registers)
-        uint64_t zb[kMaxW];
+        crt_centred<WQ>(r, dq, N, a.L, a.wq, a.mc, a.k + a.o.qhat, a.k + a.o.qhat_inv, a.k + a.o.Q,
+                        a.k + a.o.Qhalf, a.k + a.o.t_q);
+        // z mod b_j = (t d_j - r) Q^-1, accumulated straight into z's exact
+        // reconstruction from its B residues
+        uint64_t zz[Wd<WB>::cap];
+        const int W = Wd<WB>::of(a.wb);
+#pragma unroll
+        for (int u = 0; u < Wd<WB>::cap; ++u)
+            if (u < W) zz[u] = 0;
         for (int j = 0; j < a.nB; ++j) {
             const ModConst m = a.mc[a.iB + j];
             const uint64_t *tb = a.k + a.o.t_b + 2 * j, *qi = a.k + a.o.qinv_b + 2 * j;
+            const uint64_t *bi = a.k + a.o.bhat_inv + 2 * j;
             const uint64_t td = mul_shoup(db[(int64_t)j * N], tb[0], tb[1], m.q);
-            const uint64_t rj = mod_word(r, a.wq, m, a.k + a.o.pow_b + (int64_t)j * (a.wq + 1));
-            zb[j] = mul_shoup(sub_mod(td, rj, m.q), qi[0], qi[1], m.q);
+            const uint64_t rj = mod_word<WQ>(r, a.wq, m, a.k + a.o.pow_b + (int64_t)j * 2 * (a.wq + 1));
+            const uint64_t zj = mul_shoup(sub_mod(td, rj, m.q), qi[0], qi[1], m.q);
+            mw_addmul<WB>(zz, a.k + a.o.bhat + (int64_t)j * W, mul_shoup(zj, bi[0], bi[1], m.q), a.wb);
         }
-        // z exactly from its B residues, then to every q_i
-        uint64_t zz[kMaxW];
-        crt_centred(zz, zb, 1, a.nB, a.wb, a.mc + a.iB, a.k + a.o.bhat, a.k + a.o.bhat_inv, a.k + a.o.B,
-                    a.k + a.o.Bhalf, nullptr);
+        reduce_centre<WB>(zz, a.nB, a.wb, a.k + a.o.B, a.k + a.o.Bhalf);
         uint64_t *out = z + comp * (int64_t)a.L * N + k;
         for (int l = 0; l < a.L; ++l)
-            out[(int64_t)l * N] = mod_word(zz, a.wb, a.mc[l], a.k + a.o.pow_q + (int64_t)l * (a.wb + 1));
+            out[(int64_t)l * N] = mod_word<WB>(zz, a.wb, a.mc[l],
+                                               a.k + a.o.pow_q + (int64_t)l * 2 * (a.wb + 1));
     }
 }
 
@@ -232,7 +286,12 @@ cudaError_t bfv_tensor(const Ctx &c, const uint64_t *A, const uint64_t *B, uint6
     // 2. centred extension to B
     int r = prof_begin(c, "k_bfv_extend", st);
     int64_t total = (int64_t)n * 4 * N;
-    k_bfv_extend<<<grid_for(total, 128), 128, 0, st>>>(a, coef, ext, total);
+    switch (a.wq) {
+        case 4: k_bfv_extend<4><<<grid_for(total, 128), 128, 0, st>>>(a, coef, ext, total); break;
+        case 5: k_bfv_extend<5><<<grid_for(total, 128), 128, 0, st>>>(a, coef, ext, total); break;
+        case 8: k_bfv_extend<8><<<grid_for(total, 128), 128, 0, st>>>(a, coef, ext, total); break;
+        default: k_bfv_extend<0><<<grid_for(total, 128), 128, 0, st>>>(a, coef, ext, total); break;
+    }
     prof_end(c, r, st);
     if ((e = launch_ntt(c, ext, a.iB, (int)nB, (int)(4 * n), nB * N, false, st))) return e;
     // 3. tensor over Q u B, back to coefficients
@@ -245,7 +304,14 @@ cudaError_t bfv_tensor(const Ctx &c, const uint64_t *A, const uint64_t *B, uint6
     // 4. scale and round, 5. NTT over Q
     r = prof_begin(c, "k_bfv_scale", st);
     total = (int64_t)n * 3 * N;
-    k_bfv_scale<<<grid_for(total, 128), 128, 0, st>>>(a, d, out, total);
+    if (a.wq == 4 && a.wb == 5)
+        k_bfv_scale<4, 5><<<grid_for(total, 128), 128, 0, st>>>(a, d, out, total);
+    else if (a.wq == 5 && a.wb == 6)
+        k_bfv_scale<5, 6><<<grid_for(total, 128), 128, 0, st>>>(a, d, out, total);
+    else if (a.wq == 8 && a.wb == 9)
+        k_bfv_scale<8, 9><<<grid_for(total, 128), 128, 0, st>>>(a, d, out, total);
+    else
+        k_bfv_scale<0, 0><<<grid_for(total, 128), 128, 0, st>>>(a, d, out, total);
     prof_end(c, r, st);
     if ((e = launch_ntt(c, out, 0, (int)L, (int)(3 * n), LN, false, st))) return e;
     return cudaGetLastError();

@@ -71,8 +71,8 @@ BfvLayout bfv_layout(const HostTables &h) {
     o.B = at;        at += wb;
     o.Bhalf = at;    at += wb;
     o.bhat_inv = at; at += 2 * nB;
-    o.pow_b = at;    at += nB * (wq + 1);  // 2^(64 k) mod b_j, k <= wq
-    o.pow_q = at;    at += L * (wb + 1);   // 2^(64 k) mod q_i, k <= wb
+    o.pow_b = at;    at += 2 * nB * (wq + 1);  // 2^(64 k) mod b_j, k <= wq (Shoup pairs)
+    o.pow_q = at;    at += 2 * L * (wb + 1);   // 2^(64 k) mod q_i, k <= wb (Shoup pairs)
     o.qinv_b = at;   at += 2 * nB;
     o.t_b = at;      at += 2 * nB;
     o.t_q = at;      at += 2 * L;
@@ -104,7 +104,8 @@ bool bfv_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         uint64_t pw = 1;
         const uint64_t r64 = (uint64_t)(((u128)1 << 64) % qs[i]);
         for (int k = 0; k <= h.wb; ++k) {
-            c[o.pow_q + (int64_t)i * (h.wb + 1) + k] = pw;
+            c[o.pow_q + (int64_t)i * 2 * (h.wb + 1) + 2 * k] = pw;
+            c[o.pow_q + (int64_t)i * 2 * (h.wb + 1) + 2 * k + 1] = shoup(pw, qs[i]);
             pw = mulm(pw, r64, qs[i]);
         }
         c[o.t_q + 2 * i] = t % qs[i];
@@ -125,7 +126,8 @@ bool bfv_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         uint64_t pw = 1;
         const uint64_t r64 = (uint64_t)(((u128)1 << 64) % b);
         for (int k = 0; k <= h.wq; ++k) {
-            c[o.pow_b + (int64_t)j * (h.wq + 1) + k] = pw;
+            c[o.pow_b + (int64_t)j * 2 * (h.wq + 1) + 2 * k] = pw;
+            c[o.pow_b + (int64_t)j * 2 * (h.wq + 1) + 2 * k + 1] = shoup(pw, b);
             pw = mulm(pw, r64, b);
         }
         const uint64_t qinv = invm(mod_small(Q, b), b);

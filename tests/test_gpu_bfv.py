@@ -127,3 +127,21 @@ def test_bfv_c3_stencil_full_size():
     y = ctx.spmv(m, ca, cx)
     torch.cuda.synchronize()
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+
+
+def test_bfv_generic_word_counts():
+    """A ring whose multi-word widths (Q: 5 words, B: 5 words) take the
+    kernels' runtime-width path rather than a specialised one."""
+    t = plain_modulus(1 << 6, 1 << 20)
+    ctx, orc = pair(6, 4, 2, 2, t, slots=24)
+    A, x = synth.small_matrix(8, 80, 40, 500, -9, 9)
+    probe = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    keys(ctx, orc, probe.rotation_steps(), 5)
+    m, plan, ca, cx, oa, ox = run_pair(ctx, orc, A, x)
+    y = ctx.spmv(m, ca, cx)
+    torch.cuda.synchronize()
+    ores = S.spmv(orc, plan, oa, ox)
+    gy = y.download()
+    for p in range(len(ores)):
+        assert np.array_equal(gy[p], ores[p]), p
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
