@@ -193,13 +193,16 @@ def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot):
     m = {
         # fused key switch (one launch of each per step and batch group)
         "k_ks_intt_rows": (n_ks * (L + 2 * K) * h * n2, n_ks * (L + 2 * K) * 2 * w),
-        "k_ks_intt_cols": (n_ks * (L + 2 * K) * (h * n1 + N), n_ks * (L + 2 * K) * 2 * w),
-        "k_ks_modup_cols": (n_ks * ext * (h * n1 + alpha * N), n_ks * (L + ext) * w),
+        # ModUp: the digit's inverse column pass, base conversion, forward column pass
+        "k_ks_modup_cols": (n_ks * (L * (h * n1 + N) + ext * (h * n1 + alpha * N)),
+                            n_ks * (L + ext) * w),
         "k_ks_rows_fwd": (n_ks * ext * h * n2, n_ks * ext * 2 * w),
         # key product with the output addend (times P) on the Q primes
         "k_ks_mac": (n_ks * 2 * (dnum * LK + L) * N,
                      n_ks * (ext + L + 2 * L + 2 * LK) * w + 2 * dnum * LK * w),
-        "k_ks_moddown_cols": (n_ks * 2 * L * (h * n1 + K * N), n_ks * 2 * (K + L) * w),
+        # ModDown: the P limbs' inverse column pass, conversion, forward column pass
+        "k_ks_moddown_cols": (n_ks * 2 * (K * (h * n1 + N) + L * (h * n1 + K * N)),
+                              n_ks * 2 * (K + L) * w),
         "k_ks_rows_final": (n_ks * 2 * L * (h * n2 + N), n_ks * 2 * L * 3 * w),
         # ciphertext arithmetic
         "k_tensor": (n_chunks * 4 * L * N, n_chunks * 7 * L * w),

@@ -7,15 +7,16 @@
 //  1. inverse NTT of d, row pass                         (d -> dc)
 //     (with HE-Mult fused in, d = a1 * b1 is formed here and in step 4, and
 //     the addend (a0 b0, a0 b1 + a1 b0) in step 4: no tensor in memory)
-//  2. inverse NTT column pass, N^-1 * Qhat^-1 folded in  (dc -> z)
-//  3. ModUp + forward column pass: one CTA raises a digit's z columns to
-//     every other prime and transforms them                 (z -> ext)
+//  2. ModUp: one CTA takes a digit's column tiles through the inverse
+//     column pass (N^-1 * Qhat^-1 folded in), raises them to every other
+//     prime and runs those primes' forward column pass     (dc -> ext)
 //  4. forward row pass of the raised limbs, in place             (ext)
 //     and the inner product with the key: the digit's own primes use d
 //     directly; the addend enters on the Q primes times P; 128-bit sums,
 //     one Montgomery reduction                                     (-> acc)
-//  5. inverse NTT of acc's P limbs, t^-1 * Phat^-1 * N^-1 folded in (-> y)
-//  6. ModDown conversion (t folded in) + forward column pass   (y -> dh)
+//  5. inverse NTT row pass of acc's P limbs                         (-> y)
+//  6. inverse column pass of y (t^-1 * Phat^-1 * N^-1 folded in), ModDown
+//     conversion (t folded in) and forward column pass        (y -> dh)
 //  7. forward row pass of delta, (acc - delta) * P^-1            (-> out)
 // Scratch per item (words): L*N (dc, z) + dnum*(L+K)*N (ext) + 2*(L+K)*N
 // (acc) + 2*L*N (dh).
@@ -108,32 +109,10 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
 }
 
-// inverse column pass in place with per-limb fold constants fc[k][4]
-template <int LC>
-__global__ __launch_bounds__(kNttThreads) void k_ks_intt_cols(KsArgs a, uint64_t *x, int64_t is,
-                                                              int nl, int prime0,
-                                                              const uint64_t *fc) {
-    constexpr int M = 1 << LC, TC = kNttTile / M;
-    __shared__ uint64_t sm[kNttTile];
-    const int N = 1 << a.log2n, C = N >> LC;
-    const int item = blockIdx.y / nl, k = blockIdx.y - item * nl, prime = prime0 + k;
-    const uint64_t q = a.mc[prime].q;
-    const TwPair *itw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N + 2 * N);
-    const int t = threadIdx.x, cc = t % TC, j = t / TC;
-    uint64_t *col = x + item * is + (int64_t)k * N + blockIdx.x * TC + cc;
-    const uint64_t *f = fc + 4 * k;
-    uint64_t v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = col[(int64_t)Pass<LC>::last(j, e) * C];
-    inv_body<LC, true>(v, j, 1, sm, ColIdx<TC>{cc}, itw, q, f[0], f[1], f[2], f[3]);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) col[(int64_t)Pass<LC>::first(j, e) * C] = v[e];
-}
-
 // ModUp of digit jd to every prime outside it, fused with the forward column
 // pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, [0, 4q))
 template <int LC>
-__global__ __launch_bounds__(kNttThreads) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
+__global__ __launch_bounds__(kNttThreads, 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
                                                                uint64_t *ext) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     __shared__ uint64_t sm[kNttTile];
@@ -142,13 +121,19 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_modup_cols(KsArgs a, const u
     const int i0 = jd * a.alpha, i1 = min(L, i0 + a.alpha), na = i1 - i0;
     const int t = threadIdx.x, cc = t % TC, j = t / TC;
     const int64_t cofs = blockIdx.x * TC + cc;
+    // the digit's own limbs: inverse column pass of the row-pass output, with
+    // N^-1 * Qhat^-1 folded in (coefficients of d times the ModUp factor)
     uint64_t zs[4][8];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (s < na) {
-            const uint64_t *src = z + ((int64_t)item * L + i0 + s) * N + cofs;
+            const int pi = i0 + s;
+            const uint64_t *src = z + ((int64_t)item * L + pi) * N + cofs;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) zs[s][e] = src[(int64_t)Pass<LC>::first(j, e) * C];
+            for (int e = 0; e < 8; ++e) zs[s][e] = src[(int64_t)Pass<LC>::last(j, e) * C];
+            const TwPair *itw = (const TwPair *)(a.tw + (int64_t)pi * 4 * N + 2 * N);
+            const uint64_t *f = a.zc + 4 * pi;
+            inv_body<LC, true>(zs[s], j, 1, sm, ColIdx<TC>{cc}, itw, a.mc[pi].q, f[0], f[1], f[2], f[3]);
         }
     }
     uint64_t *dst0 = ext + ((int64_t)item * a.dnum + jd) * LK * N + cofs;
@@ -282,7 +267,7 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
 // with t folded in, fused with the forward column pass: -> dh [n][2][L][N]
 template <int LC>
-__global__ __launch_bounds__(kNttThreads) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
+__global__ __launch_bounds__(kNttThreads, 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
                                                                  uint64_t *dh) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     __shared__ uint64_t sm[kNttTile];
@@ -290,13 +275,18 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_moddown_cols(KsArgs a, const
     const int ic = blockIdx.y;  // item * 2 + component
     const int t = threadIdx.x, cc = t % TC, j = t / TC;
     const int64_t cofs = blockIdx.x * TC + cc;
+    // the P limbs: inverse column pass of the row-pass output, with
+    // t^-1 * Phat^-1 * N^-1 folded in
     uint64_t ys[4][8];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (s < K) {
             const uint64_t *src = acc + ((int64_t)ic * LK + L + s) * N + cofs;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) ys[s][e] = src[(int64_t)Pass<LC>::first(j, e) * C];
+            for (int e = 0; e < 8; ++e) ys[s][e] = src[(int64_t)Pass<LC>::last(j, e) * C];
+            const TwPair *itw = (const TwPair *)(a.tw + (int64_t)(L + s) * 4 * N + 2 * N);
+            const uint64_t *f = a.yc + 4 * s;
+            inv_body<LC, true>(ys[s], j, 1, sm, ColIdx<TC>{cc}, itw, a.mc[L + s].q, f[0], f[1], f[2], f[3]);
         }
     }
     for (int i = 0; i < L; ++i) {
@@ -364,9 +354,6 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     r = prof_begin(c, "k_ks_intt_rows", st);
     k_ks_intt_rows_src<LR><<<dim3(gr, n * L), kNttThreads, 0, st>>>(a, s, z);
     prof_end(c, r, st);
-    r = prof_begin(c, "k_ks_intt_cols", st);
-    k_ks_intt_cols<LC><<<dim3(gc, n * L), kNttThreads, 0, st>>>(a, z, L * N, (int)L, 0, a.zc);
-    prof_end(c, r, st);
     r = prof_begin(c, "k_ks_modup_cols", st);
     k_ks_modup_cols<LC><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
     prof_end(c, r, st);
@@ -390,10 +377,6 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     k_ks_intt_rows<LR><<<dim3(gr, n * 2 * K), kNttThreads, 0, st>>>(a, acc + L * N, LK * N,
                                                                     acc + L * N, LK * N, (int)K,
                                                                     (int)L);
-    prof_end(c, r, st);
-    r = prof_begin(c, "k_ks_intt_cols", st);
-    k_ks_intt_cols<LC><<<dim3(gc, n * 2 * K), kNttThreads, 0, st>>>(a, acc + L * N, LK * N,
-                                                                     (int)K, (int)L, a.yc);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_moddown_cols", st);
     k_ks_moddown_cols<LC><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
