@@ -111,8 +111,8 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
 
 // ModUp of digit jd to every prime outside it, fused with the forward column
 // pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, [0, 4q))
-template <int LC>
-__global__ __launch_bounds__(kNttThreads, 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
+template <int LC, int AMAX>
+__global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
                                                                uint64_t *ext) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     __shared__ uint64_t sm[kNttTile];
@@ -123,9 +123,9 @@ __global__ __launch_bounds__(kNttThreads, 2) void k_ks_modup_cols(KsArgs a, cons
     const int64_t cofs = blockIdx.x * TC + cc;
     // the digit's own limbs: inverse column pass of the row-pass output, with
     // N^-1 * Qhat^-1 folded in (coefficients of d times the ModUp factor)
-    uint64_t zs[4][8];
+    uint64_t zs[AMAX][8];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < AMAX; ++s) {
         if (s < na) {
             const int pi = i0 + s;
             const uint64_t *src = z + ((int64_t)item * L + pi) * N + cofs;
@@ -145,7 +145,7 @@ __global__ __launch_bounds__(kNttThreads, 2) void k_ks_modup_cols(KsArgs a, cons
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = 0;
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < AMAX; ++s) {
             if (s < na) {
                 const uint64_t *cst = a.modup_mod + (((int64_t)jd * a.alpha + s) * LK + l) * 2;
                 const uint64_t w = cst[0], ws = cst[1];
@@ -266,8 +266,8 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
 
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
 // with t folded in, fused with the forward column pass: -> dh [n][2][L][N]
-template <int LC>
-__global__ __launch_bounds__(kNttThreads, 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
+template <int LC, int KMAX>
+__global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
                                                                  uint64_t *dh) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     __shared__ uint64_t sm[kNttTile];
@@ -277,9 +277,9 @@ __global__ __launch_bounds__(kNttThreads, 2) void k_ks_moddown_cols(KsArgs a, co
     const int64_t cofs = blockIdx.x * TC + cc;
     // the P limbs: inverse column pass of the row-pass output, with
     // t^-1 * Phat^-1 * N^-1 folded in
-    uint64_t ys[4][8];
+    uint64_t ys[KMAX][8];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < KMAX; ++s) {
         if (s < K) {
             const uint64_t *src = acc + ((int64_t)ic * LK + L + s) * N + cofs;
 #pragma unroll
@@ -296,7 +296,7 @@ __global__ __launch_bounds__(kNttThreads, 2) void k_ks_moddown_cols(KsArgs a, co
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = 0;
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < KMAX; ++s) {
             if (s < K) {
                 const uint64_t w = a.phat_t[((int64_t)s * L + i) * 2];
                 const uint64_t ws = a.phat_t[((int64_t)s * L + i) * 2 + 1];
@@ -355,7 +355,10 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     k_ks_intt_rows_src<LR><<<dim3(gr, n * L), kNttThreads, 0, st>>>(a, s, z);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_modup_cols", st);
-    k_ks_modup_cols<LC><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
+    if (c.alpha <= 2)
+        k_ks_modup_cols<LC, 2><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
+    else
+        k_ks_modup_cols<LC, 4><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_fwd", st);
     k_ks_rows_fwd<LR><<<dim3(gr, n * c.dnum * LK), kNttThreads, 0, st>>>(a, ext);
@@ -379,7 +382,10 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
                                                                     (int)L);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_moddown_cols", st);
-    k_ks_moddown_cols<LC><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
+    if (c.K <= 2)
+        k_ks_moddown_cols<LC, 2><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
+    else
+        k_ks_moddown_cols<LC, 4><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_final", st);
     k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, out);
