@@ -195,16 +195,22 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t 
 // Items vary fastest so a key limb stays in L2 while every item uses it.
 // DN > 0: dnum known at compile time, every digit's loads issued before the
 // first product; DN = 0: any dnum, one digit at a time.
-template <int DN>
+template <int DN, int IT>
 __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc s, KsAdd ad, const uint64_t *ext,
                                                 const uint64_t *key, uint64_t *acc, int n) {
-    // grid: x = coefficient pairs, y = l * n + item
+    // grid: x = coefficient pairs, y = l * ceil(n / IT) + item group; IT
+    // items per thread share the key loads
     const int N = 1 << a.log2n, LK = a.L + a.K;
-    const int l = blockIdx.y / n;
-    const int64_t item = blockIdx.y - (int64_t)l * n;
+    const int ng = (n + IT - 1) / IT;
+    const int l = blockIdx.y / ng;
+    const int64_t item0 = (int64_t)(blockIdx.y - l * ng) * IT;
     const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (k >= N) return;
     const ModConst mc = a.mc[l];
+#pragma unroll 1
+    for (int it = 0; it < IT; ++it) {
+    const int64_t item = item0 + it;
+    if (item >= n) break;
     constexpr int B = DN > 0 ? DN : 1;
     const int dnum = DN > 0 ? DN : a.dnum;
     uint64_t h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
@@ -262,6 +268,7 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
     uint64_t *o1 = o0 + (int64_t)LK * N;
     *(ulonglong2 *)o0 = make_ulonglong2(redc(h0a, l0a, mc.q, mc.qneg), redc(h0b, l0b, mc.q, mc.qneg));
     *(ulonglong2 *)o1 = make_ulonglong2(redc(h1a, l1a, mc.q, mc.qneg), redc(h1b, l1b, mc.q, mc.qneg));
+    }
 }
 
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
@@ -365,14 +372,15 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_mac", st);
     {
-        const dim3 g((unsigned)((N / 2 + 255) / 256), (unsigned)(n * LK));
+        constexpr int IT = 2;  // items per thread
+        const dim3 g((unsigned)((N / 2 + 255) / 256), (unsigned)(((n + IT - 1) / IT) * LK));
         const KsAdd ad{add, add_is, add_cs, add_mask};
         switch (c.dnum) {
-            case 2: k_ks_mac<2><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 3: k_ks_mac<3><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 4: k_ks_mac<4><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 5: k_ks_mac<5><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            default: k_ks_mac<0><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 2: k_ks_mac<2, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 3: k_ks_mac<3, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 4: k_ks_mac<4, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 5: k_ks_mac<5, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            default: k_ks_mac<0, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
         }
     }
     prof_end(c, r, st);
