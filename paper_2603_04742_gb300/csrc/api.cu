@@ -695,7 +695,7 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
               upload(ctx, d.modup_mod, h.modup_mod) && upload(ctx, d.md_pk, h.md_pk) &&
               upload(ctx, d.md_phat, h.md_phat) && upload(ctx, d.md_t, h.md_t) &&
               upload(ctx, d.md_pinv, h.md_pinv) && upload(ctx, d.p_mod_q, h.p_mod_q) &&
-              upload(ctx, d.p_mont, h.p_mont) &&
+              upload(ctx, d.p_mont, h.p_mont) && upload(ctx, d.p_mont2, h.p_mont2) &&
               upload(ctx, d.slot_idx, h.slot_idx) && upload(ctx, d.dec, h.dec) &&
               upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod) &&
               upload(ctx, d.ks_zc, h.ks_zc) && upload(ctx, d.ks_yc, h.ks_yc) &&

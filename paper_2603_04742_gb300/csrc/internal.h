@@ -44,6 +44,7 @@ struct HostTables {
     std::vector<uint64_t> p_mod_q;     // [L][2]
     // P * 2^64 mod q_i: P in Montgomery form, for sums reduced by REDC
     std::vector<uint64_t> p_mont;      // [L]
+    std::vector<uint64_t> p_mont2;     // [L] P * 2^128 mod q_i
     // slot positions in the NTT domain: [N/2] for row 0, then [N/2] for row 1
     std::vector<int32_t> slot_idx;
     // decryption CRT: per Q prime (Qhat_i^-1 mod q_i, Shoup) and (Qhat_i mod t, Shoup),
@@ -71,6 +72,7 @@ struct DevTables {
     uint64_t *md_pinv = nullptr;
     uint64_t *p_mod_q = nullptr;
     uint64_t *p_mont = nullptr;
+    uint64_t *p_mont2 = nullptr;
     int32_t *slot_idx = nullptr;
     uint64_t *dec = nullptr;
     double *dec_inv_q = nullptr;

@@ -34,6 +34,7 @@ struct KsArgs {
     const uint64_t *phat_t;    // [K][L][2]  Phat_k * t mod q_i
     const uint64_t *pinv;      // [L][2]
     const uint64_t *pmont;     // [L]     P * 2^64 mod q_i
+    const uint64_t *pmont2;    // [L]     P * 2^128 mod q_i
     int log2n, L, K, dnum, alpha;
 };
 
@@ -54,6 +55,19 @@ struct KsAdd {
     int64_t is, cs;
     int mask;
 };
+
+// (a b + c d) * 2^-64 mod q, left in [0, 2q) (a, b, c, d < q < 2^50, so
+// the 128-bit sum stays below q * 2^64)
+__device__ __forceinline__ uint64_t mont_lazy(uint64_t a, uint64_t b, uint64_t c, uint64_t d,
+                                              const ModConst &m) {
+    uint64_t lo = a * b, hi = __umul64hi(a, b);
+    const uint64_t l2 = c * d;
+    hi += __umul64hi(c, d);
+    lo += l2;
+    hi += lo < l2;
+    const uint64_t t = lo * m.qneg;
+    return hi + __umul64hi(t, m.q) + (lo != 0);
+}
 
 __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
     const uint64_t m = lo * qneg;
@@ -218,15 +232,18 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
     ulonglong2 own = make_ulonglong2(0, 0);
     if (l < a.L) {
         ulonglong2 y0 = make_ulonglong2(0, 0), y1 = make_ulonglong2(0, 0);
+        uint64_t pm = a.pmont[l];
         if (s.ta) {
             const int64_t o = item * s.ts + (int64_t)l * N + k, LN = (int64_t)a.L * N;
             const ulonglong2 a0 = *(const ulonglong2 *)(s.ta + o), b0 = *(const ulonglong2 *)(s.tb + o);
             const ulonglong2 a1 = *(const ulonglong2 *)(s.ta + o + LN);
             const ulonglong2 b1 = *(const ulonglong2 *)(s.tb + o + LN);
             own = make_ulonglong2(mul_mod(a1.x, b1.x, mc), mul_mod(a1.y, b1.y, mc));
-            y0 = make_ulonglong2(mul_mod(a0.x, b0.x, mc), mul_mod(a0.y, b0.y, mc));
-            y1 = make_ulonglong2(add_mod(mul_mod(a0.x, b1.x, mc), mul_mod(a1.x, b0.x, mc), mc.q),
-                                 add_mod(mul_mod(a0.y, b1.y, mc), mul_mod(a1.y, b0.y, mc), mc.q));
+            // y0, y1 as Montgomery residues (times 2^-64, in [0, 2q)); their
+            // factor P * 2^128 mod q restores the scale in the final reduction
+            y0 = make_ulonglong2(mont_lazy(a0.x, b0.x, 0, 0, mc), mont_lazy(a0.y, b0.y, 0, 0, mc));
+            y1 = make_ulonglong2(mont_lazy(a0.x, b1.x, a1.x, b0.x, mc), mont_lazy(a0.y, b1.y, a1.y, b0.y, mc));
+            pm = a.pmont2[l];
         } else {
             own = *(const ulonglong2 *)(s.d + item * s.ds + (int64_t)l * N + k);
             if (ad.p) {
@@ -235,7 +252,6 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
                 if (ad.mask & 2) y1 = *(const ulonglong2 *)(base + ad.cs);
             }
         }
-        const uint64_t pm = a.pmont[l];
         uint64_t p;
         p = y0.x * pm; l0a += p; h0a += __umul64hi(y0.x, pm) + (l0a < p);
         p = y0.y * pm; l0b += p; h0b += __umul64hi(y0.y, pm) + (l0b < p);
@@ -436,6 +452,7 @@ static KsArgs ks_args(const Ctx &c) {
     a.phat_t = h->d.md_phat_t;
     a.pinv = h->d.md_pinv;
     a.pmont = h->d.p_mont;
+    a.pmont2 = h->d.p_mont2;
     a.log2n = c.log2n;
     a.L = c.L;
     a.K = c.K;

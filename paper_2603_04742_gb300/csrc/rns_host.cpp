@@ -215,6 +215,7 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
     h.md_pinv.assign((size_t)L * 2, 0);
     h.p_mod_q.assign((size_t)L * 2, 0);
     h.p_mont.assign((size_t)L, 0);
+    h.p_mont2.assign((size_t)L, 0);
     for (int k = 0; k < K; ++k) {
         const uint64_t pk = h.q[L + k];
         uint64_t phat = 1;
@@ -239,6 +240,7 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         h.p_mod_q[i * 2] = P;
         h.p_mod_q[i * 2 + 1] = shoup(P, qi);
         h.p_mont[i] = mulm(P, (0 - qi) % qi, qi);
+        h.p_mont2[i] = mulm(h.p_mont[i], (0 - qi) % qi, qi);
         const uint64_t pinv = invm(P, qi);
         h.md_pinv[i * 2] = pinv;
         h.md_pinv[i * 2 + 1] = shoup(pinv, qi);
