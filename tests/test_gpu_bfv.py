@@ -145,3 +145,22 @@ def test_bfv_generic_word_counts():
     for p in range(len(ores)):
         assert np.array_equal(gy[p], ores[p]), p
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+
+
+def test_bfv_plain_matrix_mode():
+    logn, L, K, dnum, t = synth.RING["c1"]
+    ctx, orc = pair(logn, L, K, dnum, t)
+    A, x = synth.workload("c1")
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    keys(ctx, orc, m.rotation_steps(), 3)
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    pa = ctx.encode_matrix_plain(m)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=9)
+    y = ctx.spmv_ptmatrix(m, pa, cx)
+    torch.cuda.synchronize()
+    ores = S.spmv_plain_matrix(orc, plan, S.encode_matrix_plain(orc, plan),
+                               S.encrypt_vector(orc, plan, x, 9))
+    gy = y.download()
+    for p in range(len(ores)):
+        assert np.array_equal(gy[p], ores[p]), p
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
