@@ -689,6 +689,7 @@ def main():
         "data": "synthetic", "config": cfg,
         "nnz_per_s": value * nnz / n_spmv,
         "step_ms": step_ms,
+        "hbm_bytes": int(ctx.device_bytes()),
         "correct": bool(correct),
         "e2e": e2e,
         "gpu_launches": int(sum(v[0] for v in prof.values())),

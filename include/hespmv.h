@@ -199,6 +199,21 @@ int hespmv_cssc_arrays(const hespmv_cssc *m, int32_t part, const int64_t **va, c
  * (ascending).  Writes at most cap entries; *n receives the total. */
 int hespmv_cssc_rotation_steps(const hespmv_cssc *m, int32_t *steps, size_t cap, size_t *n);
 
+/* Key transfer: the key holder hands the evaluator its evaluation keys
+ * (public key, relinearisation key, Galois keys) without the secret key.
+ * Format: "HSKY", version, kind, Galois key count, ring fingerprint, then
+ * [sk [L+K][N]] (HESPMV_KEYS_ALL only), pk [2][L][N], rlk
+ * [dnum][2][L+K][N], and per Galois key its element (u64) and key, as the
+ * device holds them (key-switching keys in Montgomery form x 2^64 mod q).
+ * buf NULL: *len receives the size only.  Deserialize validates the ring,
+ * the length, every residue and every Galois element (HESPMV_E_INVALID) and
+ * replaces the context's keys; a context loaded with HESPMV_KEYS_EVAL
+ * evaluates and encrypts but refuses to decrypt.  Synchronous. */
+#define HESPMV_KEYS_EVAL 0
+#define HESPMV_KEYS_ALL 1
+int hespmv_keys_serialize(hespmv_ctx *ctx, int32_t what, void *buf, size_t cap, size_t *len);
+int hespmv_keys_deserialize(hespmv_ctx *ctx, const void *buf, size_t len);
+
 /* Serialize a CSSC plan (Algorithm 1: what Client A keeps, or the chunk
  * shapes it hands to the cloud).  Format, little-endian, fields 8-byte
  * aligned: magic "HSCS", version, kind, s, rows, cols, nnz, n_parts, then

@@ -145,6 +145,18 @@ class Context:
     def encode_cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x=0):
         return Cssc(self, csr_rows, csr_cols, rowptr, colidx, vals, max_abs_x)
 
+    def keys_serialize(self, what=B.HESPMV_KEYS_EVAL):
+        """Evaluation keys (or, HESPMV_KEYS_ALL, every key) as bytes."""
+        n = c_size_t()
+        self.check(self.lib.hespmv_keys_serialize(self.h, what, None, 0, byref(n)))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        self.check(self.lib.hespmv_keys_serialize(self.h, what, buf, n.value, byref(n)))
+        return buf.raw[:n.value]
+
+    def keys_deserialize(self, data):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self.check(self.lib.hespmv_keys_deserialize(self.h, buf, len(data)))
+
     def cssc_from_bytes(self, data):
         """A plan from Cssc.serialize output (hespmv_cssc_deserialize)."""
         buf = ctypes.create_string_buffer(bytes(data), len(data))

@@ -26,6 +26,8 @@ HESPMV_VECTOR = 1
 HESPMV_SCHEME_BGV = 0
 HESPMV_SCHEME_CKKS = 1
 HESPMV_SCHEME_BFV = 2
+HESPMV_KEYS_EVAL = 0
+HESPMV_KEYS_ALL = 1
 HESPMV_SER_FULL = 0
 HESPMV_SER_SHAPE = 1
 HESPMV_KEY_SECRET = 0
@@ -86,6 +88,8 @@ SIGNATURES = {
     "hespmv_ctbatch_upload": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_download": (c_int, [c_void_p, u64p, c_size_t, c_void_p]),
     "hespmv_ctbatch_serialize": (c_int, [c_void_p, c_void_p, c_size_t, szp]),
+    "hespmv_keys_serialize": (c_int, [c_void_p, c_int32, c_void_p, c_size_t, szp]),
+    "hespmv_keys_deserialize": (c_int, [c_void_p, c_void_p, c_size_t]),
     "hespmv_encrypt_real": (c_int, [c_void_p, c_void_p, c_int32, f64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_encode_matrix_plain_real": (c_int, [c_void_p, c_void_p, f64p, POINTER(c_void_p)]),
     "hespmv_ckks_encode": (c_int, [c_void_p, f64p, c_size_t, c_int32, i64p]),

@@ -11,6 +11,8 @@
 #include <thread>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace hespmv;
@@ -32,6 +34,12 @@ struct DeviceGuard {
         cudaGetDevice(&cur);
         if (prev >= 0 && cur != prev) cudaSetDevice(prev);
     }
+};
+
+// NVTX range for profilers (a no-op when none is attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
 };
 
 #define FAIL(code, msg)        \
@@ -516,9 +524,11 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     const size_t G = pp.G, GR = pp.GR;
     const size_t prod_w = pp.total_chunks * CT;
     uint64_t *prod = ws, *dbuf = prod + prod_w, *scr = dbuf + G * 3 * LN;
+    Range r_eval("hespmv: evaluation");
     // 1) HE-Mult of every chunk pair, G at a time across instances (HE-CMult
     //    when the matrix is in the clear)
     if (pp.pt_matrix) {
+        Range r("hespmv: HE-CMult");
         size_t k0 = 0;
         for (size_t i = 0; i < n_inst; ++i) {
             const size_t nk = ms[i]->plan.chunks.size();
@@ -526,6 +536,7 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
             k0 += nk;
         }
     } else {
+        Range r("hespmv: HE-Mult + relinearisation");
         std::vector<std::pair<size_t, size_t>> all;  // (instance, chunk)
         all.reserve(pp.total_chunks);
         for (size_t i = 0; i < n_inst; ++i)
@@ -554,6 +565,7 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     }
     // 2) totalSum: batched rotation rounds
     if (pp.rp) {
+        Range r("hespmv: totalSum rotations");
         uint64_t *V = dbuf, *CUR = V + GR * CT, *PB = CUR + GR * CT, *OB = PB + GR * CT;
         uint64_t *ks = OB + GR * CT;
         const int32_t *I = pp.rp->d_idx;
@@ -586,6 +598,7 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         }
     }
     // 3) masked accumulation per partition
+    Range r_mask("hespmv: masked accumulation");
     size_t k0 = 0;
     for (size_t i = 0; i < n_inst; ++i) {
         const Plan &pl = ms[i]->plan;
@@ -823,6 +836,7 @@ int hespmv_keygen(hespmv_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size
     if (rc) return rc;
     if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("keygen: ") + cudaGetErrorString(e));
     ctx->have_keys = true;
+    ctx->has_sk = true;
     return HESPMV_OK;
 }
 
@@ -1036,6 +1050,7 @@ namespace {
 
 const uint32_t kCsscMagic = 0x53435348u;  // "HSCS"
 const uint32_t kCtMagic = 0x54435348u;    // "HSCT"
+const uint32_t kKeyMagic = 0x594B5348u;   // "HSKY"
 const uint32_t kSerVersion = 1;
 
 struct Writer {
@@ -1268,6 +1283,119 @@ int hespmv_ctbatch_deserialize(hespmv_ctx *ctx, const void *buf, size_t len, hes
 // Encode and encrypt (or, plain, only encode) the chunks of one operand.
 // BGV: integer values (matrix values from the plan, or x); CKKS: real values
 // `real` (the matrix's CSR values, or x) encoded at 2^scale_bits.
+// ------------------------------------------------------------ key transfer
+// "HSKY", version, what, Galois key count, ring fingerprint, then [sk], pk,
+// rlk and each Galois key (u64 element, key), all as the device holds them.
+int hespmv_keys_serialize(hespmv_ctx *ctx, int32_t what, void *buf, size_t cap, size_t *len) {
+    if (!ctx || !len || (what != HESPMV_KEYS_EVAL && what != HESPMV_KEYS_ALL)) return HESPMV_E_INVALID;
+    if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "no keys");
+    if (what == HESPMV_KEYS_ALL && !ctx->has_sk) FAIL(HESPMV_E_INVALID, "no secret key in this context");
+    NEED_DEVICE(ctx);
+    const size_t N = ctx->h.N, L = ctx->h.L, LK = L + ctx->h.K, KW = (size_t)ctx->h.dnum * 2 * LK * N;
+    const size_t words = (what == HESPMV_KEYS_ALL ? LK * N : 0) + 2 * L * N + KW + ctx->gk.size() * (1 + KW);
+    *len = 24 + words * 8;
+    if (!buf) return HESPMV_OK;
+    if (cap < *len) FAIL(HESPMV_E_INVALID, "buffer too small");
+    Writer w{(uint8_t *)buf, cap};
+    w.val(kKeyMagic);
+    w.val(kSerVersion);
+    w.val((uint32_t)what);
+    w.val((uint32_t)ctx->gk.size());
+    w.val(ring_fingerprint(ctx));
+    DeviceGuard g(ctx->device);
+    uint8_t *p = (uint8_t *)buf + w.n;
+    auto take = [&](const uint64_t *dev, size_t n) {
+        const cudaError_t e = cudaMemcpy(p, dev, n * 8, cudaMemcpyDeviceToHost);
+        p += n * 8;
+        return e == cudaSuccess;
+    };
+    bool ok = true;
+    if (what == HESPMV_KEYS_ALL) ok = take(ctx->sk, LK * N);
+    ok = ok && take(ctx->pk, 2 * L * N) && take(ctx->rlk, KW);
+    for (auto &kv : ctx->gk) {
+        const uint64_t e = kv.first;
+        std::memcpy(p, &e, 8);
+        p += 8;
+        ok = ok && take(kv.second, KW);
+    }
+    if (!ok) FAIL(HESPMV_E_CUDA, "key download failed");
+    return HESPMV_OK;
+}
+
+int hespmv_keys_deserialize(hespmv_ctx *ctx, const void *buf, size_t len) {
+    if (!ctx || !buf) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    Reader r{(const uint8_t *)buf, len};
+    uint32_t magic = 0, ver = 0, what = 0, ng = 0;
+    uint64_t fp = 0;
+    r.val(magic), r.val(ver), r.val(what), r.val(ng), r.val(fp);
+    if (!r.ok || magic != kKeyMagic || ver != kSerVersion) FAIL(HESPMV_E_INVALID, "not a key stream");
+    if (what != HESPMV_KEYS_EVAL && what != HESPMV_KEYS_ALL) FAIL(HESPMV_E_INVALID, "unknown key kind");
+    if (fp != ring_fingerprint(ctx)) FAIL(HESPMV_E_INVALID, "keys belong to another ring");
+    const size_t N = ctx->h.N, L = ctx->h.L, LK = L + ctx->h.K, KW = (size_t)ctx->h.dnum * 2 * LK * N;
+    const size_t words = (what == HESPMV_KEYS_ALL ? LK * N : 0) + 2 * L * N + KW;
+    if (ng > (len - r.n) / 8 / (1 + KW) || r.n + (words + (size_t)ng * (1 + KW)) * 8 != len)
+        FAIL(HESPMV_E_INVALID, "key stream length mismatch");
+    const uint8_t *p = (const uint8_t *)buf + r.n;
+    // every residue below its prime: limb l of an [.][LK][N] or [.][L][N] block
+    auto check = [&](const uint8_t *src, size_t n, size_t limbs) {
+        for (size_t i = 0; i < n; ++i) {
+            uint64_t v;
+            std::memcpy(&v, src + i * 8, 8);
+            if (v >= ctx->h.q[(i / N) % limbs]) return false;
+        }
+        return true;
+    };
+    {
+        const uint8_t *q = p;
+        bool ok = true;
+        if (what == HESPMV_KEYS_ALL) ok = check(q, LK * N, LK), q += LK * N * 8;
+        ok = ok && check(q, 2 * L * N, L);
+        q += 2 * L * N * 8;
+        ok = ok && check(q, KW, LK);
+        q += KW * 8;
+        std::set<uint64_t> seen;
+        for (uint32_t k = 0; ok && k < ng; ++k) {
+            uint64_t e;
+            std::memcpy(&e, q, 8);
+            ok = e % 2 == 1 && e < 2 * N && seen.insert(e).second && check(q + 8, KW, LK);
+            q += (1 + KW) * 8;
+        }
+        if (!ok) FAIL(HESPMV_E_INVALID, "key stream holds an invalid residue or Galois element");
+    }
+    DeviceGuard g(ctx->device);
+    if (!ctx->sk) {
+        ctx->sk = owned<uint64_t>(ctx, LK * N);
+        ctx->pk = owned<uint64_t>(ctx, 2 * L * N);
+        ctx->rlk = owned<uint64_t>(ctx, KW);
+        if (!ctx->sk || !ctx->pk || !ctx->rlk) FAIL(HESPMV_E_NOMEM, "key allocation failed");
+    }
+    auto put = [&](uint64_t *dev, size_t n) {
+        const bool ok = cudaMemcpy(dev, p, n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        p += n * 8;
+        return ok;
+    };
+    bool ok = true;
+    if (what == HESPMV_KEYS_ALL)
+        ok = put(ctx->sk, LK * N);
+    else
+        ok = cudaMemset(ctx->sk, 0, LK * N * 8) == cudaSuccess;
+    ok = ok && put(ctx->pk, 2 * L * N) && put(ctx->rlk, KW);
+    for (uint32_t k = 0; ok && k < ng; ++k) {
+        uint64_t e;
+        std::memcpy(&e, p, 8);
+        p += 8;
+        uint64_t *key = ctx->gk.count((uint32_t)e) ? ctx->gk[(uint32_t)e] : owned<uint64_t>(ctx, KW);
+        if (!key) FAIL(HESPMV_E_NOMEM, "key allocation failed");
+        ctx->gk[(uint32_t)e] = key;
+        ok = put(key, KW);
+    }
+    if (!ok) FAIL(HESPMV_E_CUDA, "key upload failed");
+    ctx->have_keys = true;
+    ctx->has_sk = what == HESPMV_KEYS_ALL;
+    return HESPMV_OK;
+}
+
 static int encrypt_impl(hespmv_ctx *ctx, const hespmv_cssc *m, int32_t which, const int64_t *x,
                         const double *real, uint64_t seed, bool plain, hespmv_ctbatch **out) {
     if (!ctx || !m || !out) return HESPMV_E_INVALID;
@@ -1502,6 +1630,7 @@ int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
     if (!ctx || !b || !slots_out || index >= b->n) return HESPMV_E_INVALID;
     if (ctx->h.scheme == HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "CKKS: hespmv_decrypt_real_slots");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    if (!ctx->has_sk) FAIL(HESPMV_E_INVALID, "this context holds evaluation keys only (no secret key)");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
@@ -1532,6 +1661,7 @@ int hespmv_decrypt_real_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t i
         return HESPMV_E_INVALID;
     if (ctx->h.scheme != HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "not a CKKS context");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
+    if (!ctx->has_sk) FAIL(HESPMV_E_INVALID, "this context holds evaluation keys only (no secret key)");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);

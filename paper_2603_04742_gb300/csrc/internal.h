@@ -215,6 +215,7 @@ struct hespmv_ctx {
     size_t owned_bytes = 0;
     // keys (device)
     bool have_keys = false;
+    bool has_sk = false;       // the secret key is present (keygen, or loaded with it)
     uint64_t *sk = nullptr;    // [L+K][N]
     uint64_t *pk = nullptr;    // [2][L][N]
     uint64_t *rlk = nullptr;   // [dnum][2][L+K][N]

@@ -388,3 +388,38 @@ def test_spmv_plain_matrix_parity(name):
     for p_ in range(len(ores)):
         assert np.array_equal(gy[p_], ores[p_])
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+
+
+def test_outputs_fully_written_over_poisoned_buffers():
+    """Every output word is written: result buffers start filled with the
+    sentinel 2^64 - 1 (never a residue) and must hold the oracle's values."""
+    logn, L, K, dnum, t = synth.RING["c1"]
+    A, x = synth.workload("c1")
+    from paper_2603_04742_gb300.api import Context, CtBatch
+    probe = Context(logn, L, K, dnum, t, device=-1, torch_alloc=False)
+    steps = probe.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals).rotation_steps()
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=1, steps=steps)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    N, CT = 1 << logn, 2 * L * (1 << logn)
+    sentinel = np.full(m.n_parts * CT, np.iinfo(np.uint64).max, dtype=np.uint64)
+    y = CtBatch.create(ctx, m.n_parts)
+    y.upload(sentinel)
+    ctx.set_graphs(False)
+    ctx.spmv(m, ca, cx, y=y)
+    torch.cuda.synchronize()
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    ores = S.spmv(orc, plan, S.encrypt_matrix(orc, plan, 2), S.encrypt_vector(orc, plan, x, 3))
+    got = y.download()
+    for p_ in range(len(ores)):
+        assert np.array_equal(got[p_], ores[p_]), p_
+    # the primitives' outputs too
+    out = torch.from_numpy(np.full(3 * L * N, -1, dtype=np.int64)).cuda()
+    ctx.he_tensor(ca.ptr, cx.ptr, out.data_ptr())
+    assert np.array_equal(host(out).reshape(3, L, N), orc.tensor(*[S.encrypt_matrix(orc, plan, 2)[0],
+                                                                   S.encrypt_vector(orc, plan, x, 3)[0]]))
+    out.fill_(-1)
+    ctx.he_mult(ca.ptr, cx.ptr, out.data_ptr())
+    got = host(out)
+    assert np.all(got[:CT] != np.iinfo(np.uint64).max) and np.all(got[CT:] == np.iinfo(np.uint64).max)

@@ -25,7 +25,8 @@ def test_cloud_evaluates_deserialized_inputs():
     cloud = Context(logn, L, K, dnum, t)
     m = client.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
     client.keygen(5, m.rotation_steps())
-    cloud.keygen(5, m.rotation_steps())
+    # the cloud receives the evaluation keys only
+    cloud.keys_deserialize(client.keys_serialize(B.HESPMV_KEYS_EVAL))
     ca = client.encrypt(m, B.HESPMV_MATRIX, seed=2)
     cx = client.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
     mc = cloud.cssc_from_bytes(m.serialize(B.HESPMV_SER_SHAPE))
@@ -40,7 +41,10 @@ def test_cloud_evaluates_deserialized_inputs():
     y_local = client.spmv(m, ca, cx)
     torch.cuda.synchronize()
     assert np.array_equal(y_local.download(), y_back.download())
-    # the cloud's plan has no values, indices or row map
+    # the cloud's plan has no values, indices or row map, and it has no secret key
+    with pytest.raises(B.HespmvError) as e:
+        cloud.decrypt_slots(y)
+    assert e.value.code == B.HESPMV_E_INVALID
     for call in (lambda: cloud.decrypt(mc, y), lambda: cloud.encrypt(mc, B.HESPMV_MATRIX)):
         with pytest.raises(B.HespmvError) as e:
             call()
@@ -76,3 +80,31 @@ def test_malformed_ciphertext_streams_refused():
     # and the context still works afterwards
     back = ctx.ctbatch_from_bytes(blob)
     assert back.n == m.n_chunks
+
+
+def test_key_streams_round_trip_and_refusals():
+    from paper_2603_04742_gb300.api import Context
+    logn, L, K, dnum, t = synth.RING["c1"]
+    a = Context(logn, L, K, dnum, t)
+    a.keygen(3, [1, 2, 7])
+    full = a.keys_serialize(B.HESPMV_KEYS_ALL)
+    b = Context(logn, L, K, dnum, t)
+    b.keys_deserialize(full)
+    for kind in (B.HESPMV_KEY_SECRET, B.HESPMV_KEY_PUBLIC, B.HESPMV_KEY_RELIN):
+        assert np.array_equal(a.key_export(kind), b.key_export(kind))
+    assert b.keys_serialize(B.HESPMV_KEYS_ALL) == full
+    ev = a.keys_serialize(B.HESPMV_KEYS_EVAL)
+    assert len(ev) < len(full)
+    head = 24
+    bad_cases = [ev[:-8], ev + b"\0" * 8, ev[:head], b"\0" * 32]
+    bad = bytearray(ev)
+    struct.pack_into("<Q", bad, head, a.moduli()[0][0])   # pk residue == q_0
+    bad_cases.append(bytes(bad))
+    bad = bytearray(ev)
+    struct.pack_into("<I", bad, 8, 5)                        # unknown kind
+    bad_cases.append(bytes(bad))
+    other = Context(logn, L, K, dnum, plain_modulus(1 << logn, 1 << 17))
+    for data, ctx in [(d, b) for d in bad_cases] + [(ev, other)]:
+        with pytest.raises(B.HespmvError) as e:
+            ctx.keys_deserialize(data)
+        assert e.value.code == B.HESPMV_E_INVALID
