@@ -435,7 +435,8 @@ typedef struct hespmv_tuning {
                            (0: 32 at N = 2^15, else 64)                                  */
     int32_t ntt_split;  /* fused key switch NTT split: 0 = default, 1 = alternative
                            (N = 2^LC x 2^LR with LC and LR exchanged or shifted by one)  */
-    int32_t reserved;
+    int32_t rows_tma;   /* fused key switch forward row pass: 0 = one CTA per tile,
+                           1 = persistent CTAs fed by bulk asynchronous copies      */
     double ms;          /* hespmv_autotune: device time of one evaluation             */
 } hespmv_tuning;
 
@@ -447,9 +448,9 @@ int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t);
 
 /* Autotuner: times the evaluation of the given SpMVs (as hespmv_spmv_batched
  * would run them, into its own result buffers, on its own stream) under
- * candidate schedules -- each NTT split, then HE-Mult batches 1, 2, 4, ...
- * up to 128, then rotation round widths 4, 8, ... up to 512 (capped by the
- * chunk counts) -- by coordinate descent from the
+ * candidate schedules -- each NTT split, each row-pass form, then HE-Mult
+ * batches 1, 2, 4, ... up to 128, then rotation round widths 4, 8, ... up to
+ * 512 (capped by the chunk counts) -- by coordinate descent from the
  * default, `reps` timed evaluations after one warm-up each, skipping any
  * whose workspace would not fit in free device memory.  Applies the fastest
  * and returns it in *best; tried[0 .. min(cap, *n_tried)) lists every
@@ -463,6 +464,17 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
  * and replayed afterwards (one launch per evaluation).  enable = 0 makes
  * every evaluation launch its kernels one by one.  Graphs are not used while
  * profiling is enabled.  Default: enabled. */
+/* Device-side waits (the bulk-copy barriers of the key-switch row pass) poll
+ * a bounded number of times; one that runs out records an error code in the
+ * context and its kernel stops early.  This call reads and clears it:
+ * HESPMV_E_TIMEOUT if set (results since the last check are invalid), else
+ * HESPMV_OK.  Decryption calls it first.  Synchronous. */
+int hespmv_device_status(hespmv_ctx *ctx, int32_t *code);
+/* Self-test of that path: launches a kernel whose wait cannot complete (a
+ * barrier expecting bytes no copy delivers), which gives up after a few
+ * polls; returns HESPMV_E_TIMEOUT and leaves the context usable. */
+int hespmv_selftest_wait_timeout(hespmv_ctx *ctx, int32_t *code);
+
 int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable);
 
 /* ------------------------------------------------------------ measurement */

@@ -715,6 +715,16 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
               upload(ctx, d.md_phat_t, h.md_phat_t);
     if (ok && h.scheme == HESPMV_SCHEME_BFV)
         ok = upload(ctx, d.bfv_delta, h.bfv_delta) && upload(ctx, d.bfv_const, h.bfv_const);
+    if (ok) {
+        d.err = owned<int>(ctx, 1);
+        ok = d.err && cudaMemset(d.err, 0, sizeof(int)) == cudaSuccess;
+    }
+    if (ok && ks_prepare(view(ctx)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "key-switch launch setup failed";
+        *out = ctx;
+        return HESPMV_E_CUDA;
+    }
     if (!ok) {
         ctx->err = "table upload failed";
         *out = ctx;
@@ -1633,6 +1643,10 @@ int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
     if (!ctx->has_sk) FAIL(HESPMV_E_INVALID, "this context holds evaluation keys only (no secret key)");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
+    {  // results that a timed-out device wait left incomplete are not decrypted
+        const int rc = hespmv_device_status(ctx, nullptr);
+        if (rc) return rc;
+    }
     const Ctx c = view(ctx);
     const int64_t N = c.N, LN = (int64_t)c.L * N;
     uint64_t *ws = workspace(ctx, (LN + 2 * N) * 8);
@@ -1664,6 +1678,10 @@ int hespmv_decrypt_real_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t i
     if (!ctx->has_sk) FAIL(HESPMV_E_INVALID, "this context holds evaluation keys only (no secret key)");
     NEED_DEVICE(ctx);
     DeviceGuard g(ctx->device);
+    {  // results that a timed-out device wait left incomplete are not decrypted
+        const int rc = hespmv_device_status(ctx, nullptr);
+        if (rc) return rc;
+    }
     const Ctx c = view(ctx);
     const int64_t N = c.N, LN = (int64_t)c.L * N;
     uint64_t *x = workspace(ctx, LN * 8);
@@ -1862,14 +1880,17 @@ void drop_graphs(hespmv_ctx *ctx) {
 
 struct TuneState {
     size_t G, GR;
-    int split;
+    int split, rows_tma;
 };
 
 void apply_tuning(hespmv_ctx *ctx, const TuneState &s) {
-    if (ctx->tune_G != s.G || ctx->tune_GR != s.GR || ctx->ks_split != s.split) drop_graphs(ctx);
+    if (ctx->tune_G != s.G || ctx->tune_GR != s.GR || ctx->ks_split != s.split ||
+        ctx->rows_tma != s.rows_tma)
+        drop_graphs(ctx);
     ctx->tune_G = s.G;
     ctx->tune_GR = s.GR;
     ctx->ks_split = s.split;
+    ctx->rows_tma = s.rows_tma;
 }
 
 }  // namespace
@@ -1882,12 +1903,15 @@ int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t) {
         FAIL(HESPMV_E_INVALID, "batch sizes must be in [0, 4096]");
     if (t->ntt_split < 0 || t->ntt_split >= ks_split_variants(view(ctx)))
         FAIL(HESPMV_E_INVALID, "no such NTT split for this ring");
+    if (t->rows_tma < 0 || t->rows_tma > (ks_fused_supported(view(ctx)) ? 1 : 0))
+        FAIL(HESPMV_E_INVALID, "no such row-pass form for this ring");
+    const TuneState ts{(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split, t->rows_tma};
     if (ctx->device >= 0) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
-        apply_tuning(ctx, {(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split});
+        apply_tuning(ctx, ts);
     } else {
-        apply_tuning(ctx, {(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split});
+        apply_tuning(ctx, ts);
     }
     return HESPMV_OK;
 }
@@ -1898,6 +1922,7 @@ int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t) {
     t->mult_batch = (int32_t)ctx->tune_G;
     t->rot_batch = (int32_t)ctx->tune_GR;
     t->ntt_split = ctx->ks_split;
+    t->rows_tma = ctx->rows_tma;
     t->ms = 0;
     return HESPMV_OK;
 }
@@ -1938,7 +1963,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         total += nc;
         for (const Chunk &ch : m[i]->plan.chunks) rot += ch.c > 1;
     }
-    const TuneState orig{ctx->tune_G, ctx->tune_GR, ctx->ks_split};
+    const TuneState orig{ctx->tune_G, ctx->tune_GR, ctx->ks_split, ctx->rows_tma};
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1957,6 +1982,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         rec.mult_batch = (int32_t)pp.G;
         rec.rot_batch = (int32_t)pp.GR;
         rec.ntt_split = s.split;
+        rec.rows_tma = s.rows_tma;
         if (pp.need_bytes > ctx->ws_bytes && pp.need_bytes - ctx->ws_bytes > free_b / 10 * 9) {
             rec.ms = -1;
             log.push_back(rec);
@@ -1980,7 +2006,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         log.push_back(rec);
         return rec.ms;
     };
-    TuneState cur{0, 0, 0}, bestS = cur;
+    TuneState cur{0, 0, 0, 0}, bestS = cur;
     double best_ms = ok ? measure(cur) : -2;
     if (best_ms < 0 && err_rc == HESPMV_OK && ok) {
         err_rc = HESPMV_E_NOMEM;
@@ -1999,20 +2025,21 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         }
     };
     // coordinate descent: NTT split, then the HE-Mult batch, then the rotation round width
-    for (int v = 1; v < ks_split_variants(c); ++v) consider({bestS.G, bestS.GR, v});
+    for (int v = 1; v < ks_split_variants(c); ++v) consider({bestS.G, bestS.GR, v, bestS.rows_tma});
+    if (ks_fused_supported(c)) consider({bestS.G, bestS.GR, bestS.split, 1});
     {
         std::vector<size_t> gs;
         for (size_t v = 1; v < 128 && v < total; v *= 2) gs.push_back(v);
         gs.push_back(std::min<size_t>(total, 128));
         const TuneState base = bestS;
-        for (size_t v : gs) consider({v, base.GR, base.split});
+        for (size_t v : gs) consider({v, base.GR, base.split, base.rows_tma});
     }
     if (rot > 0) {
         std::vector<size_t> grs;
         for (size_t v = 4; v < 512 && v < rot; v *= 2) grs.push_back(v);
         grs.push_back(std::min<size_t>(rot, 512));
         const TuneState base = bestS;
-        for (size_t v : grs) consider({base.G, v, base.split});
+        for (size_t v : grs) consider({base.G, v, base.split, base.rows_tma});
     }
     if (st) cudaStreamSynchronize(st);
     if (e0) cudaEventDestroy(e0);
@@ -2027,11 +2054,34 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
     best->mult_batch = (int32_t)bestS.G;
     best->rot_batch = (int32_t)bestS.GR;
     best->ntt_split = bestS.split;
-    best->reserved = 0;
+    best->rows_tma = bestS.rows_tma;
     best->ms = best_ms;
     if (n_tried) *n_tried = log.size();
     for (size_t i = 0; tried && i < log.size() && i < cap; ++i) tried[i] = log[i];
     return HESPMV_OK;
+}
+
+int hespmv_device_status(hespmv_ctx *ctx, int32_t *code) {
+    if (!ctx) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    int v = 0;
+    CK(cudaMemcpy(&v, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code) *code = v;
+    if (v) {
+        CK(cudaMemset(ctx->d.err, 0, sizeof(int)));
+        FAIL(HESPMV_E_TIMEOUT, "a device-side wait ran out (code " + std::to_string(v) + ")");
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_selftest_wait_timeout(hespmv_ctx *ctx, int32_t *code) {
+    if (!ctx) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    CK(op_wait_probe(view(ctx), 0));
+    CK(cudaDeviceSynchronize());
+    return hespmv_device_status(ctx, code);
 }
 
 int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable) {

@@ -82,6 +82,7 @@ struct DevTables {
     uint64_t *md_phat_t = nullptr;
     uint64_t *bfv_delta = nullptr;
     uint64_t *bfv_const = nullptr;
+    int *err = nullptr;  // device error word written by bounded waits
 };
 
 bool build_tables(const hespmv_params &p, HostTables &h, std::string &err);
@@ -237,6 +238,7 @@ struct hespmv_ctx {
     size_t tune_G = 0;   // HE-Mult batch: ciphertexts per fused key switch
     size_t tune_GR = 0;  // totalSum round width: ciphertexts per rotation round
     int ks_split = 0;    // fused key switch: NTT split variant (column/row pass sizes)
+    int rows_tma = 0;    // fused key switch: persistent TMA-fed forward row pass
     // staging for evaluations from host buffers
     void *io = nullptr;
     size_t io_bytes = 0;
@@ -267,9 +269,9 @@ namespace hespmv {
 struct Ctx {
     const hespmv_ctx *c;
     int N, L, K, dnum, alpha, log2n;
-    int ks_split;
+    int ks_split, rows_tma;
 };
 inline Ctx view(const hespmv_ctx *c) {
-    return Ctx{c, c->h.N, c->h.L, c->h.K, c->h.dnum, c->h.alpha, c->h.log2n, c->ks_split};
+    return Ctx{c, c->h.N, c->h.L, c->h.K, c->h.dnum, c->h.alpha, c->h.log2n, c->ks_split, c->rows_tma};
 }
 }  // namespace hespmv

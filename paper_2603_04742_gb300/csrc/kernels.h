@@ -62,6 +62,11 @@ cudaError_t bfv_tensor(const Ctx &c, const uint64_t *A, const uint64_t *B, uint6
 cudaError_t op_bfv_delta(const Ctx &c, const uint64_t *m, uint64_t *out, size_t n, cudaStream_t st);
 // number of NTT split variants the fused key switch offers for this ring
 int ks_split_variants(const Ctx &c);
+// one-time launch setup of the fused key switch (shared-memory limits and
+// persistent grid sizes); call outside any stream capture
+cudaError_t ks_prepare(const Ctx &c);
+// self-test: a bounded wait that runs out and sets the device error word
+cudaError_t op_wait_probe(const Ctx &c, cudaStream_t st);
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);

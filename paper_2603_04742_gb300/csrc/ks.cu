@@ -20,6 +20,9 @@
 //  7. forward row pass of delta, (acc - delta) * P^-1            (-> out)
 // Scratch per item (words): L*N (dc, z) + dnum*(L+K)*N (ext) + 2*(L+K)*N
 // (acc) + 2*L*N (dh).
+#include <algorithm>
+
+#include "async_copy.cuh"
 #include "kernels.h"
 #include "ntt_core.cuh"
 
@@ -35,6 +38,7 @@ struct KsArgs {
     const uint64_t *pinv;      // [L][2]
     const uint64_t *pmont;     // [L]     P * 2^64 mod q_i
     const uint64_t *pmont2;    // [L]     P * 2^128 mod q_i
+    int *err;                  // device error word (bounded waits)
     int log2n, L, K, dnum, alpha;
 };
 
@@ -197,6 +201,94 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t 
     for (int e = 0; e < 8; ++e) v[e] = x[Pass<LR>::first(j, e)];
     fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
     store8(x + 8 * j, v);
+}
+
+// The same row pass with persistent CTAs walking the 2048-word row tiles:
+// the TMA engine (cp.async.bulk) brings the next tile into the second
+// shared buffer while the current one is transformed.  A schedule option
+// (the autotuner times both; on the stencil ring the direct kernel wins).
+template <int LR>
+__global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd_tma(KsArgs a, uint64_t *ext, int n_tiles,
+                                                                 int log_gr) {
+    constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
+    extern __shared__ __align__(128) uint64_t dyn[];
+    uint64_t *const buf0 = dyn, *const buf1 = dyn + kNttTile;
+    uint64_t *sm = dyn + 2 * kNttTile, *bars = sm + kRowTileWords;
+    const int N = 1 << a.log2n, n1 = a.log2n - LR, LK = a.L + a.K;
+    const int t = threadIdx.x, rr = t / P, j = t % P;
+    // tile id = (limb block) * 2^log_gr + x (32-bit: fewer than 2^31 tiles);
+    // the digit's own primes keep d itself
+    auto skip = [&](int id) {
+        const int y = id >> log_gr, l = y % LK, jd = (y / LK) % a.dnum;
+        const int i0 = jd * a.alpha;
+        return l >= i0 && l < min(a.L, i0 + a.alpha);
+    };
+    auto next = [&](int id) {
+        while (id < n_tiles && skip(id)) id += gridDim.x;
+        return id;
+    };
+    auto tile = [&](int id) { return ext + (int64_t)id * kNttTile; };  // N = 2^log_gr * kNttTile
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int id = next(blockIdx.x);
+    if (t == 0 && id < n_tiles) bulk_load(buf0, tile(id), kNttTile * 8, &bars[0]);
+    uint32_t ph0 = 0, ph1 = 0;  // parity each buffer's barrier completes next
+    int cur = 0;
+    bool pending = false;  // a prefetch into the other buffer is in flight
+    while (id < n_tiles) {
+        uint64_t *const b = cur ? buf1 : buf0, *const other = cur ? buf0 : buf1;
+        const int nid = next(id + gridDim.x);
+        if (t == 0 && nid < n_tiles) {  // `other` was released by the barrier ending the last tile
+            fence_proxy_async_smem();
+            bulk_load(other, tile(nid), kNttTile * 8, &bars[cur ^ 1]);
+        }
+        pending = nid < n_tiles;
+        if (!__syncthreads_and(mbar_wait(&bars[cur], cur ? ph1 : ph0, kWaitPolls, a.err))) break;
+        if (cur) ph1 ^= 1; else ph0 ^= 1;
+        const int y = id >> log_gr;
+        const int l = y % LK, row = (id & ((1 << log_gr) - 1)) * TR + rr;
+        const uint64_t q = a.mc[l].q;
+        const TwPair *tw = (const TwPair *)(a.tw + (int64_t)l * 4 * N);
+        uint64_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = b[rr * M + Pass<LR>::first(j, e)];
+        fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
+        store8(tile(id) + rr * M + 8 * j, v);
+        __syncthreads();  // b fully read before it is refilled
+        id = nid;
+        cur ^= 1;
+        pending = false;
+    }
+    // after a timed-out wait: let an issued prefetch land before the CTA exits
+    if (t == 0 && pending) mbar_wait(&bars[cur ^ 1], cur ? ph0 : ph1, kWaitPolls, a.err);
+}
+
+constexpr size_t kRowsTmaSmem = (2 * kNttTile + kRowTileWords + 2) * sizeof(uint64_t);
+
+// persistent grid of the TMA row pass: its resident CTAs on the whole GPU
+// (set by ks_prepare, outside any stream capture)
+template <int LR>
+int &rows_fwd_blocks() {
+    static int blocks = 152 * 4;
+    return blocks;
+}
+
+template <int LR>
+cudaError_t rows_fwd_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_ks_rows_fwd_tma<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kRowsTmaSmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ks_rows_fwd_tma<LR>, kNttThreads,
+                                                           kRowsTmaSmem)))
+        return e;
+    rows_fwd_blocks<LR>() = std::max(1, per_sm) * std::max(1, sms);
+    return cudaSuccess;
 }
 
 // Inner product with the key: acc[item][c][l] = sum_j e_j * key[j][c][l]
@@ -383,8 +475,17 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     else
         k_ks_modup_cols<LC, 4><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
     prof_end(c, r, st);
-    r = prof_begin(c, "k_ks_rows_fwd", st);
-    k_ks_rows_fwd<LR><<<dim3(gr, n * c.dnum * LK), kNttThreads, 0, st>>>(a, ext);
+    if (c.rows_tma) {
+        r = prof_begin(c, "k_ks_rows_fwd_tma", st);
+        const int tiles = (int)(n * c.dnum * LK * gr);  // n is capped so this stays below 2^31
+        int log_gr = 0;
+        while ((1 << log_gr) < gr) ++log_gr;
+        const int grid = std::min(tiles, rows_fwd_blocks<LR>());
+        k_ks_rows_fwd_tma<LR><<<grid, kNttThreads, kRowsTmaSmem, st>>>(a, ext, tiles, log_gr);
+    } else {
+        r = prof_begin(c, "k_ks_rows_fwd", st);
+        k_ks_rows_fwd<LR><<<dim3(gr, n * c.dnum * LK), kNttThreads, 0, st>>>(a, ext);
+    }
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_mac", st);
     {
@@ -441,6 +542,18 @@ static cudaError_t ks_dispatch(const Ctx &c, const KsArgs &a, const KsSrc &s, co
 
 int ks_split_variants(const Ctx &c) { return ks_fused_supported(c) ? 2 : 1; }
 
+cudaError_t ks_prepare(const Ctx &c) {
+    if (!ks_fused_supported(c)) return cudaSuccess;
+    switch (c.log2n) {  // the row-pass sizes of both NTT splits
+        case 15: { cudaError_t e = rows_fwd_prepare<8>(); return e ? e : rows_fwd_prepare<7>(); }
+        case 14: { cudaError_t e = rows_fwd_prepare<7>(); return e ? e : rows_fwd_prepare<8>(); }
+        case 13: { cudaError_t e = rows_fwd_prepare<7>(); return e ? e : rows_fwd_prepare<6>(); }
+        case 12: { cudaError_t e = rows_fwd_prepare<6>(); return e ? e : rows_fwd_prepare<7>(); }
+        case 11: { cudaError_t e = rows_fwd_prepare<6>(); return e ? e : rows_fwd_prepare<5>(); }
+        default: return cudaSuccess;
+    }
+}
+
 static KsArgs ks_args(const Ctx &c) {
     const hespmv_ctx *h = c.c;
     KsArgs a;
@@ -453,6 +566,7 @@ static KsArgs ks_args(const Ctx &c) {
     a.pinv = h->d.md_pinv;
     a.pmont = h->d.p_mont;
     a.pmont2 = h->d.p_mont2;
+    a.err = h->d.err;
     a.log2n = c.log2n;
     a.L = c.L;
     a.K = c.K;

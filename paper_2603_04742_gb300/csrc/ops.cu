@@ -1,6 +1,7 @@
 // Elementwise ciphertext kernels, the key-switching stages, samplers and the
 // encode / decrypt helpers.  Grid-stride loops over flat word indices; every
 // access is coalesced along the coefficient index.
+#include "async_copy.cuh"
 #include "kernels.h"
 
 namespace hespmv {
@@ -607,6 +608,25 @@ cudaError_t op_crt_to_t(const Ctx &c, const uint64_t *x, uint64_t *m, cudaStream
 
 cudaError_t op_gather_slots(const Ctx &c, const uint64_t *E, uint64_t *slots, cudaStream_t st) {
     LAUNCH(k_gather_slots, (int64_t)c.N, st, E, slots, c.N, c.c->d.slot_idx);
+}
+
+// Self-test of the bounded waits: a barrier that expects 16 bytes no copy
+// ever delivers; every thread's wait runs out after a few polls and the
+// device error word is set.  Nothing faults and nothing is left in flight.
+__global__ void k_wait_probe(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;" ::"r"(smem_u32(&bar)) : "memory");
+    }
+    __syncthreads();
+    mbar_wait(&bar, 0, 1024, err);
+}
+
+cudaError_t op_wait_probe(const Ctx &c, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(c.c->d.err);
+    return cudaGetLastError();
 }
 
 }  // namespace hespmv

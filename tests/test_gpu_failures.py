@@ -68,3 +68,19 @@ def test_bad_arguments_are_refused_before_any_launch():
     ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=3)
     cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=4)
     assert list(ctx.decrypt(m, ctx.spmv(m, ca, cx))) == list(A.matvec(x))
+
+
+def test_bounded_device_wait_reports_timeout():
+    """A device-side wait that cannot complete gives up, the host reads
+    HESPMV_E_TIMEOUT, and the context keeps working."""
+    from paper_2603_04742_gb300.api import Context
+    logn, L, K, dnum, t = synth.RING["c1"]
+    ctx = Context(logn, L, K, dnum, t)
+    ctx.keygen(1)
+    rc, code = ctx.selftest_wait_timeout()
+    assert rc == B.HESPMV_E_TIMEOUT and code == 1
+    ctx.device_status()                       # cleared: no error now
+    A, x = synth.workload("c1")
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    y = ctx.spmv(m, ctx.encrypt(m, B.HESPMV_MATRIX, seed=1), ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=2))
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x))

@@ -423,3 +423,45 @@ def test_outputs_fully_written_over_poisoned_buffers():
     ctx.he_mult(ca.ptr, cx.ptr, out.data_ptr())
     got = host(out)
     assert np.all(got[:CT] != np.iinfo(np.uint64).max) and np.all(got[CT:] == np.iinfo(np.uint64).max)
+
+
+@pytest.mark.parametrize("split,rows_tma", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_fused_keyswitch_both_splits_n2048(split, rows_tma):
+    """N = 2^11, the smallest fused ring, under both NTT splits (2^5 x 2^6 and
+    2^6 x 2^5): HE-Mult and a rotation bit-exact with the oracle."""
+    N = 1 << 11
+    t = plain_modulus(N, 1 << 18)
+    ctx, orc = make_pair(11, 4, 2, 2, t, seed=5, steps=[1, 9])
+    ctx.set_tuning(0, 0, split, rows_tma)
+    A, oc, vals = _random_slot_ciphertexts(ctx, orc, 2, 13)
+    L, CT = 4, 2 * 4 * N
+    out = torch.zeros(CT, dtype=torch.int64, device="cuda")
+    ctx.he_mult(A.ptr, A.ptr + CT * 8, out.data_ptr())
+    assert np.array_equal(host(out).reshape(2, L, N), orc.mult(oc[0], oc[1]))
+    ctx.he_rotate(A.ptr, 9, out.data_ptr())
+    assert np.array_equal(host(out).reshape(2, L, N), orc.rotate(oc[0], 9))
+    ctx.device_status()
+
+
+def test_row_pass_forms_identical_n32768():
+    """At the stencil ring the TMA-fed row pass (both NTT splits) gives the
+    same HE-Mult as the oracle-checked default form."""
+    from paper_2603_04742_gb300.api import Context
+    logn, L, K, dnum, t = synth.RING["c3"]
+    A, xf = synth.workload("c3")
+    A.vals = synth.quantize(A.vals)
+    x = synth.quantize(xf)
+    ctx = Context(logn, L, K, dnum, t)
+    ctx.keygen(1, [])
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    outs = []
+    for split, tma in ((0, 0), (0, 1), (1, 1)):
+        ctx.set_tuning(0, 0, split, tma)
+        y = ctx.spmv(m, ca, cx)
+        torch.cuda.synchronize()
+        outs.append(y.download())
+    ctx.device_status()
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
