@@ -455,6 +455,9 @@ struct SpmvPrep {
     RotPlan *rp = nullptr;
     size_t need_bytes = 0;
     bool pt_matrix = false;  // matrix operand in the clear: HE-CMult, no key switch
+    // host operands of a single instance: each HE-Mult group's chunks are
+    // uploaded on the context's copy stream and waited for by that group only
+    const uint64_t *hA = nullptr, *hX = nullptr;
 };
 
 // Per-matrix device state an evaluation reads: mask plaintexts (cached per
@@ -480,8 +483,11 @@ int prepare_matrix(hespmv_ctx *ctx, const hespmv_cssc *cm, cudaStream_t st) {
 }
 
 // batch sizes and workspace bytes of an evaluation over the given chunk counts
-void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &pp) {
-    const size_t tune_G = c.c->tune_G, tune_GR = c.c->tune_GR;
+void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &pp,
+                size_t max_G = 0) {
+    size_t tune_G = c.c->tune_G;
+    const size_t tune_GR = c.c->tune_GR;
+    if (max_G) tune_G = std::min(tune_G ? tune_G : 32, max_G);
     const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
     pp.total_chunks = total_chunks;
     pp.rot_chunks = rot_chunks;
@@ -496,7 +502,7 @@ void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &
 // Everything an evaluation needs besides kernel launches: per-matrix state,
 // the (cached) rotation schedule, the workspace size.
 int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, SpmvPrep &pp,
-                 cudaStream_t st) {
+                 cudaStream_t st, size_t max_G = 0) {
     const Ctx c = view(ctx);
     size_t total = 0, rot = 0;
     for (size_t i = 0; i < n_inst; ++i) {
@@ -505,7 +511,7 @@ int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, S
         total += ms[i]->plan.chunks.size();
         for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
     }
-    spmv_sizes(c, total, rot, pp);
+    spmv_sizes(c, total, rot, pp, max_G);
     pp.rp = nullptr;
     if (rot) {
         pp.rp = rotation_plan(ctx, n_inst, ms, (int)pp.GR);
@@ -541,9 +547,23 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         all.reserve(pp.total_chunks);
         for (size_t i = 0; i < n_inst; ++i)
             for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
-        for (size_t g0 = 0; g0 < all.size(); g0 += G) {
+        if (pp.hA) {  // uploads on the side stream, one event per group
+            cudaStream_t cs = ctx->copy_stream;
+            CK(cudaEventRecord(ctx->copy_events[0], st));  // fork
+            CK(cudaStreamWaitEvent(cs, ctx->copy_events[0], 0));
+            for (size_t g0 = 0, gi = 1; g0 < all.size(); g0 += G, ++gi) {
+                const size_t gn = std::min(G, all.size() - g0);
+                CK(cudaMemcpyAsync((uint64_t *)A[0] + g0 * CT, pp.hA + g0 * CT, gn * CT * 8,
+                                   cudaMemcpyHostToDevice, cs));
+                CK(cudaMemcpyAsync((uint64_t *)X[0] + g0 * CT, pp.hX + g0 * CT, gn * CT * 8,
+                                   cudaMemcpyHostToDevice, cs));
+                CK(cudaEventRecord(ctx->copy_events[gi], cs));
+            }
+        }
+        for (size_t g0 = 0, gi = 1; g0 < all.size(); g0 += G, ++gi) {
             const size_t gn = std::min(G, all.size() - g0);
             const size_t i = all[g0].first, k = all[g0].second;
+            if (pp.hA) CK(cudaStreamWaitEvent(st, ctx->copy_events[gi], 0));  // this group's chunks
             const bool bgv = ctx->h.scheme != HESPMV_SCHEME_BFV;  // BGV and CKKS tensors are limb-wise
             if (bgv && ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
                 // one matrix's consecutive chunks: tensor product fused into the key switch
@@ -623,11 +643,23 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
 // graphs are disabled.
 int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
-              cudaStream_t st, bool pt_matrix = false) {
+              cudaStream_t st, bool pt_matrix = false, const uint64_t *hA = nullptr,
+              const uint64_t *hX = nullptr, size_t max_G = 0) {
     SpmvPrep pp;
-    int rc = spmv_prepare(ctx, n_inst, ms, pp, st);
+    int rc = spmv_prepare(ctx, n_inst, ms, pp, st, max_G);
     if (rc) return rc;
     pp.pt_matrix = pt_matrix;
+    pp.hA = hA;
+    pp.hX = hX;
+    if (hA) {  // side stream and one event per HE-Mult group (plus the fork)
+        if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        const size_t groups = (pp.total_chunks + pp.G - 1) / pp.G + 1;
+        while (ctx->copy_events.size() < groups) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ctx->copy_events.push_back(e);
+        }
+    }
     uint64_t *ws = workspace(ctx, pp.need_bytes);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     const bool profiling = ctx->prof && ctx->prof->on;
@@ -635,6 +667,9 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     std::vector<uint64_t> key;
     key.push_back((uint64_t)(uintptr_t)ws);
     key.push_back(pt_matrix ? 1 : 0);
+    key.push_back((uint64_t)(uintptr_t)hA);
+    key.push_back((uint64_t)(uintptr_t)hX);
+    key.push_back(pp.G);
     for (size_t i = 0; i < n_inst; ++i) {
         key.push_back(ms[i]->uid);
         key.push_back((uint64_t)(uintptr_t)A[i]);
@@ -753,6 +788,8 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     }
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
     delete ctx->prof;
     delete ctx;
 }
@@ -1615,17 +1652,13 @@ int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_ho
     uint64_t *io = (uint64_t *)ctx->io;
     if (!io) FAIL(HESPMV_E_NOMEM, "staging allocation failed");
     uint64_t *dA = io, *dX = io + nc * ct_bytes / 8, *dY = dX + nc * ct_bytes / 8;
-    int rc = HESPMV_OK;
-    if (cudaMemcpyAsync(dA, A_host, nc * ct_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dX, X_host, nc * ct_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        rc = HESPMV_E_CUDA;
-        ctx->err = "upload failed";
-    }
-    if (!rc) {
-        const uint64_t *pa = dA, *px = dX;
-        uint64_t *py = dY;
-        rc = spmv_core(ctx, 1, &m, &pa, &px, &py, st);
-    }
+    // uploads overlap the HE-Mult: four groups of chunks, each key switch
+    // waiting only for its own chunks (on the stencil ring four beat two,
+    // three or seven: smaller groups cost key-switch efficiency)
+    const uint64_t *pa = dA, *px = dX;
+    uint64_t *py = dY;
+    int rc = spmv_core(ctx, 1, &m, &pa, &px, &py, st, false, A_host, X_host,
+                       std::max<size_t>(1, (nc + 3) / 4));
     if (!rc && (cudaMemcpyAsync(y_host, dY, np * ct_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess)) {
         rc = HESPMV_E_CUDA;

@@ -239,9 +239,12 @@ struct hespmv_ctx {
     size_t tune_GR = 0;  // totalSum round width: ciphertexts per rotation round
     int ks_split = 0;    // fused key switch: NTT split variant (column/row pass sizes)
     int rows_tma = 0;    // fused key switch: persistent TMA-fed forward row pass
-    // staging for evaluations from host buffers
+    // staging for evaluations from host buffers, and the side stream and
+    // events that overlap their uploads with the HE-Mult groups
     void *io = nullptr;
     size_t io_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
     // CKKS encoder tables and CRT constants (host, made on first use)
     hespmv::CkksCodec *codec = nullptr;
     hespmv::CrtReal *crt = nullptr;
