@@ -128,7 +128,7 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
 }
 
 // ModUp of digit jd to every prime outside it, fused with the forward column
-// pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, [0, 4q))
+// pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, unreduced, < 32q)
 template <int LC, int AMAX>
 __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
                                                                uint64_t *ext) {
@@ -182,7 +182,7 @@ __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_col
 }
 
 // Forward row pass, in place, of every raised limb: ext[item][jd][l] for the
-// primes l outside digit jd (output unreduced, < 32q).
+// primes l outside digit jd (output unreduced, < 64q).
 template <int LR>
 __global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t *ext) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
@@ -292,7 +292,7 @@ cudaError_t rows_fwd_prepare() {
 }
 
 // Inner product with the key: acc[item][c][l] = sum_j e_j * key[j][c][l]
-// with e_j = ext[item][j][l] (< 32q) or, on digit j's own primes, d itself.
+// with e_j = ext[item][j][l] (< 64q) or, on digit j's own primes, d itself.
 // Keys are in Montgomery form, so the 128-bit sum needs one reduction.
 // On the Q primes the addend y_c of the output, times P, joins the sum
 // (P * 2^64 mod q as its factor): (acc + P y - delta) * P^-1 = (acc - delta)
@@ -450,8 +450,8 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const u
     fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
     const uint64_t w = a.pinv[2 * i], ws = a.pinv[2 * i + 1];
 #pragma unroll
-    for (int e = 0; e < 8; ++e)  // delta < 32q unreduced: (acc + 32q - delta) * P^-1, fully reduced
-        v[e] = mul_shoup(xa[e] + 32 * q - v[e], w, ws, q);
+    for (int e = 0; e < 8; ++e)  // delta < 64q unreduced: (acc + 64q - delta) * P^-1, fully reduced
+        v[e] = mul_shoup(xa[e] + 64 * q - v[e], w, ws, q);
     store8(out + ((int64_t)ic * L + i) * N + rofs + 8 * j, v);
 }
 

@@ -45,6 +45,18 @@ __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint6
     return a * w - qh * q;
 }
 
+// Same, with the quotient estimated from three of the four 32 x 32-bit partial
+// products of a * ws (the low-by-low product and the low halves of the cross
+// products are dropped): the estimate is low by at most three, so the result
+// is in [0, 4q).  For q < 2^50 and any a < 2^64.
+__device__ __forceinline__ uint64_t mul_shoup_lazy4(uint64_t a, uint64_t w, uint64_t ws,
+                                                    uint64_t q) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
+    const uint64_t qh = (uint64_t)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - qh * q;
+}
+
 // Barrett reduction of a 128-bit value x = hi:lo < 2^(2k), q of k bits:
 // q1 = x >> (k-1), q3 = (q1 * mu) >> (k+1), r = x - q3 q in [0, 3q).
 __device__ __forceinline__ uint64_t barrett_reduce(uint64_t hi, uint64_t lo, uint64_t q,

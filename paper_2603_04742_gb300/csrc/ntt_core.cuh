@@ -16,9 +16,10 @@
 // twb = 1 for the column pass and 2^n1 + row for the row pass (stage offset
 // n1), which reproduces the index m + i of the textbook loop.
 //
-// Lazy ranges: forward butterflies let values grow by 2q per stage (no
-// reduction until the consumer's Shoup or Montgomery product); inverse
-// (Gentleman-Sande) butterflies keep [0, 2q).  Twiddles are (w, Shoup) pairs,
+// Lazy ranges: forward butterflies let values grow by 4q per stage (no
+// reduction until the consumer's Shoup or Montgomery product; their products
+// use a three-partial-product quotient estimate, result in [0, 4q)); inverse
+// (Gentleman-Sande) butterflies keep [0, 2q) with the exact Shoup quotient.  Twiddles are (w, Shoup) pairs,
 // one 16-byte load per butterfly.
 #pragma once
 #include "modarith.cuh"
@@ -28,13 +29,13 @@ namespace hespmv {
 constexpr int kNttThreads = 256;
 constexpr int kNttTile = 2048;  // words per CTA
 
-// (x, y) -> (x + w y, x - w y + 2q) without reducing x: w y is taken in
-// [0, 2q), so each stage raises the bound by at most 2q.  Inputs below 2q
-// stay below (2 + 2 log2 N) q <= 32q < 2^55 after a whole transform.
+// (x, y) -> (x + w y, x - w y + 4q) without reducing x: w y is taken in
+// [0, 4q), so each stage raises the bound by at most 4q.  Inputs below 4q
+// stay below (4 + 4 log2 N) q <= 64q < 2^56 after a whole transform.
 __device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
-    const uint64_t t = mul_shoup_lazy(y, w, ws, q);
-    y = x + q2 - t;
+    const uint64_t t = mul_shoup_lazy4(y, w, ws, q);
+    y = x + 2 * q2 - t;
     x = x + t;
 }
 
