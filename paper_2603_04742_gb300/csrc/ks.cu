@@ -128,7 +128,8 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
 }
 
 // ModUp of digit jd to every prime outside it, fused with the forward column
-// pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, unreduced, < 32q)
+// pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, unreduced:
+// conversion sums below 4 alpha q <= 16q, then 4q per stage)
 template <int LC, int AMAX>
 __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
                                                                uint64_t *ext) {
@@ -157,7 +158,7 @@ __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_col
     uint64_t *dst0 = ext + ((int64_t)item * a.dnum + jd) * LK * N + cofs;
     for (int l = 0; l < LK; ++l) {
         if (l >= i0 && l < i1) continue;
-        const uint64_t q = a.mc[l].q, q2 = 2 * q;
+        const uint64_t q = a.mc[l].q;
         const TwPair *tw = (const TwPair *)(a.tw + (int64_t)l * 4 * N);
         uint64_t v[8];
 #pragma unroll
@@ -168,10 +169,7 @@ __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_col
                 const uint64_t *cst = a.modup_mod + (((int64_t)jd * a.alpha + s) * LK + l) * 2;
                 const uint64_t w = cst[0], ws = cst[1];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    uint64_t x = v[e] + mul_shoup_lazy(zs[s][e], w, ws, q);
-                    v[e] = x >= q2 ? x - q2 : x;
-                }
+                for (int e = 0; e < 8; ++e) v[e] += mul_shoup_lazy4(zs[s][e], w, ws, q);  // < 4q each
             }
         }
         fwd_body<LC>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
@@ -182,7 +180,7 @@ __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_col
 }
 
 // Forward row pass, in place, of every raised limb: ext[item][jd][l] for the
-// primes l outside digit jd (output unreduced, < 64q).
+// primes l outside digit jd (output unreduced, < 80q).
 template <int LR>
 __global__ __launch_bounds__(kNttThreads) void k_ks_rows_fwd(KsArgs a, uint64_t *ext) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
@@ -292,7 +290,7 @@ cudaError_t rows_fwd_prepare() {
 }
 
 // Inner product with the key: acc[item][c][l] = sum_j e_j * key[j][c][l]
-// with e_j = ext[item][j][l] (< 64q) or, on digit j's own primes, d itself.
+// with e_j = ext[item][j][l] (< 80q) or, on digit j's own primes, d itself.
 // Keys are in Montgomery form, so the 128-bit sum needs one reduction.
 // On the Q primes the addend y_c of the output, times P, joins the sum
 // (P * 2^64 mod q as its factor): (acc + P y - delta) * P^-1 = (acc - delta)
@@ -405,7 +403,7 @@ __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_c
         }
     }
     for (int i = 0; i < L; ++i) {
-        const uint64_t q = a.mc[i].q, q2 = 2 * q;
+        const uint64_t q = a.mc[i].q;
         const TwPair *tw = (const TwPair *)(a.tw + (int64_t)i * 4 * N);
         uint64_t v[8];
 #pragma unroll
@@ -416,10 +414,7 @@ __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_c
                 const uint64_t w = a.phat_t[((int64_t)s * L + i) * 2];
                 const uint64_t ws = a.phat_t[((int64_t)s * L + i) * 2 + 1];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    uint64_t x = v[e] + mul_shoup_lazy(ys[s][e], w, ws, q);
-                    v[e] = x >= q2 ? x - q2 : x;
-                }
+                for (int e = 0; e < 8; ++e) v[e] += mul_shoup_lazy4(ys[s][e], w, ws, q);  // < 4q each
             }
         }
         fwd_body<LC>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
@@ -450,8 +445,8 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_rows_final(KsArgs a, const u
     fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
     const uint64_t w = a.pinv[2 * i], ws = a.pinv[2 * i + 1];
 #pragma unroll
-    for (int e = 0; e < 8; ++e)  // delta < 64q unreduced: (acc + 64q - delta) * P^-1, fully reduced
-        v[e] = mul_shoup(xa[e] + 64 * q - v[e], w, ws, q);
+    for (int e = 0; e < 8; ++e)  // delta < 80q unreduced: (acc + 128q - delta) * P^-1, fully reduced
+        v[e] = mul_shoup(xa[e] + 128 * q - v[e], w, ws, q);
     store8(out + ((int64_t)ic * L + i) * N + rofs + 8 * j, v);
 }
 

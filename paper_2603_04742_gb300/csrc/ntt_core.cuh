@@ -30,8 +30,9 @@ constexpr int kNttThreads = 256;
 constexpr int kNttTile = 2048;  // words per CTA
 
 // (x, y) -> (x + w y, x - w y + 4q) without reducing x: w y is taken in
-// [0, 4q), so each stage raises the bound by at most 4q.  Inputs below 4q
-// stay below (4 + 4 log2 N) q <= 64q < 2^56 after a whole transform.
+// [0, 4q), so each stage raises the bound by at most 4q.  Inputs below 16q
+// (base-conversion sums of up to four lazy products) stay below
+// (16 + 4 log2 N) q <= 76q < 2^57 after a whole transform.
 __device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
     const uint64_t t = mul_shoup_lazy4(y, w, ws, q);
