@@ -17,9 +17,9 @@
 // n1), which reproduces the index m + i of the textbook loop.
 //
 // Lazy ranges: forward butterflies let values grow by 4q per stage (no
-// reduction until the consumer's Shoup or Montgomery product; their products
-// use a three-partial-product quotient estimate, result in [0, 4q)); inverse
-// (Gentleman-Sande) butterflies keep [0, 2q) with the exact Shoup quotient.  Twiddles are (w, Shoup) pairs,
+// reduction until the consumer's Shoup or Montgomery product); inverse
+// (Gentleman-Sande) butterflies keep [0, 4q).  Both take their products with
+// a three-partial-product Shoup quotient estimate, result in [0, 4q).  Twiddles are (w, Shoup) pairs,
 // one 16-byte load per butterfly.
 #pragma once
 #include "modarith.cuh"
@@ -45,12 +45,13 @@ __device__ __forceinline__ uint64_t reduce_full(uint64_t x, uint64_t q, uint64_t
     return mul_shoup(x, 1, one_s, q);
 }
 
-// x, y in [0, 2q) -> (x + y, (x - y) w) in [0, 2q)
+// x, y in [0, 4q) -> (x + y, (x - y) w) in [0, 4q)  (q2 = 2q)
 __device__ __forceinline__ void gs_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
+    const uint64_t q4 = 2 * q2;
     uint64_t u = x + y;
-    u = u >= q2 ? u - q2 : u;
-    uint64_t v = mul_shoup_lazy(x + q2 - y, w, ws, q);
+    u = u >= q4 ? u - q4 : u;
+    const uint64_t v = mul_shoup_lazy4(x + q4 - y, w, ws, q);
     x = u;
     y = v;
 }
@@ -142,7 +143,7 @@ __device__ __forceinline__ void inv_round_last(uint64_t (&v)[8], int j, uint32_t
         if ((e & ((1 << NS) - 1)) & dist) continue;
         const uint64_t x = v[e], y = v[e + dist];
         v[e] = mul_shoup(x + y, c0, c0s, q);
-        v[e + dist] = mul_shoup(x + q2 - y, c1, c1s, q);
+        v[e + dist] = mul_shoup(x + 2 * q2 - y, c1, c1s, q);
     }
 }
 
@@ -214,9 +215,9 @@ __device__ __forceinline__ void fwd_body(uint64_t (&v)[8], int j, uint32_t twb, 
 }
 
 // Inverse sub-transform of one tile.  On entry v[e] holds the element at
-// Pass::last(j, e) (in [0, 2q)); on return Pass::first(j, e).  With FOLD the
+// Pass::last(j, e) (in [0, 4q)); on return Pass::first(j, e).  With FOLD the
 // final stage scales by (c0, c1) and reduces fully (only for the last pass of
-// a transform, twb == 1); otherwise outputs are in [0, 2q).
+// a transform, twb == 1); otherwise outputs are in [0, 4q).
 template <int LOGM, bool FOLD, class SIdx>
 __device__ __forceinline__ void inv_body(uint64_t (&v)[8], int j, uint32_t twb, uint64_t *sm,
                                          SIdx si, const TwPair *__restrict__ itw, uint64_t q,
