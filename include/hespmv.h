@@ -305,6 +305,39 @@ int hespmv_spmv_ptmatrix(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctb
 int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_host,
                      const uint64_t *X_host, uint64_t *y_host, void *stream);
 
+/* Packed ciphertexts (the wire form of hespmv_spmv_host_packed).  RNS
+ * residues are uniform below primes of at most W = max_i bitlen(q_i) bits
+ * (i < L), so a residue takes W bits instead of 64: each limb of a
+ * ciphertext [2][L][N] becomes ceil(N W / 64) little-endian u64 words, with
+ * residue k in bits [k W, k W + W) of the limb's bit string (bit b of the
+ * string is bit b mod 64 of word b / 64; the unused high bits of a limb's
+ * last word are zero).  *words receives the words of one packed ciphertext
+ * and *bits receives W (either may be NULL).  Host only. */
+int hespmv_ct_packed_words(const hespmv_ctx *ctx, size_t *words, int32_t *bits);
+/* n_ct ciphertexts [n_ct][2][L][N] -> packed (n_ct * words u64, caller-owned).
+ * HESPMV_E_INVALID if a residue is not below its prime.  Host only. */
+int hespmv_ct_pack(const hespmv_ctx *ctx, const uint64_t *cts, size_t n_ct, uint64_t *packed);
+/* The inverse; HESPMV_E_INVALID if a residue is not below its prime or a
+ * padding bit is set.  Host only. */
+int hespmv_ct_unpack(const hespmv_ctx *ctx, const uint64_t *packed, size_t n_ct, uint64_t *cts);
+/* hespmv_spmv_host on packed buffers: A_packed and X_packed hold n_chunks
+ * packed ciphertexts each and are copied to the device in groups (the
+ * copies of later groups overlapping the HE-Mult of earlier ones; each group
+ * is unpacked on the device just before its HE-Mult); y_packed receives the n_parts results, packed on the
+ * device.  A residue that is not below its prime is evaluated reduced modulo
+ * the prime and the call returns HESPMV_E_INVALID.  Synchronises `stream`.
+ * Page-locked host buffers (cudaHostAlloc) make the copies asynchronous. */
+int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
+                            const uint64_t *X_packed, uint64_t *y_packed, void *stream);
+/* Upload groups of the host-buffer evaluations (1..64; 0 restores the
+ * default, 7).  The chunks are uploaded in that many groups; the HE-Mult of a
+ * group starts when its own upload has landed, and consecutive groups run on
+ * two streams so that one group's kernels fill the tails of the other's.
+ * More groups start the work earlier but give each fused key switch fewer
+ * ciphertexts.  Results do not depend on it.  Host only. */
+int hespmv_set_upload_groups(hespmv_ctx *ctx, int32_t groups);
+int hespmv_get_upload_groups(const hespmv_ctx *ctx, int32_t *groups);
+
 /* Many independent SpMVs in one batched evaluation (same context and keys):
  * every stage runs once over the chunks of all n instances.  y[i] as in
  * hespmv_spmv. */

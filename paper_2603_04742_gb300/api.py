@@ -242,6 +242,43 @@ class Context:
         self.check(self.lib.hespmv_spmv_host(self.h, m.h, _u64p(A_host), _u64p(X_host),
                                              _u64p(y_host), _stream_handle(stream)))
 
+    def set_upload_groups(self, groups):
+        """Upload groups of spmv_host / spmv_host_packed (0: the default)."""
+        self.check(self.lib.hespmv_set_upload_groups(self.h, groups))
+
+    def get_upload_groups(self):
+        g = c_int32()
+        self.check(self.lib.hespmv_get_upload_groups(self.h, byref(g)))
+        return g.value
+
+    # ---- packed ciphertexts (W bits per residue) ----
+    def ct_packed_words(self):
+        """(u64 words of one packed ciphertext, bits per residue W)."""
+        w, b = c_size_t(0), c_int32(0)
+        self.check(self.lib.hespmv_ct_packed_words(self.h, byref(w), byref(b)))
+        return w.value, b.value
+
+    def ct_pack(self, cts):
+        cts = np.ascontiguousarray(cts, dtype=np.uint64)
+        n = cts.size // (2 * self.L * self.N)
+        assert cts.size == n * 2 * self.L * self.N
+        out = np.zeros((n, self.ct_packed_words()[0]), dtype=np.uint64)
+        self.check(self.lib.hespmv_ct_pack(self.h, _u64p(cts), n, _u64p(out)))
+        return out
+
+    def ct_unpack(self, packed):
+        packed = np.ascontiguousarray(packed, dtype=np.uint64)
+        w = self.ct_packed_words()[0]
+        n = packed.size // w
+        assert packed.size == n * w
+        out = np.zeros((n, 2, self.L, self.N), dtype=np.uint64)
+        self.check(self.lib.hespmv_ct_unpack(self.h, _u64p(packed), n, _u64p(out)))
+        return out
+
+    def spmv_host_packed(self, m, A_packed, X_packed, y_packed, stream=None):
+        self.check(self.lib.hespmv_spmv_host_packed(self.h, m.h, _u64p(A_packed), _u64p(X_packed),
+                                                    _u64p(y_packed), _stream_handle(stream)))
+
     def decrypt(self, m, y):
         out = np.zeros(m.rows, dtype=np.int64)
         self.check(self.lib.hespmv_decrypt(self.h, m.h, y.h, _i64p(out)))

@@ -106,6 +106,12 @@ SIGNATURES = {
     "hespmv_encrypt": (c_int, [c_void_p, c_void_p, c_int32, i64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_spmv": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p), c_void_p]),
     "hespmv_spmv_host": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),
+    "hespmv_ct_packed_words": (c_int, [c_void_p, szp, i32p]),
+    "hespmv_ct_pack": (c_int, [c_void_p, u64p, c_size_t, u64p]),
+    "hespmv_ct_unpack": (c_int, [c_void_p, u64p, c_size_t, u64p]),
+    "hespmv_spmv_host_packed": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),
+    "hespmv_set_upload_groups": (c_int, [c_void_p, c_int32]),
+    "hespmv_get_upload_groups": (c_int, [c_void_p, i32p]),
     "hespmv_encode_matrix_plain": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
     "hespmv_spmv_ptmatrix": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_void_p),
                                      c_void_p]),

@@ -450,6 +450,33 @@ RotPlan *rotation_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const 
     return P;
 }
 
+// packed ciphertexts: words of one limb and of one ciphertext
+size_t packed_limb_words(const HostTables &h) { return ((size_t)h.N * h.pack_bits + 63) / 64; }
+size_t packed_ct_words(const HostTables &h) { return 2 * (size_t)h.L * packed_limb_words(h); }
+
+// Default upload groups of a host evaluation.  On the stencil workload
+// (27 chunks, 177 MB packed) 4 to 7 groups are within 2 % of each other, 7
+// the fastest; fewer groups delay the first HE-Mult, more make each fused key
+// switch too small.
+constexpr size_t kUploadGroups = 7;
+
+// upload (and HE-Mult) group sizes of a host evaluation of nc chunks
+std::vector<size_t> upload_group_sizes(const hespmv_ctx *ctx, size_t nc) {
+    const size_t groups = std::min(std::max<size_t>(nc, 1),
+                                   ctx->upload_groups > 0 ? (size_t)ctx->upload_groups : kUploadGroups);
+    std::vector<size_t> g;
+    for (size_t k = 0; k < groups; ++k) g.push_back((nc * (k + 1)) / groups - (nc * k) / groups);
+    if (g.empty() || g[0] == 0) g.assign(1, std::max<size_t>(nc, 1));
+    return g;
+}
+
+// status of a device error word value
+int status_of_code(hespmv_ctx *ctx, int v) {
+    if (v == 0) return HESPMV_OK;
+    if (v == kErrBadResidue) FAIL(HESPMV_E_INVALID, "a packed input residue was not below its prime");
+    FAIL(HESPMV_E_TIMEOUT, "a device-side wait ran out (code " + std::to_string(v) + ")");
+}
+
 struct SpmvPrep {
     size_t total_chunks = 0, rot_chunks = 0, G = 1, GR = 1;
     RotPlan *rp = nullptr;
@@ -458,7 +485,30 @@ struct SpmvPrep {
     // host operands of a single instance: each HE-Mult group's chunks are
     // uploaded on the context's copy stream and waited for by that group only
     const uint64_t *hA = nullptr, *hX = nullptr;
+    // packed host operands: staged in pkA / pkX (pk_words per ciphertext),
+    // unpacked on the copy stream group by group
+    uint64_t *pkA = nullptr, *pkX = nullptr;
+    int64_t pk_words = 0;
+    // HE-Mult groups alternate between two streams, each with its own
+    // tensor / key-switch scratch of mult_w words
+    bool dual = false;
+    size_t mult_w = 0;
+    // HE-Mult group sizes of a host evaluation (empty: groups of G)
+    std::vector<size_t> gsz;
 };
+
+// HE-Mult groups of an evaluation over `total` chunks: (first chunk, count)
+std::vector<std::pair<size_t, size_t>> mult_groups(const SpmvPrep &pp, size_t total) {
+    std::vector<std::pair<size_t, size_t>> g;
+    size_t g0 = 0;
+    for (size_t k = 0; g0 < total; ++k) {
+        // never above G: the scratch holds G ciphertexts
+        const size_t n = std::min(total - g0, k < pp.gsz.size() ? std::min(pp.gsz[k], pp.G) : pp.G);
+        g.push_back({g0, n});
+        g0 += n;
+    }
+    return g;
+}
 
 // Per-matrix device state an evaluation reads: mask plaintexts (cached per
 // chunk height), the matrix's mask table, the Galois permutations of its
@@ -496,6 +546,7 @@ void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &
     const size_t prod_w = total_chunks * CT;
     const size_t mult_w = pp.G * 3 * LN + std::max(ks_words(c, pp.G), tensor_scratch_words(c, pp.G));
     const size_t rot_w = rot_chunks ? 4 * pp.GR * CT + ks_words(c, pp.GR) : 0;
+    pp.mult_w = mult_w;
     pp.need_bytes = (prod_w + std::max(mult_w, rot_w)) * 8;
 }
 
@@ -547,28 +598,45 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         all.reserve(pp.total_chunks);
         for (size_t i = 0; i < n_inst; ++i)
             for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
+        const std::vector<std::pair<size_t, size_t>> groups = mult_groups(pp, all.size());
         if (pp.hA) {  // uploads on the side stream, one event per group
             cudaStream_t cs = ctx->copy_stream;
             CK(cudaEventRecord(ctx->copy_events[0], st));  // fork
             CK(cudaStreamWaitEvent(cs, ctx->copy_events[0], 0));
-            for (size_t g0 = 0, gi = 1; g0 < all.size(); g0 += G, ++gi) {
-                const size_t gn = std::min(G, all.size() - g0);
-                CK(cudaMemcpyAsync((uint64_t *)A[0] + g0 * CT, pp.hA + g0 * CT, gn * CT * 8,
-                                   cudaMemcpyHostToDevice, cs));
-                CK(cudaMemcpyAsync((uint64_t *)X[0] + g0 * CT, pp.hX + g0 * CT, gn * CT * 8,
-                                   cudaMemcpyHostToDevice, cs));
+            if (pp.dual) CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->copy_events[0], 0));
+            for (size_t gi = 1; gi <= groups.size(); ++gi) {
+                const size_t g0 = groups[gi - 1].first, gn = groups[gi - 1].second;
+                if (pp.pkA) {  // packed: the group's compute stream unpacks
+                    const int64_t PW = pp.pk_words;
+                    CK(cudaMemcpyAsync(pp.pkA + g0 * PW, pp.hA + g0 * PW, gn * PW * 8, cudaMemcpyHostToDevice,
+                                       cs));
+                    CK(cudaMemcpyAsync(pp.pkX + g0 * PW, pp.hX + g0 * PW, gn * PW * 8, cudaMemcpyHostToDevice,
+                                       cs));
+                } else {
+                    CK(cudaMemcpyAsync((uint64_t *)A[0] + g0 * CT, pp.hA + g0 * CT, gn * CT * 8,
+                                       cudaMemcpyHostToDevice, cs));
+                    CK(cudaMemcpyAsync((uint64_t *)X[0] + g0 * CT, pp.hX + g0 * CT, gn * CT * 8,
+                                       cudaMemcpyHostToDevice, cs));
+                }
                 CK(cudaEventRecord(ctx->copy_events[gi], cs));
             }
         }
-        for (size_t g0 = 0, gi = 1; g0 < all.size(); g0 += G, ++gi) {
-            const size_t gn = std::min(G, all.size() - g0);
+        for (size_t gi = 1; gi <= groups.size(); ++gi) {
+            const size_t g0 = groups[gi - 1].first, gn = groups[gi - 1].second;
             const size_t i = all[g0].first, k = all[g0].second;
-            if (pp.hA) CK(cudaStreamWaitEvent(st, ctx->copy_events[gi], 0));  // this group's chunks
+            // odd groups of a dual schedule: second stream, second scratch
+            const bool alt = pp.dual && (gi & 1) == 0;
+            cudaStream_t gs = alt ? ctx->aux_stream : st;
+            uint64_t *gd = dbuf + (alt ? pp.mult_w : 0), *gscr = scr + (alt ? pp.mult_w : 0);
+            if (pp.hA) CK(cudaStreamWaitEvent(gs, ctx->copy_events[gi], 0));  // this group's chunks
+            if (pp.pkA)
+                CK(op_ct_unpack(c, pp.pkA + g0 * pp.pk_words, (uint64_t *)A[0] + g0 * CT,
+                                pp.pkX + g0 * pp.pk_words, (uint64_t *)X[0] + g0 * CT, gn, gs));
             const bool bgv = ctx->h.scheme != HESPMV_SCHEME_BFV;  // BGV and CKKS tensors are limb-wise
             if (bgv && ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
                 // one matrix's consecutive chunks: tensor product fused into the key switch
                 CK(relin_tensor_fused(c, A[i] + k * CT, X[i] + k * CT, ctx->rlk, prod + g0 * CT, gn,
-                                      scr, st));
+                                      gscr, gs));
                 continue;
             }
             size_t s = 0;
@@ -576,11 +644,15 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                 const size_t ii = all[g0 + s].first, kk = all[g0 + s].second;
                 size_t run = 1;
                 while (s + run < gn && all[g0 + s + run].first == ii) ++run;
-                CK(tensor_n(c, A[ii] + kk * CT, X[ii] + kk * CT, dbuf + s * 3 * LN, run, scr, st));
+                CK(tensor_n(c, A[ii] + kk * CT, X[ii] + kk * CT, gd + s * 3 * LN, run, gscr, gs));
                 s += run;
             }
-            CK(keyswitch_n(c, dbuf + 2 * LN, 3 * LN, ctx->rlk, prod + g0 * CT, dbuf, 3 * LN, LN, 3,
-                           gn, scr, st));
+            CK(keyswitch_n(c, gd + 2 * LN, 3 * LN, ctx->rlk, prod + g0 * CT, gd, 3 * LN, LN, 3, gn, gscr,
+                           gs));
+        }
+        if (pp.dual) {  // join the second stream
+            CK(cudaEventRecord(ctx->join_event, ctx->aux_stream));
+            CK(cudaStreamWaitEvent(st, ctx->join_event, 0));
         }
     }
     // 2) totalSum: batched rotation rounds
@@ -644,17 +716,31 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
 int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
               cudaStream_t st, bool pt_matrix = false, const uint64_t *hA = nullptr,
-              const uint64_t *hX = nullptr, size_t max_G = 0) {
+              const uint64_t *hX = nullptr, const std::vector<size_t> *gsz = nullptr,
+              uint64_t *pkA = nullptr, uint64_t *pkX = nullptr) {
     SpmvPrep pp;
+    size_t max_G = 0;
+    if (gsz)
+        for (size_t v : *gsz) max_G = std::max(max_G, v);
     int rc = spmv_prepare(ctx, n_inst, ms, pp, st, max_G);
     if (rc) return rc;
+    if (gsz) pp.gsz = *gsz;
     pp.pt_matrix = pt_matrix;
     pp.hA = hA;
     pp.hX = hX;
+    pp.pkA = pkA;
+    pp.pkX = pkX;
+    pp.pk_words = (int64_t)packed_ct_words(ctx->h);
     if (hA) {  // side stream and one event per HE-Mult group (plus the fork)
         if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-        const size_t groups = (pp.total_chunks + pp.G - 1) / pp.G + 1;
-        while (ctx->copy_events.size() < groups) {
+        const size_t n_groups = mult_groups(pp, pp.total_chunks).size();
+        if (!pt_matrix && n_groups > 1) {  // two or more groups: two compute streams
+            if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+            if (!ctx->join_event) CK(cudaEventCreateWithFlags(&ctx->join_event, cudaEventDisableTiming));
+            pp.dual = true;
+            pp.need_bytes += pp.mult_w * 8;
+        }
+        while (ctx->copy_events.size() < n_groups + 1) {
             cudaEvent_t e;
             CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             ctx->copy_events.push_back(e);
@@ -669,7 +755,11 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     key.push_back(pt_matrix ? 1 : 0);
     key.push_back((uint64_t)(uintptr_t)hA);
     key.push_back((uint64_t)(uintptr_t)hX);
+    key.push_back((uint64_t)(uintptr_t)pkA);
+    key.push_back((uint64_t)(uintptr_t)pkX);
+    key.push_back(pp.dual ? 1 : 0);
     key.push_back(pp.G);
+    for (size_t v : pp.gsz) key.push_back(v);
     for (size_t i = 0; i < n_inst; ++i) {
         key.push_back(ms[i]->uid);
         key.push_back((uint64_t)(uintptr_t)A[i]);
@@ -789,6 +879,9 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->join_event) cudaEventDestroy(ctx->join_event);
+    if (ctx->err_host) cudaFreeHost(ctx->err_host);
     for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
     delete ctx->prof;
     delete ctx;
@@ -1652,19 +1745,119 @@ int hespmv_spmv_host(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_ho
     uint64_t *io = (uint64_t *)ctx->io;
     if (!io) FAIL(HESPMV_E_NOMEM, "staging allocation failed");
     uint64_t *dA = io, *dX = io + nc * ct_bytes / 8, *dY = dX + nc * ct_bytes / 8;
-    // uploads overlap the HE-Mult: four groups of chunks, each key switch
-    // waiting only for its own chunks (on the stencil ring four beat two,
-    // three or seven: smaller groups cost key-switch efficiency)
+    // uploads overlap the HE-Mult: groups of chunks (hespmv_set_upload_groups),
+    // each key switch waiting only for its own chunks, consecutive groups on
+    // two streams
     const uint64_t *pa = dA, *px = dX;
     uint64_t *py = dY;
-    int rc = spmv_core(ctx, 1, &m, &pa, &px, &py, st, false, A_host, X_host,
-                       std::max<size_t>(1, (nc + 3) / 4));
+    const std::vector<size_t> gsz = upload_group_sizes(ctx, nc);
+    int rc = spmv_core(ctx, 1, &m, &pa, &px, &py, st, false, A_host, X_host, &gsz);
     if (!rc && (cudaMemcpyAsync(y_host, dY, np * ct_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess)) {
         rc = HESPMV_E_CUDA;
         ctx->err = "download failed";
     }
     cudaStreamSynchronize(st);
+    return rc;
+}
+
+int hespmv_ct_packed_words(const hespmv_ctx *ctx, size_t *words, int32_t *bits) {
+    if (!ctx) return HESPMV_E_INVALID;
+    if (words) *words = packed_ct_words(ctx->h);
+    if (bits) *bits = ctx->h.pack_bits;
+    return HESPMV_OK;
+}
+
+int hespmv_ct_pack(const hespmv_ctx *ctx, const uint64_t *cts, size_t n_ct, uint64_t *packed) {
+    if (!ctx || (n_ct && (!cts || !packed))) return HESPMV_E_INVALID;
+    const HostTables &h = ctx->h;
+    const int W = h.pack_bits, L = h.L, N = h.N;
+    const size_t LW = packed_limb_words(h);
+    for (size_t limb = 0; limb < n_ct * 2 * L; ++limb) {
+        const uint64_t q = h.q[limb % L], *src = cts + limb * N;
+        uint64_t *dst = packed + limb * LW;
+        std::fill(dst, dst + LW, 0);
+        for (int k = 0; k < N; ++k) {
+            const uint64_t v = src[k];
+            if (v >= q) return HESPMV_E_INVALID;
+            const uint64_t bit = (uint64_t)k * W;
+            const int sh = (int)(bit & 63);
+            dst[bit >> 6] |= v << sh;
+            if (sh + W > 64) dst[(bit >> 6) + 1] |= v >> (64 - sh);
+        }
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_ct_unpack(const hespmv_ctx *ctx, const uint64_t *packed, size_t n_ct, uint64_t *cts) {
+    if (!ctx || (n_ct && (!cts || !packed))) return HESPMV_E_INVALID;
+    const HostTables &h = ctx->h;
+    const int W = h.pack_bits, L = h.L, N = h.N;
+    const size_t LW = packed_limb_words(h);
+    const uint64_t mask = W == 64 ? ~0ull : (1ull << W) - 1;
+    const uint64_t used = (uint64_t)N * W - 64 * (LW - 1);  // bits of the last word in use
+    for (size_t limb = 0; limb < n_ct * 2 * L; ++limb) {
+        const uint64_t q = h.q[limb % L], *src = packed + limb * LW;
+        uint64_t *dst = cts + limb * N;
+        if (used < 64 && (src[LW - 1] >> used)) return HESPMV_E_INVALID;
+        for (int k = 0; k < N; ++k) {
+            const uint64_t bit = (uint64_t)k * W;
+            const int sh = (int)(bit & 63);
+            uint64_t v = src[bit >> 6] >> sh;
+            if (sh + W > 64) v |= src[(bit >> 6) + 1] << (64 - sh);
+            v &= mask;
+            if (v >= q) return HESPMV_E_INVALID;
+            dst[k] = v;
+        }
+    }
+    return HESPMV_OK;
+}
+
+int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
+                            const uint64_t *X_packed, uint64_t *y_packed, void *stream) {
+    if (!ctx || !m || !A_packed || !X_packed || !y_packed) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const size_t nc = m->plan.chunks.size(), np = m->plan.parts.size();
+    const size_t CT = 2 * (size_t)ctx->h.L * ctx->h.N, PW = packed_ct_words(ctx->h);
+    cudaStream_t st = (cudaStream_t)stream;
+    // device staging owned by the context, grown on demand: unpacked A, X, y,
+    // then packed A, X, y
+    const size_t need = (2 * nc + np) * (CT + PW) * 8;
+    if (ctx->io_bytes < need) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, ctx->io);
+        ctx->io = dev_alloc(ctx, need);
+        ctx->io_bytes = ctx->io ? need : 0;
+    }
+    uint64_t *io = (uint64_t *)ctx->io;
+    if (!io) FAIL(HESPMV_E_NOMEM, "staging allocation failed");
+    if (!ctx->err_host && cudaHostAlloc((void **)&ctx->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        ctx->err_host = nullptr;
+        FAIL(HESPMV_E_NOMEM, "page-locked status word allocation failed");
+    }
+    uint64_t *dA = io, *dX = dA + nc * CT, *dY = dX + nc * CT;
+    uint64_t *pA = dY + np * CT, *pX = pA + nc * PW, *pY = pX + nc * PW;
+    const uint64_t *a = dA, *x = dX;
+    uint64_t *y = dY;
+    const Ctx c = view(ctx);
+    *ctx->err_host = 0;
+    const std::vector<size_t> gsz = upload_group_sizes(ctx, nc);
+    int rc = spmv_core(ctx, 1, &m, &a, &x, &y, st, false, A_packed, X_packed, &gsz, pA, pX);
+    if (!rc && (op_ct_pack(c, dY, pY, np, st) != cudaSuccess ||
+                cudaMemcpyAsync(y_packed, pY, np * PW * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(ctx->err_host, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)) {
+        rc = HESPMV_E_CUDA;
+        ctx->err = "packed evaluation failed";
+    }
+    cudaStreamSynchronize(st);
+    if (!rc && *ctx->err_host) {
+        const int v = *ctx->err_host;
+        if (cudaMemset(ctx->d.err, 0, sizeof(int)) != cudaSuccess) FAIL(HESPMV_E_CUDA, "status reset failed");
+        return status_of_code(ctx, v);
+    }
     return rc;
 }
 
@@ -1949,6 +2142,18 @@ int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t) {
     return HESPMV_OK;
 }
 
+int hespmv_set_upload_groups(hespmv_ctx *ctx, int32_t groups) {
+    if (!ctx || groups < 0 || groups > 64) return HESPMV_E_INVALID;
+    ctx->upload_groups = groups;
+    return HESPMV_OK;
+}
+
+int hespmv_get_upload_groups(const hespmv_ctx *ctx, int32_t *groups) {
+    if (!ctx || !groups) return HESPMV_E_INVALID;
+    *groups = ctx->upload_groups > 0 ? ctx->upload_groups : (int32_t)kUploadGroups;
+    return HESPMV_OK;
+}
+
 int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t) {
     if (!ctx || !t) return HESPMV_E_INVALID;
     *t = hespmv_tuning{};
@@ -2101,11 +2306,8 @@ int hespmv_device_status(hespmv_ctx *ctx, int32_t *code) {
     int v = 0;
     CK(cudaMemcpy(&v, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (code) *code = v;
-    if (v) {
-        CK(cudaMemset(ctx->d.err, 0, sizeof(int)));
-        FAIL(HESPMV_E_TIMEOUT, "a device-side wait ran out (code " + std::to_string(v) + ")");
-    }
-    return HESPMV_OK;
+    if (v) CK(cudaMemset(ctx->d.err, 0, sizeof(int)));
+    return status_of_code(ctx, v);
 }
 
 int hespmv_selftest_wait_timeout(hespmv_ctx *ctx, int32_t *code) {

@@ -21,6 +21,7 @@ struct HostTables {
     // BFV: auxiliary basis B = table entries [iB, iB + nB); multi-word
     // constants of exact Chinese remaindering over Q (wq words) and B (wb)
     int nB = 0, iB = 0, wq = 0, wb = 0;
+    int pack_bits = 0;  // bits per residue of packed ciphertexts: max bit length of q_0..q_{L-1}
     std::vector<uint64_t> bfv_delta;   // [L][2] floor(Q/t) mod q_i, Shoup pair
     std::vector<uint64_t> bfv_const;   // packed, see BfvLayout
     uint64_t bfv_qinv_t = 0;           // Q^-1 mod t (decryption)
@@ -243,8 +244,15 @@ struct hespmv_ctx {
     // events that overlap their uploads with the HE-Mult groups
     void *io = nullptr;
     size_t io_bytes = 0;
+    int *err_host = nullptr;  // page-locked copy of the device error word (packed host path)
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> copy_events;
+    // HE-Mult groups of host evaluations alternate between the evaluation
+    // stream and this one (each with its own scratch), so that a group's
+    // kernels fill the tails of the previous group's; joined by join_event
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t join_event = nullptr;
+    int upload_groups = 0;  // upload groups of host evaluations (0: default)
     // CKKS encoder tables and CRT constants (host, made on first use)
     hespmv::CkksCodec *codec = nullptr;
     hespmv::CrtReal *crt = nullptr;

@@ -67,6 +67,16 @@ int ks_split_variants(const Ctx &c);
 cudaError_t ks_prepare(const Ctx &c);
 // self-test: a bounded wait that runs out and sets the device error word
 cudaError_t op_wait_probe(const Ctx &c, cudaStream_t st);
+// device error word code of the unpack kernel (kErrWaitTimeout = 1 is the
+// bounded waits')
+constexpr int kErrBadResidue = 2;
+// packed ciphertexts (h.pack_bits bits per residue, whole-word limbs) <-> u64
+// residues, n ciphertexts; unpack converts pa -> oa and, when pb is given,
+// pb -> ob in the same launch; a residue not below its prime sets
+// kErrBadResidue in the device error word
+cudaError_t op_ct_unpack(const Ctx &c, const uint64_t *pa, uint64_t *oa, const uint64_t *pb, uint64_t *ob,
+                         size_t n, cudaStream_t st);
+cudaError_t op_ct_pack(const Ctx &c, const uint64_t *in, uint64_t *out, size_t n, cudaStream_t st);
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);

@@ -629,4 +629,75 @@ cudaError_t op_wait_probe(const Ctx &c, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Packed ciphertext limbs (W bits per residue, little-endian bit string per
+// limb of limb_words words) -> u64 residues, one thread per residue; two
+// arrays per launch (blockIdx.y).  The second word is read only when the
+// residue crosses into it, which stays inside the limb.  A residue not below
+// its prime is stored reduced and flagged in the device error word.
+__global__ void k_ct_unpack(const uint64_t *pa, uint64_t *oa, const uint64_t *pb, uint64_t *ob,
+                            int64_t total, int log2n, int L, int W, int64_t limb_words,
+                            const ModConst *mc, int *err) {
+    const uint64_t *in = blockIdx.y ? pb : pa;
+    uint64_t *out = blockIdx.y ? ob : oa;
+    const uint64_t mask = W == 64 ? ~0ull : (1ull << W) - 1;
+    const int64_t nmask = (1LL << log2n) - 1;
+    GRID_STRIDE(i, total) {
+        const int64_t limb = i >> log2n, bit = (i & nmask) * W;
+        const uint64_t *src = in + limb * limb_words + (bit >> 6);
+        const int sh = (int)(bit & 63);
+        uint64_t v = src[0] >> sh;
+        if (sh + W > 64) v |= src[1] << (64 - sh);
+        v &= mask;
+        const uint64_t q = mc[limb % L].q;
+        if (v >= q) {
+            v %= q;
+            atomicExch(err, kErrBadResidue);
+        }
+        out[i] = v;
+    }
+}
+
+// u64 residues (each below 2^W) -> packed limbs, one thread per output word:
+// the residues whose bits meet word w of a limb are those with
+// k W < 64 w + 64 and k W + W > 64 w.
+__global__ void k_ct_pack(const uint64_t *in, uint64_t *out, int64_t total_words, int log2n, int W,
+                          int64_t limb_words) {
+    const int64_t N = 1LL << log2n;
+    GRID_STRIDE(i, total_words) {
+        const int64_t limb = i / limb_words, b0 = (i - limb * limb_words) * 64;
+        const uint64_t *src = in + (limb << log2n);
+        int64_t k1 = (b0 + 64 + W - 1) / W;
+        if (k1 > N) k1 = N;
+        uint64_t word = 0;
+        for (int64_t k = b0 / W; k < k1; ++k) {
+            const int64_t sh = k * W - b0;  // in (-W, 64)
+            word |= sh >= 0 ? src[k] << sh : src[k] >> -sh;
+        }
+        out[i] = word;
+    }
+}
+
+cudaError_t op_ct_unpack(const Ctx &c, const uint64_t *pa, uint64_t *oa, const uint64_t *pb, uint64_t *ob,
+                         size_t n, cudaStream_t st) {
+    const int64_t total = (int64_t)n * 2 * c.L * c.N;
+    if (total == 0) return cudaSuccess;
+    const int W = c.c->h.pack_bits;
+    const int64_t lw = ((int64_t)c.N * W + 63) / 64;
+    const int r = prof_begin(c, "k_ct_unpack", st);
+    k_ct_unpack<<<dim3(grid_for(total), pb ? 2 : 1), kThreads, 0, st>>>(pa, oa, pb, ob, total, c.log2n, c.L,
+                                                                         W, lw, c.c->d.mc, c.c->d.err);
+    prof_end(c, r, st);
+    return cudaGetLastError();
+}
+
+cudaError_t op_ct_pack(const Ctx &c, const uint64_t *in, uint64_t *out, size_t n, cudaStream_t st) {
+    const int W = c.c->h.pack_bits;
+    const int64_t lw = ((int64_t)c.N * W + 63) / 64, total = (int64_t)n * 2 * c.L * lw;
+    if (total == 0) return cudaSuccess;
+    const int r = prof_begin(c, "k_ct_pack", st);
+    k_ct_pack<<<grid_for(total), kThreads, 0, st>>>(in, out, total, c.log2n, W, lw);
+    prof_end(c, r, st);
+    return cudaGetLastError();
+}
+
 }  // namespace hespmv

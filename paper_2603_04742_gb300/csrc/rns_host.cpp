@@ -1,6 +1,7 @@
 // Host construction of the RNS parameter tables: prime search, roots of
 // unity, twiddle tables (with Shoup companions) and the base-conversion
 // constants of hybrid key switching.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -145,6 +146,8 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         }
         h.nB = (int)h.q.size() - h.iB;
     }
+    h.pack_bits = 0;
+    for (int i = 0; i < p.L; ++i) h.pack_bits = std::max(h.pack_bits, 64 - __builtin_clzll(h.q[i]));
     const int M = (int)h.q.size();
     h.psi.resize(M);
     h.mc.resize(M);

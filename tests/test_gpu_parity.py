@@ -303,6 +303,58 @@ def test_spmv_host_buffers_and_batched_match():
         assert np.array_equal(hy, ys[i].download())
 
 
+def _set_packed_residue(packed, limb_words, limb, k, W, v):
+    """Overwrite residue k of limb `limb` in one packed ciphertext with v."""
+    lo = limb * limb_words * 64 + k * W
+    for w in range(lo // 64, (lo + W - 1) // 64 + 1):
+        sh = lo - 64 * w
+        m = (((1 << W) - 1) << sh if sh >= 0 else ((1 << W) - 1) >> -sh) & ((1 << 64) - 1)
+        part = (v << sh if sh >= 0 else v >> -sh) & m
+        packed[w] = np.uint64((int(packed[w]) & ~m & ((1 << 64) - 1)) | part)
+
+
+def test_spmv_host_packed_matches_device_path():
+    """The packed host path (upload of W-bit residues, unpack kernels per
+    upload group, pack kernel for the result) gives the packed form of the
+    device path's result ciphertexts, bit for bit, on chunk counts that leave
+    ragged upload groups; a residue >= q is reported and leaves the context
+    usable."""
+    logn, L, K, dnum, t = synth.RING["c1"]
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t, slots=256)
+    ctx.keygen(12)
+    words, W = ctx.ct_packed_words()
+    for seed, (rows, cols, nnz) in enumerate([(300, 280, 900), (700, 640, 5000), (1, 1, 1)]):
+        A, x = synth.small_matrix(seed, rows, cols, nnz)
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=21 + seed)
+        cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=31 + seed)
+        y = ctx.spmv(m, ca, cx).download()
+        pA, pX = ctx.ct_pack(ca.download()), ctx.ct_pack(cx.download())
+        py = np.zeros((m.n_parts, words), dtype=np.uint64)
+        hy = np.zeros_like(y)
+        # upload groups: one, ragged, more groups than chunks, the default
+        for groups in (1, 3, 64, 0):
+            ctx.set_upload_groups(groups)
+            py[:] = 0
+            ctx.spmv_host_packed(m, pA, pX, py)
+            assert np.array_equal(py, ctx.ct_pack(y)), (seed, m.n_chunks, groups)
+            ctx.spmv_host(m, ca.download(), cx.download(), hy)
+            assert np.array_equal(hy, y), (seed, m.n_chunks, groups)
+        assert np.array_equal(ctx.ct_unpack(py), y)
+        assert list(ctx.decrypt(m, ctx.spmv(m, ca, cx))) == list(A.matvec(x))
+    # an unreduced residue in the last chunk's vector ciphertext
+    q = ctx.moduli()[0]
+    bad = pX.copy()
+    _set_packed_residue(bad[-1], words // (2 * L), 2 * L - 1, 3, W, q[L - 1])
+    with pytest.raises(B.HespmvError) as ei:
+        ctx.spmv_host_packed(m, pA, bad, py)
+    assert ei.value.code == B.HESPMV_E_INVALID
+    ctx.device_status()
+    ctx.spmv_host_packed(m, pA, pX, py)
+    assert np.array_equal(py, ctx.ct_pack(y))
+
+
 def test_spmv_edge_cases():
     logn, L, K, dnum, t = synth.RING["c1"]
     from paper_2603_04742_gb300.api import Context
