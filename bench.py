@@ -174,13 +174,35 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot):
+# a 64 x 64 -> 128-bit word product of the BFV multi-word arithmetic takes 4
+# of the 10 heavy-pipe partial products of a Shoup product
+WORD_PRODUCT_MULMODS = 0.4
+
+
+def bfv_basis(logn, L, t, q):
+    """Auxiliary basis size and multi-word widths of the BFV HE-Mult (the
+    library's rule: B > 2 t N Q in primes of q's size; words for Q and B
+    with room for a sign and sums)."""
+    import math
+    lq = sum(math.log2(v) for v in q[:L])
+    need = math.log2(t) + logn + 2 + lq
+    lb = math.log2(q[-1])
+    nB = int(math.ceil(need / lb))
+    wq = int(math.ceil((lq + 2) / 64)) + 1
+    wb = int(math.ceil((nB * lb + 2) / 64)) + 1
+    return nB, wq, wb
+
+
+def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot, bfv=None):
     """Algorithmic work of one step in kernel `name`: (mulmods, bytes).
 
     n_ks = key switches per step (relinearisations + elementary rotations).
     Mulmods count every modular product (NTT butterflies, base conversions,
     key products, masks); bytes count one read of every input and one write
-    of every output of the kernel (a key is read once per step)."""
+    of every output of the kernel (a key is read once per step).  bfv =
+    (nB, wq, wb) adds the BFV HE-Mult kernels: its NTTs, the exact extension
+    and scale-and-round (Shoup products, plus word products of the
+    multi-word sums at WORD_PRODUCT_MULMODS each)."""
     logn, L, K, dnum = ring[:4]
     N = 1 << logn
     LK = L + K
@@ -217,6 +239,24 @@ def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot):
         "k_moddown_delta": (n_ks * 2 * (K + K * L + L) * N, n_ks * 2 * (K + L) * w),
         "k_moddown_final": (n_ks * 2 * L * N, n_ks * 2 * L * 3 * w),
     }
+    if bfv:
+        nB, wq, wb = bfv
+        n = n_chunks
+        wp = WORD_PRODUCT_MULMODS
+        inv = 4 * n * L + 3 * n * (L + nB)     # limb transforms: a, b over Q; d over Q u B
+        fwd = 4 * n * nB + 3 * n * L           # a, b over B; the result over Q
+        m.update({
+            "k_intt_rows": (inv * h * n2, inv * 2 * w),
+            "k_intt_cols": (inv * (h * n1 + N), inv * 2 * w),
+            "k_fntt_rows": (fwd * h * n2, fwd * 2 * w),
+            "k_fntt_cols": (fwd * h * n1, fwd * 2 * w),
+            "k_bfv_extend": (4 * n * N * (L + nB * (wq + 1) + wp * L * wq),
+                             4 * n * (L + nB) * w),
+            "k_bfv_tensor": (n * (L + nB) * N * 4, n * (4 * L + 4 * nB + 3 * (L + nB)) * w),
+            "k_bfv_scale": (3 * n * N * (2 * L + nB * (3 + wq + 1) + L * (wb + 1)
+                                         + wp * (L * wq + nB * wb)),
+                            3 * n * (2 * L + nB) * w),
+        })
     return m.get(name, (0, 0))
 
 
@@ -321,12 +361,12 @@ def per_step_ms(fn, stream, n):
     return [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
 
 
-def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"):
+def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3", bfv=None):
     peaks, peak_kind = measured_peaks()
     kernels = {}
     total_ms = sum(v[1] for v in prof.values())
     for name, (cnt, kms) in prof.items():
-        mm, by = kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot)
+        mm, by = kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot, bfv)
         kernels[name] = {"launches_per_step": cnt / steps, "ms_per_step": kms / steps,
                          "share": kms / total_ms if total_ms else 0.0,
                          "mulmods_per_step": mm, "bytes_per_step": by}
@@ -674,8 +714,15 @@ def main():
 
     n_chunks = sum(m.n_chunks for m in ms)
     n_ks = n_chunks + sum(m.n_keyswitch for m in ms)
+    bfv = None
+    if args.scheme == "bfv":
+        logn, L = ring[0], ring[1]
+        bfv = bfv_basis(logn, L, ring[4], ctx.moduli()[0])
     kernels, roof = roofline(ctx, prof, args.steps, ring, n_ks, n_chunks,
-                             sum(m.n_parts for m in ms), sum(m.n_rot for m in ms), args.config)
+                             sum(m.n_parts for m in ms), sum(m.n_rot for m in ms), args.config, bfv)
+    # the committed DRAM counters are for the BGV kernels of this workload
+    if args.scheme != "bgv":
+        roof["traffic"] = None
 
     cpu = None
     if not args.no_cpu_baseline and args.scheme == "bgv":

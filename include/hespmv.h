@@ -322,8 +322,9 @@ int hespmv_ct_pack(const hespmv_ctx *ctx, const uint64_t *cts, size_t n_ct, uint
 int hespmv_ct_unpack(const hespmv_ctx *ctx, const uint64_t *packed, size_t n_ct, uint64_t *cts);
 /* hespmv_spmv_host on packed buffers: A_packed and X_packed hold n_chunks
  * packed ciphertexts each and are copied to the device in groups (the
- * copies of later groups overlapping the HE-Mult of earlier ones; each group
- * is unpacked on the device just before its HE-Mult); y_packed receives the n_parts results, packed on the
+ * copies of later groups overlapping the HE-Mult of earlier ones; the fused
+ * HE-Mult reads the packed residues directly, other paths unpack each group
+ * first); y_packed receives the n_parts results, packed on the
  * device.  A residue that is not below its prime is evaluated reduced modulo
  * the prime and the call returns HESPMV_E_INVALID.  Synchronises `stream`.
  * Page-locked host buffers (cudaHostAlloc) make the copies asynchronous. */

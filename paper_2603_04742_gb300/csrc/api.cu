@@ -629,16 +629,21 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
             cudaStream_t gs = alt ? ctx->aux_stream : st;
             uint64_t *gd = dbuf + (alt ? pp.mult_w : 0), *gscr = scr + (alt ? pp.mult_w : 0);
             if (pp.hA) CK(cudaStreamWaitEvent(gs, ctx->copy_events[gi], 0));  // this group's chunks
+            const bool bgv = ctx->h.scheme != HESPMV_SCHEME_BFV;  // BGV and CKKS tensors are limb-wise
+            if (bgv && ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
+                // one matrix's consecutive chunks: tensor product fused into the key switch,
+                // reading packed host operands directly where given
+                if (pp.pkA)
+                    CK(relin_tensor_fused(c, pp.pkA + g0 * pp.pk_words, pp.pkX + g0 * pp.pk_words, ctx->rlk,
+                                          prod + g0 * CT, gn, gscr, gs, ctx->h.pack_bits));
+                else
+                    CK(relin_tensor_fused(c, A[i] + k * CT, X[i] + k * CT, ctx->rlk, prod + g0 * CT, gn,
+                                          gscr, gs));
+                continue;
+            }
             if (pp.pkA)
                 CK(op_ct_unpack(c, pp.pkA + g0 * pp.pk_words, (uint64_t *)A[0] + g0 * CT,
                                 pp.pkX + g0 * pp.pk_words, (uint64_t *)X[0] + g0 * CT, gn, gs));
-            const bool bgv = ctx->h.scheme != HESPMV_SCHEME_BFV;  // BGV and CKKS tensors are limb-wise
-            if (bgv && ks_fused_supported(c) && all[g0 + gn - 1].first == i) {
-                // one matrix's consecutive chunks: tensor product fused into the key switch
-                CK(relin_tensor_fused(c, A[i] + k * CT, X[i] + k * CT, ctx->rlk, prod + g0 * CT, gn,
-                                      gscr, gs));
-                continue;
-            }
             size_t s = 0;
             while (s < gn) {  // tensor over runs of one instance's consecutive chunks
                 const size_t ii = all[g0 + s].first, kk = all[g0 + s].second;

@@ -81,10 +81,12 @@ cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, c
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);
 // relinearised HE-Mult of n ciphertext pairs (A + i*2LN, B + i*2LN) with the
-// tensor product fused into the key switch (requires ks_fused_supported)
+// tensor product fused into the key switch (requires ks_fused_supported);
+// pk_bits > 0: A and B are packed ciphertexts of that many bits per residue
+// (a residue not below its prime sets kErrBadResidue)
 cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *B,
                                const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
-                               cudaStream_t st);
+                               cudaStream_t st, int pk_bits = 0);
 // x <- x * 2^64 mod q over n_items x (L+K) limbs (keys to Montgomery form)
 cudaError_t op_to_mont(const Ctx &c, uint64_t *x, size_t n_items, cudaStream_t st);
 

@@ -45,12 +45,33 @@ struct KsArgs {
 // Input of a key switch: d (NTT domain, item stride ds), or, fused with the
 // tensor product of HE-Mult, d = a1 * b1 for ciphertexts a = ta + i*ts,
 // b = tb + i*ts, whose (a0 b0, a0 b1 + a1 b0) is then the addend.
+// With pk_bits > 0, ta and tb hold packed ciphertexts (pk_bits bits per
+// residue, limbs of pk_lw words, ts words per ciphertext), read and checked
+// here instead of in a separate unpack pass.
 struct KsSrc {
     const uint64_t *d;
     int64_t ds;
     const uint64_t *ta, *tb;
     int64_t ts;
+    int pk_bits = 0;
+    int64_t pk_lw = 0;
 };
+
+// residue k of a packed limb; one not below q is reduced and flagged
+__device__ __forceinline__ uint64_t packed_residue(const uint64_t *limb, int64_t k, int W, uint64_t q,
+                                                   int *err) {
+    const int64_t bit = k * W;
+    const uint64_t *p = limb + (bit >> 6);
+    const int sh = (int)(bit & 63);
+    uint64_t v = p[0] >> sh;
+    if (sh + W > 64) v |= p[1] << (64 - sh);
+    v &= (1ull << W) - 1;  // W < 64
+    if (v >= q) {
+        v %= q;
+        atomicExch(err, kErrBadResidue);
+    }
+    return v;
+}
 
 // Addend of the key switch's output: component c (add_mask bit c) of
 // add + item * is + c * cs, [L][N] each.
@@ -114,6 +135,13 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
     uint64_t v[8];
     if (s.d) {
         load8(v, s.d + item * s.ds + off + 8 * j);
+    } else if (s.pk_bits) {  // d2 = a1 * b1 from packed operands
+        const int64_t limb = (int64_t)(L + k) * s.pk_lw, c0 = (int64_t)row * M + 8 * j;
+        const uint64_t *pa = s.ta + item * s.ts + limb, *pb = s.tb + item * s.ts + limb;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            v[e] = mul_mod(packed_residue(pa, c0 + e, s.pk_bits, mc.q, a.err),
+                           packed_residue(pb, c0 + e, s.pk_bits, mc.q, a.err), mc);
     } else {  // d2 = a1 * b1
         uint64_t x[8], y[8];
         load8(x, s.ta + item * s.ts + LN + off + 8 * j);
@@ -324,10 +352,24 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
         ulonglong2 y0 = make_ulonglong2(0, 0), y1 = make_ulonglong2(0, 0);
         uint64_t pm = a.pmont[l];
         if (s.ta) {
-            const int64_t o = item * s.ts + (int64_t)l * N + k, LN = (int64_t)a.L * N;
-            const ulonglong2 a0 = *(const ulonglong2 *)(s.ta + o), b0 = *(const ulonglong2 *)(s.tb + o);
-            const ulonglong2 a1 = *(const ulonglong2 *)(s.ta + o + LN);
-            const ulonglong2 b1 = *(const ulonglong2 *)(s.tb + o + LN);
+            ulonglong2 a0, b0, a1, b1;
+            if (s.pk_bits) {
+                const uint64_t q = mc.q;
+                const int W = s.pk_bits;
+                const uint64_t *pa0 = s.ta + item * s.ts + (int64_t)l * s.pk_lw;
+                const uint64_t *pb0 = s.tb + item * s.ts + (int64_t)l * s.pk_lw;
+                const uint64_t *pa1 = pa0 + (int64_t)a.L * s.pk_lw, *pb1 = pb0 + (int64_t)a.L * s.pk_lw;
+                a0 = make_ulonglong2(packed_residue(pa0, k, W, q, a.err), packed_residue(pa0, k + 1, W, q, a.err));
+                b0 = make_ulonglong2(packed_residue(pb0, k, W, q, a.err), packed_residue(pb0, k + 1, W, q, a.err));
+                a1 = make_ulonglong2(packed_residue(pa1, k, W, q, a.err), packed_residue(pa1, k + 1, W, q, a.err));
+                b1 = make_ulonglong2(packed_residue(pb1, k, W, q, a.err), packed_residue(pb1, k + 1, W, q, a.err));
+            } else {
+                const int64_t o = item * s.ts + (int64_t)l * N + k, LN = (int64_t)a.L * N;
+                a0 = *(const ulonglong2 *)(s.ta + o);
+                b0 = *(const ulonglong2 *)(s.tb + o);
+                a1 = *(const ulonglong2 *)(s.ta + o + LN);
+                b1 = *(const ulonglong2 *)(s.tb + o + LN);
+            }
             own = make_ulonglong2(mul_mod(a1.x, b1.x, mc), mul_mod(a1.y, b1.y, mc));
             // y0, y1 as Montgomery residues (times 2^-64, in [0, 2q)); their
             // factor P * 2^128 mod q restores the scale in the final reduction
@@ -593,13 +635,15 @@ cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, c
 
 cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *B,
                                const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
-                               cudaStream_t st) {
+                               cudaStream_t st, int pk_bits) {
     const KsArgs a = ks_args(c);
     const int64_t CT = 2 * (int64_t)c.L * c.N;
+    const int64_t lw = pk_bits ? ((int64_t)c.N * pk_bits + 63) / 64 : 0;
+    const int64_t TS = pk_bits ? 2 * c.L * lw : CT;  // words per input ciphertext
     const size_t maxn = ks_max_items(c);
     for (size_t i0 = 0; i0 < n; i0 += maxn) {
         const int m = (int)std::min(maxn, n - i0);
-        KsSrc s{nullptr, 0, A + i0 * CT, B + i0 * CT, CT};
+        KsSrc s{nullptr, 0, A + i0 * TS, B + i0 * TS, TS, pk_bits, lw};
         cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, nullptr, 0, 0, 0, m, scratch, st);
         if (e != cudaSuccess) return e;
     }
