@@ -330,8 +330,22 @@ int hespmv_ct_unpack(const hespmv_ctx *ctx, const uint64_t *packed, size_t n_ct,
  * Page-locked host buffers (cudaHostAlloc) make the copies asynchronous. */
 int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
                             const uint64_t *X_packed, uint64_t *y_packed, void *stream);
+/* Pipelined form of hespmv_spmv_host_packed for a stream of independent
+ * evaluations: enqueues the uploads, the evaluation and the result download
+ * and returns without waiting.  Consecutive calls use two staging slots in
+ * turn, so a call's uploads run while the previous call computes; a slot is
+ * refilled only once the call that used it before has copied its result out
+ * (ordered on the device, the host never blocks).  A_packed, X_packed and
+ * y_packed must stay valid and unmodified until `stream` has passed the call
+ * (e.g. cudaStreamSynchronize); the uploads run on the context's own copy
+ * stream, ordered after the slot's previous evaluation only.  Kernels are
+ * launched one by one (no graph).  A residue not below its prime is reported
+ * by hespmv_device_status, not by this call. */
+int hespmv_spmv_host_packed_async(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
+                                  const uint64_t *X_packed, uint64_t *y_packed, void *stream);
 /* Upload groups of the host-buffer evaluations (1..64; 0 restores the
- * default, 7).  The chunks are uploaded in that many groups; the HE-Mult of a
+ * defaults: 7 for the synchronous calls, 2 for the pipelined one;
+ * hespmv_get_upload_groups gives 0 while the defaults apply).  The chunks are uploaded in that many groups; the HE-Mult of a
  * group starts when its own upload has landed, and consecutive groups run on
  * two streams so that one group's kernels fill the tails of the other's.
  * More groups start the work earlier but give each fused key switch fewer

@@ -242,8 +242,14 @@ class Context:
         self.check(self.lib.hespmv_spmv_host(self.h, m.h, _u64p(A_host), _u64p(X_host),
                                              _u64p(y_host), _stream_handle(stream)))
 
+    def spmv_host_packed_async(self, m, A_packed, X_packed, y_packed, stream=None):
+        """Enqueue only: the buffers must outlive the stream's progress past
+        this call (synchronise the stream before reading y_packed)."""
+        self.check(self.lib.hespmv_spmv_host_packed_async(self.h, m.h, _u64p(A_packed), _u64p(X_packed),
+                                                          _u64p(y_packed), _stream_handle(stream)))
+
     def set_upload_groups(self, groups):
-        """Upload groups of spmv_host / spmv_host_packed (0: the default)."""
+        """Upload groups of the host-buffer evaluations (0: the defaults)."""
         self.check(self.lib.hespmv_set_upload_groups(self.h, groups))
 
     def get_upload_groups(self):

@@ -110,6 +110,7 @@ SIGNATURES = {
     "hespmv_ct_pack": (c_int, [c_void_p, u64p, c_size_t, u64p]),
     "hespmv_ct_unpack": (c_int, [c_void_p, u64p, c_size_t, u64p]),
     "hespmv_spmv_host_packed": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),
+    "hespmv_spmv_host_packed_async": (c_int, [c_void_p, c_void_p, u64p, u64p, u64p, c_void_p]),
     "hespmv_set_upload_groups": (c_int, [c_void_p, c_int32]),
     "hespmv_get_upload_groups": (c_int, [c_void_p, i32p]),
     "hespmv_encode_matrix_plain": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),

@@ -459,11 +459,17 @@ size_t packed_ct_words(const HostTables &h) { return 2 * (size_t)h.L * packed_li
 // the fastest; fewer groups delay the first HE-Mult, more make each fused key
 // switch too small.
 constexpr size_t kUploadGroups = 7;
+// Pipelined evaluations overlap a call's uploads with the previous call's
+// compute, so the groups only need to let the HE-Mult start before the whole
+// upload has landed: 2 groups (1048 SpMV/s on the stencil) beat 1 (975), 4
+// (1012) and 7 (884).
+constexpr size_t kPipelinedUploadGroups = 2;
 
 // upload (and HE-Mult) group sizes of a host evaluation of nc chunks
-std::vector<size_t> upload_group_sizes(const hespmv_ctx *ctx, size_t nc) {
+std::vector<size_t> upload_group_sizes(const hespmv_ctx *ctx, size_t nc, bool pipelined = false) {
+    const size_t dflt = pipelined ? kPipelinedUploadGroups : kUploadGroups;
     const size_t groups = std::min(std::max<size_t>(nc, 1),
-                                   ctx->upload_groups > 0 ? (size_t)ctx->upload_groups : kUploadGroups);
+                                   ctx->upload_groups > 0 ? (size_t)ctx->upload_groups : dflt);
     std::vector<size_t> g;
     for (size_t k = 0; k < groups; ++k) g.push_back((nc * (k + 1)) / groups - (nc * k) / groups);
     if (g.empty() || g[0] == 0) g.assign(1, std::max<size_t>(nc, 1));
@@ -495,6 +501,10 @@ struct SpmvPrep {
     size_t mult_w = 0;
     // HE-Mult group sizes of a host evaluation (empty: groups of G)
     std::vector<size_t> gsz;
+    // pipelined host evaluation: the uploads wait for this event (or nothing)
+    // instead of the evaluation stream's earlier work
+    bool pipelined = false;
+    cudaEvent_t copy_after = nullptr;
 };
 
 // HE-Mult groups of an evaluation over `total` chunks: (first chunk, count)
@@ -602,7 +612,10 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         if (pp.hA) {  // uploads on the side stream, one event per group
             cudaStream_t cs = ctx->copy_stream;
             CK(cudaEventRecord(ctx->copy_events[0], st));  // fork
-            CK(cudaStreamWaitEvent(cs, ctx->copy_events[0], 0));
+            if (!pp.pipelined)
+                CK(cudaStreamWaitEvent(cs, ctx->copy_events[0], 0));
+            else if (pp.copy_after)  // the staging slot's previous evaluation is done with it
+                CK(cudaStreamWaitEvent(cs, pp.copy_after, 0));
             if (pp.dual) CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->copy_events[0], 0));
             for (size_t gi = 1; gi <= groups.size(); ++gi) {
                 const size_t g0 = groups[gi - 1].first, gn = groups[gi - 1].second;
@@ -722,7 +735,8 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *const *A, const uint64_t *const *X, uint64_t *const *Y,
               cudaStream_t st, bool pt_matrix = false, const uint64_t *hA = nullptr,
               const uint64_t *hX = nullptr, const std::vector<size_t> *gsz = nullptr,
-              uint64_t *pkA = nullptr, uint64_t *pkX = nullptr) {
+              uint64_t *pkA = nullptr, uint64_t *pkX = nullptr, bool pipelined = false,
+              cudaEvent_t copy_after = nullptr) {
     SpmvPrep pp;
     size_t max_G = 0;
     if (gsz)
@@ -730,6 +744,8 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     int rc = spmv_prepare(ctx, n_inst, ms, pp, st, max_G);
     if (rc) return rc;
     if (gsz) pp.gsz = *gsz;
+    pp.pipelined = pipelined;
+    pp.copy_after = copy_after;
     pp.pt_matrix = pt_matrix;
     pp.hA = hA;
     pp.hX = hX;
@@ -754,7 +770,9 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     uint64_t *ws = workspace(ctx, pp.need_bytes);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
     const bool profiling = ctx->prof && ctx->prof->on;
-    if (!ctx->use_graphs || profiling) return spmv_enqueue(ctx, n_inst, ms, A, X, Y, pp, ws, st);
+    // pipelined host evaluations launch eagerly: a graph launch would order
+    // its uploads after the stream's earlier evaluations
+    if (!ctx->use_graphs || profiling || pipelined) return spmv_enqueue(ctx, n_inst, ms, A, X, Y, pp, ws, st);
     std::vector<uint64_t> key;
     key.push_back((uint64_t)(uintptr_t)ws);
     key.push_back(pt_matrix ? 1 : 0);
@@ -885,6 +903,10 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    for (int s = 0; s < 2; ++s) {
+        if (ctx->slot_free[s]) cudaEventDestroy(ctx->slot_free[s]);
+        dev_free(ctx, ctx->aio[s]);
+    }
     if (ctx->join_event) cudaEventDestroy(ctx->join_event);
     if (ctx->err_host) cudaFreeHost(ctx->err_host);
     for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
@@ -903,7 +925,7 @@ int hespmv_ctx_moduli(const hespmv_ctx *ctx, uint64_t *moduli, uint64_t *psi, ui
 
 int hespmv_ctx_device_bytes(const hespmv_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) return HESPMV_E_INVALID;
-    *bytes = ctx->owned_bytes + ctx->ws_bytes;
+    *bytes = ctx->owned_bytes + ctx->ws_bytes + ctx->io_bytes + ctx->aio_bytes[0] + ctx->aio_bytes[1];
     return HESPMV_OK;
 }
 
@@ -1866,6 +1888,44 @@ int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_
     return rc;
 }
 
+int hespmv_spmv_host_packed_async(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
+                                  const uint64_t *X_packed, uint64_t *y_packed, void *stream) {
+    if (!ctx || !m || !A_packed || !X_packed || !y_packed) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const size_t nc = m->plan.chunks.size(), np = m->plan.parts.size();
+    const size_t CT = 2 * (size_t)ctx->h.L * ctx->h.N, PW = packed_ct_words(ctx->h);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int s = ctx->aslot;
+    // staging of this slot: unpacked A, X, y, then packed A, X, y
+    const size_t need = (2 * nc + np) * (CT + PW) * 8;
+    if (ctx->aio_bytes[s] < need) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, ctx->aio[s]);
+        ctx->aio[s] = dev_alloc(ctx, need);
+        ctx->aio_bytes[s] = ctx->aio[s] ? need : 0;
+        ctx->slot_used[s] = false;
+    }
+    uint64_t *io = (uint64_t *)ctx->aio[s];
+    if (!io) FAIL(HESPMV_E_NOMEM, "staging allocation failed");
+    if (!ctx->slot_free[s]) CK(cudaEventCreateWithFlags(&ctx->slot_free[s], cudaEventDisableTiming));
+    uint64_t *dA = io, *dX = dA + nc * CT, *dY = dX + nc * CT;
+    uint64_t *pA = dY + np * CT, *pX = pA + nc * PW, *pY = pX + nc * PW;
+    const uint64_t *a = dA, *x = dX;
+    uint64_t *y = dY;
+    const Ctx c = view(ctx);
+    const std::vector<size_t> gsz = upload_group_sizes(ctx, nc, true);
+    int rc = spmv_core(ctx, 1, &m, &a, &x, &y, st, false, A_packed, X_packed, &gsz, pA, pX, true,
+                       ctx->slot_used[s] ? ctx->slot_free[s] : nullptr);
+    if (rc) return rc;
+    CK(op_ct_pack(c, dY, pY, np, st));
+    CK(cudaMemcpyAsync(y_packed, pY, np * PW * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ctx->slot_free[s], st));
+    ctx->slot_used[s] = true;
+    ctx->aslot = s ^ 1;
+    return HESPMV_OK;
+}
+
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out) {
     if (!ctx || !b || !slots_out || index >= b->n) return HESPMV_E_INVALID;
@@ -2155,7 +2215,7 @@ int hespmv_set_upload_groups(hespmv_ctx *ctx, int32_t groups) {
 
 int hespmv_get_upload_groups(const hespmv_ctx *ctx, int32_t *groups) {
     if (!ctx || !groups) return HESPMV_E_INVALID;
-    *groups = ctx->upload_groups > 0 ? ctx->upload_groups : (int32_t)kUploadGroups;
+    *groups = ctx->upload_groups > 0 ? ctx->upload_groups : 0;
     return HESPMV_OK;
 }
 

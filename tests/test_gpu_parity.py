@@ -355,6 +355,53 @@ def test_spmv_host_packed_matches_device_path():
     assert np.array_equal(py, ctx.ct_pack(y))
 
 
+def test_spmv_host_packed_async_pipeline():
+    """Pipelined packed evaluations: calls on two instances in flight at once
+    (both staging slots reused several times, uploads overlapping earlier
+    calls' compute) give the device path's results bit for bit; a bad residue
+    shows up in the device status."""
+    logn, L, K, dnum, t = synth.RING["c1"]
+    from paper_2603_04742_gb300.api import Context
+    ctx = Context(logn, L, K, dnum, t, slots=256)
+    ctx.keygen(13)
+    words, W = ctx.ct_packed_words()
+    inst = []
+    for seed, (rows, cols, nnz) in enumerate([(700, 640, 5000), (300, 280, 900)]):
+        A, x = synth.small_matrix(40 + seed, rows, cols, nnz)
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=51 + seed)
+        cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=61 + seed)
+        y = ctx.spmv(m, ca, cx).download()
+        inst.append((m, ctx.ct_pack(ca.download()), ctx.ct_pack(cx.download()), ctx.ct_pack(y)))
+    stream = torch.cuda.Stream()
+    outs = []
+    for r in range(6):
+        m, pA, pX, py = inst[r % 2]
+        out = np.zeros((m.n_parts, words), dtype=np.uint64)
+        outs.append((out, py))
+        ctx.spmv_host_packed_async(m, pA, pX, out, stream=stream)
+    stream.synchronize()
+    for r, (out, py) in enumerate(outs):
+        assert np.array_equal(out, py), r
+    ctx.device_status()
+    # a synchronous call in between keeps its own staging
+    m, pA, pX, py = inst[0]
+    out = np.zeros_like(py)
+    ctx.spmv_host_packed(m, pA, pX, out)
+    assert np.array_equal(out, py)
+    bad = pX.copy()
+    _set_packed_residue(bad[0], words // (2 * L), L, 9, W, ctx.moduli()[0][0])
+    ctx.spmv_host_packed_async(m, pA, bad, out, stream=stream)
+    stream.synchronize()
+    with pytest.raises(B.HespmvError) as ei:
+        ctx.device_status()
+    assert ei.value.code == B.HESPMV_E_INVALID
+    ctx.spmv_host_packed_async(m, pA, pX, out, stream=stream)
+    stream.synchronize()
+    ctx.device_status()
+    assert np.array_equal(out, py)
+
+
 def test_spmv_edge_cases():
     logn, L, K, dnum, t = synth.RING["c1"]
     from paper_2603_04742_gb300.api import Context

@@ -101,11 +101,11 @@ def test_unpack_rejects_unreduced_residue():
 
 def test_upload_groups_setting():
     ctx = host_ctx()
-    assert ctx.get_upload_groups() == 7
+    assert ctx.get_upload_groups() == 0          # the defaults
     ctx.set_upload_groups(3)
     assert ctx.get_upload_groups() == 3
     ctx.set_upload_groups(0)
-    assert ctx.get_upload_groups() == 7
+    assert ctx.get_upload_groups() == 0
     for bad in (-1, 65):
         with pytest.raises(HespmvError):
             ctx.set_upload_groups(bad)
