@@ -101,7 +101,7 @@ __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, u
 }
 
 // Launch bounds: the row passes fit 48 registers (5 CTAs, 40 warps per SM)
-// and the final row pass 64 (4 CTAs) without spilling, which took 8 us off
+// and the final row pass of 2^8 points 64 (4 CTAs) without spilling, which took 8 us off
 // each of the forward and final row passes on the stencil ring; the
 // conversion kernels and the key product stay at 3 CTAs per SM (at 64
 // registers they spill and gain nothing).
@@ -475,7 +475,7 @@ __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_c
 // Forward row pass of delta, then out = (acc - delta) * P^-1 (the addend is
 // already in acc, times P).
 template <int LR>
-__global__ __launch_bounds__(kNttThreads, 4) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
+__global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
                                                                const uint64_t *dh, uint64_t *out) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
     __shared__ uint64_t sm[kRowTileWords];
