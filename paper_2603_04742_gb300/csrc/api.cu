@@ -696,6 +696,10 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                         FAIL(HESPMV_E_INVALID, "missing Galois key for element " + std::to_string(o.g));
                     auto pit = ctx->perms.find(o.g);
                     if (pit == ctx->perms.end()) FAIL(HESPMV_E_INVALID, "missing Galois permutation");
+                    if (ks_fused_supported(c)) {  // permutation and slot scatter inside the key switch
+                        CK(rotate_fused_inplace(c, CUR, I + o.a, pit->second, it->second, o.m, ks, st));
+                        break;
+                    }
                     CK(op_ct_move(c, PB, nullptr, CUR, I + o.a, pit->second, false, o.m, st));
                     CK(keyswitch_n(c, PB + LN, CT, it->second, OB, PB, CT, LN, 1, o.m, ks, st));
                     CK(op_ct_move(c, CUR, I + o.a, OB, nullptr, nullptr, false, o.m, st));

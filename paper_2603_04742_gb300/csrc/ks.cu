@@ -48,6 +48,9 @@ struct KsArgs {
 // With pk_bits > 0, ta and tb hold packed ciphertexts (pk_bits bits per
 // residue, limbs of pk_lw words, ts words per ciphertext), read and checked
 // here instead of in a separate unpack pass.
+// With idx, item i reads slot idx[i] of d (stride ds); with perm, coefficient
+// c of each limb reads coefficient perm[c] (a Galois automorphism in the NTT
+// domain), so a rotation's permutation needs no separate pass.
 struct KsSrc {
     const uint64_t *d;
     int64_t ds;
@@ -55,6 +58,8 @@ struct KsSrc {
     int64_t ts;
     int pk_bits = 0;
     int64_t pk_lw = 0;
+    const int32_t *idx = nullptr;
+    const int32_t *perm = nullptr;
 };
 
 // residue k of a packed limb; one not below q is reduced and flagged
@@ -74,11 +79,14 @@ __device__ __forceinline__ uint64_t packed_residue(const uint64_t *limb, int64_t
 }
 
 // Addend of the key switch's output: component c (add_mask bit c) of
-// add + item * is + c * cs, [L][N] each.
+// add + item * is + c * cs, [L][N] each (item -> idx[item], coefficient
+// c -> perm[c] when given, as for KsSrc).
 struct KsAdd {
     const uint64_t *p;
     int64_t is, cs;
     int mask;
+    const int32_t *idx = nullptr;
+    const int32_t *perm = nullptr;
 };
 
 // (a b + c d) * 2^-64 mod q, left in [0, 2q) (a, b, c, d < q < 2^50, so
@@ -139,8 +147,13 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
     const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
     const int64_t off = (int64_t)k * N + (int64_t)row * M, LN = (int64_t)L * N;
     uint64_t v[8];
-    if (s.d) {
-        load8(v, s.d + item * s.ds + off + 8 * j);
+    if (s.d && s.perm) {  // rotation: d through the Galois permutation
+        const uint64_t *base = s.d + (int64_t)(s.idx ? s.idx[item] : item) * s.ds + (int64_t)k * N;
+        const int32_t *pm = s.perm + (int64_t)row * M + 8 * j;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = base[pm[e]];
+    } else if (s.d) {
+        load8(v, s.d + (int64_t)(s.idx ? s.idx[item] : item) * s.ds + off + 8 * j);
     } else if (s.pk_bits) {  // d2 = a1 * b1 from packed operands
         const int64_t limb = (int64_t)(L + k) * s.pk_lw, c0 = (int64_t)row * M + 8 * j;
         const uint64_t *pa = s.ta + item * s.ts + limb, *pb = s.tb + item * s.ts + limb;
@@ -382,10 +395,20 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
             y0 = make_ulonglong2(mont_lazy(a0.x, b0.x, 0, 0, mc), mont_lazy(a0.y, b0.y, 0, 0, mc));
             y1 = make_ulonglong2(mont_lazy(a0.x, b1.x, a1.x, b0.x, mc), mont_lazy(a0.y, b1.y, a1.y, b0.y, mc));
             pm = a.pmont2[l];
-        } else {
-            own = *(const ulonglong2 *)(s.d + item * s.ds + (int64_t)l * N + k);
+        } else if (s.perm) {  // rotation: d and the addend through the Galois permutation
+            const int32_t p0 = s.perm[k], p1 = s.perm[k + 1];
+            const uint64_t *dl = s.d + (int64_t)(s.idx ? s.idx[item] : item) * s.ds + (int64_t)l * N;
+            own = make_ulonglong2(dl[p0], dl[p1]);
             if (ad.p) {
-                const uint64_t *base = ad.p + item * ad.is + (int64_t)l * N + k;
+                const int32_t q0 = ad.perm ? ad.perm[k] : (int32_t)k, q1 = ad.perm ? ad.perm[k + 1] : (int32_t)k + 1;
+                const uint64_t *base = ad.p + (int64_t)(ad.idx ? ad.idx[item] : item) * ad.is + (int64_t)l * N;
+                if (ad.mask & 1) y0 = make_ulonglong2(base[q0], base[q1]);
+                if (ad.mask & 2) y1 = make_ulonglong2(base[ad.cs + q0], base[ad.cs + q1]);
+            }
+        } else {
+            own = *(const ulonglong2 *)(s.d + (int64_t)(s.idx ? s.idx[item] : item) * s.ds + (int64_t)l * N + k);
+            if (ad.p) {
+                const uint64_t *base = ad.p + (int64_t)(ad.idx ? ad.idx[item] : item) * ad.is + (int64_t)l * N + k;
                 if (ad.mask & 1) y0 = *(const ulonglong2 *)base;
                 if (ad.mask & 2) y1 = *(const ulonglong2 *)(base + ad.cs);
             }
@@ -476,7 +499,8 @@ __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_c
 // already in acc, times P).
 template <int LR>
 __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
-                                                               const uint64_t *dh, uint64_t *out) {
+                                                               const uint64_t *dh, uint64_t *out,
+                                                               const int32_t *oidx) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
     __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L, LK = L + a.K;
@@ -486,6 +510,8 @@ __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(
     const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
     const int64_t rofs = (int64_t)row * M;
     const uint64_t *src = dh + ((int64_t)ic * L + i) * N + rofs;
+    // item ic / 2 writes ciphertext slot oidx[ic / 2] when given (uniform per CTA)
+    const int64_t oc = oidx ? (int64_t)oidx[ic >> 1] * 2 + (ic & 1) : ic;
     uint64_t xa[8], v[8];
     load8(xa, acc + ((int64_t)ic * LK + i) * N + rofs + 8 * j);  // fetched before the transform
 #pragma unroll
@@ -495,13 +521,13 @@ __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(
 #pragma unroll
     for (int e = 0; e < 8; ++e)  // delta < 80q unreduced: (acc + 128q - delta) * P^-1, fully reduced
         v[e] = mul_shoup(xa[e] + 128 * q - v[e], w, ws, q);
-    store8(out + ((int64_t)ic * L + i) * N + rofs + 8 * j, v);
+    store8(out + (oc * L + i) * N + rofs + 8 * j, v);
 }
 
 template <int LC, int LR>
 static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
-                            uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
-                            int add_mask, int n, uint64_t *scratch, cudaStream_t st) {
+                            uint64_t *out, const KsAdd &ad, const int32_t *oidx, int n, uint64_t *scratch,
+                            cudaStream_t st) {
     const int64_t N = c.N, L = c.L, K = c.K, LK = L + K;
     uint64_t *z = scratch;
     uint64_t *ext = z + n * L * N;
@@ -534,7 +560,6 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     {
         constexpr int IT = 2;  // items per thread
         const dim3 g((unsigned)((N / 2 + 255) / 256), (unsigned)(((n + IT - 1) / IT) * LK));
-        const KsAdd ad{add, add_is, add_cs, add_mask};
         switch (c.dnum) {
             case 2: k_ks_mac<2, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
             case 3: k_ks_mac<3, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
@@ -556,7 +581,7 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
         k_ks_moddown_cols<LC, 4><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_final", st);
-    k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, out);
+    k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, out, oidx);
     prof_end(c, r, st);
     return cudaGetLastError();
 }
@@ -568,9 +593,9 @@ bool ks_fused_supported(const Ctx &c) {
 // NTT split of the two passes, N = 2^LC (column pass) x 2^LR (row pass):
 // variant 0 is the default, variant 1 the alternative the autotuner tries.
 static cudaError_t ks_dispatch(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
-                               uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
-                               int add_mask, int m, uint64_t *scratch, cudaStream_t st) {
-#define KS_CALL(LC, LR) ks_fused<LC, LR>(c, a, s, key, out, add, add_is, add_cs, add_mask, m, scratch, st)
+                               uint64_t *out, const KsAdd &ad, int m, uint64_t *scratch, cudaStream_t st,
+                               const int32_t *oidx = nullptr) {
+#define KS_CALL(LC, LR) ks_fused<LC, LR>(c, a, s, key, out, ad, oidx, m, scratch, st)
     const bool alt = c.ks_split == 1;
     switch (c.log2n) {
         case 15: return alt ? KS_CALL(8, 7) : KS_CALL(7, 8);
@@ -631,9 +656,8 @@ cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, c
     for (size_t i0 = 0; i0 < n; i0 += maxn) {
         const int m = (int)std::min(maxn, n - i0);
         KsSrc s{d + i0 * d_stride, d_stride, nullptr, nullptr, 0};
-        cudaError_t e = ks_dispatch(c, a, s, key, out + i0 * 2 * c.L * c.N,
-                                    add ? add + i0 * add_is : nullptr, add_is, add_cs, add_mask, m,
-                                    scratch, st);
+        const KsAdd ad{add ? add + i0 * add_is : nullptr, add_is, add_cs, add_mask};
+        cudaError_t e = ks_dispatch(c, a, s, key, out + i0 * 2 * c.L * c.N, ad, m, scratch, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -650,7 +674,24 @@ cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *
     for (size_t i0 = 0; i0 < n; i0 += maxn) {
         const int m = (int)std::min(maxn, n - i0);
         KsSrc s{nullptr, 0, A + i0 * TS, B + i0 * TS, TS, pk_bits, lw};
-        cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, nullptr, 0, 0, 0, m, scratch, st);
+        cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, KsAdd{nullptr, 0, 0, 0}, m, scratch, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t rotate_fused_inplace(const Ctx &c, uint64_t *cts, const int32_t *idx, const int32_t *perm,
+                                 const uint64_t *gk, size_t n, uint64_t *scratch, cudaStream_t st) {
+    const KsArgs a = ks_args(c);
+    const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
+    const size_t maxn = ks_max_items(c);
+    for (size_t i0 = 0; i0 < n; i0 += maxn) {
+        const int m = (int)std::min(maxn, n - i0);
+        KsSrc s{cts + LN, CT, nullptr, nullptr, 0};
+        s.idx = idx + i0;
+        s.perm = perm;
+        const KsAdd ad{cts, CT, LN, 1, idx + i0, perm};
+        cudaError_t e = ks_dispatch(c, a, s, gk, cts, ad, m, scratch, st, idx + i0);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
