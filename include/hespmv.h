@@ -332,8 +332,8 @@ int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_
                             const uint64_t *X_packed, uint64_t *y_packed, void *stream);
 /* Pipelined form of hespmv_spmv_host_packed for a stream of independent
  * evaluations: enqueues the uploads, the evaluation and the result download
- * and returns without waiting.  Consecutive calls use two staging slots in
- * turn, so a call's uploads run while the previous call computes; a slot is
+ * and returns without waiting.  Consecutive calls use three staging slots in
+ * turn, so a call's uploads run while earlier calls compute; a slot is
  * refilled only once the call that used it before has copied its result out
  * (ordered on the device, the host never blocks).  A_packed, X_packed and
  * y_packed must stay valid and unmodified until `stream` has passed the call

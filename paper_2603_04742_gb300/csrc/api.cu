@@ -907,7 +907,7 @@ void hespmv_destroy(hespmv_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < hespmv_ctx::kSlots; ++s) {
         if (ctx->slot_free[s]) cudaEventDestroy(ctx->slot_free[s]);
         dev_free(ctx, ctx->aio[s]);
     }
@@ -929,7 +929,8 @@ int hespmv_ctx_moduli(const hespmv_ctx *ctx, uint64_t *moduli, uint64_t *psi, ui
 
 int hespmv_ctx_device_bytes(const hespmv_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) return HESPMV_E_INVALID;
-    *bytes = ctx->owned_bytes + ctx->ws_bytes + ctx->io_bytes + ctx->aio_bytes[0] + ctx->aio_bytes[1];
+    *bytes = ctx->owned_bytes + ctx->ws_bytes + ctx->io_bytes;
+    for (size_t b : ctx->aio_bytes) *bytes += b;
     return HESPMV_OK;
 }
 
@@ -1926,7 +1927,7 @@ int hespmv_spmv_host_packed_async(hespmv_ctx *ctx, const hespmv_cssc *m, const u
     CK(cudaMemcpyAsync(y_packed, pY, np * PW * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(ctx->slot_free[s], st));
     ctx->slot_used[s] = true;
-    ctx->aslot = s ^ 1;
+    ctx->aslot = (s + 1) % hespmv_ctx::kSlots;
     return HESPMV_OK;
 }
 

@@ -253,13 +253,14 @@ struct hespmv_ctx {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t join_event = nullptr;
     int upload_groups = 0;  // upload groups of host evaluations (0: default)
-    // pipelined packed host evaluations: two staging slots used in turn; a
+    // pipelined packed host evaluations: kSlots staging slots used in turn; a
     // slot's uploads wait for slot_free[s], recorded when the evaluation that
     // used it last has copied its result out
-    void *aio[2] = {nullptr, nullptr};
-    size_t aio_bytes[2] = {0, 0};
-    cudaEvent_t slot_free[2] = {nullptr, nullptr};
-    bool slot_used[2] = {false, false};
+    static constexpr int kSlots = 3;
+    void *aio[kSlots] = {};
+    size_t aio_bytes[kSlots] = {};
+    cudaEvent_t slot_free[kSlots] = {};
+    bool slot_used[kSlots] = {};
     int aslot = 0;
     // CKKS encoder tables and CRT constants (host, made on first use)
     hespmv::CkksCodec *codec = nullptr;
