@@ -80,16 +80,16 @@ cudaError_t op_ct_pack(const Ctx &c, const uint64_t *in, uint64_t *out, size_t n
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);
-// relinearised HE-Mult of n ciphertext pairs (A + i*2LN, B + i*2LN) with the
-// tensor product fused into the key switch (requires ks_fused_supported);
-// pk_bits > 0: A and B are packed ciphertexts of that many bits per residue
-// (a residue not below its prime sets kErrBadResidue)
 // HE-Rot of n ciphertexts in place, fused (requires ks_fused_supported):
 // slot idx[i] of cts [..][2][L][N] becomes its image under the Galois
 // automorphism of permutation perm (NTT domain), key-switched with gk; the
 // slots must be distinct
 cudaError_t rotate_fused_inplace(const Ctx &c, uint64_t *cts, const int32_t *idx, const int32_t *perm,
                                  const uint64_t *gk, size_t n, uint64_t *scratch, cudaStream_t st);
+// relinearised HE-Mult of n ciphertext pairs (A + i*2LN, B + i*2LN) with the
+// tensor product fused into the key switch (requires ks_fused_supported);
+// pk_bits > 0: A and B are packed ciphertexts of that many bits per residue
+// (a residue not below its prime sets kErrBadResidue)
 cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *B,
                                const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
                                cudaStream_t st, int pk_bits = 0);

@@ -280,6 +280,52 @@ def test_spmv_c3_full_size_parity_and_tolerance():
     assert np.max(np.abs(yhat - yref)) <= 1e-3 * np.max(np.abs(yref))
 
 
+def _uniform_rows_matrix(seed, rows, cols, per_row):
+    """Every row holds exactly per_row non-zeros: all chunks are one column
+    wide (c = 1) when rows fill whole partitions, so no rotation runs."""
+    g = np.random.default_rng(seed)
+    colidx = np.concatenate([np.sort(g.choice(cols, per_row, replace=False)) for _ in range(rows)])
+    vals = g.integers(-15, 16, size=rows * per_row)
+    vals[vals == 0] = 7
+    rowptr = np.arange(rows + 1, dtype=np.int64) * per_row
+    x = g.integers(-15, 16, size=cols)
+    return synth.CSR(rows, cols, rowptr, colidx.astype(np.int32), vals.astype(np.int64)), x
+
+
+def test_spmv_no_rotation_partitions_parity():
+    """A matrix whose chunks are all one column wide (no rotation anywhere)
+    over two partitions: the result matches the oracle's sequential
+    Algorithm 4 bit for bit on the device path, the graph replay and every
+    host-buffer path."""
+    logn, L, K, dnum, t = synth.RING["c1"]
+    A, x = _uniform_rows_matrix(77, 2 * (1 << (logn - 1)), 3000, 5)   # two partitions
+    ctx, orc = make_pair(logn, L, K, dnum, t, seed=1, steps=[])
+    m, y, out, oout = run_spmv_pair(ctx, orc, A, x)
+    assert m.n_rot == 0 and m.n_parts == 2
+    assert list(out) == list(A.matvec(x)) == list(oout)
+    ref = y.download()
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    for _ in range(2):   # capture, then replay
+        assert np.array_equal(ctx.spmv(m, ca, cx).download(), ref)
+    words, _ = ctx.ct_packed_words()
+    pA, pX = ctx.ct_pack(ca.download()), ctx.ct_pack(cx.download())
+    py = np.zeros((m.n_parts, words), dtype=np.uint64)
+    hy = np.zeros_like(ref)
+    for groups in (1, 3, 0):
+        ctx.set_upload_groups(groups)
+        ctx.spmv_host(m, ca.download(), cx.download(), hy)
+        assert np.array_equal(hy, ref), groups
+        ctx.spmv_host_packed(m, pA, pX, py)
+        assert np.array_equal(ctx.ct_unpack(py), ref), groups
+        stream = torch.cuda.Stream()
+        for _ in range(3):
+            ctx.spmv_host_packed_async(m, pA, pX, py, stream=stream)
+        stream.synchronize()
+        assert np.array_equal(ctx.ct_unpack(py), ref), groups
+    ctx.device_status()
+
+
 def test_spmv_host_buffers_and_batched_match():
     logn, L, K, dnum, t = synth.RING["c1"]
     from paper_2603_04742_gb300.api import Context
