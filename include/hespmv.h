@@ -34,6 +34,9 @@
  *    NULL = legacy default stream).  Calls without a stream argument
  *    (keygen, encrypt, decrypt, uploads of keys) synchronise the device
  *    before returning.
+ *  - A context's evaluations share its workspace: evaluations enqueued on
+ *    different streams must not overlap (order them, or use one stream, or
+ *    the server of hespmv_server_*, whose slots have their own workspaces).
  */
 #ifndef HESPMV_H
 #define HESPMV_H
@@ -338,7 +341,8 @@ int hespmv_spmv_host_packed(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_
  * (ordered on the device, the host never blocks).  A_packed, X_packed and
  * y_packed must stay valid and unmodified until `stream` has passed the call
  * (e.g. cudaStreamSynchronize); the uploads run on the context's own copy
- * stream, ordered after the slot's previous evaluation only.  Kernels are
+ * stream, ordered after the slot's previous evaluation only.  Consecutive
+ * calls must use the same stream (the evaluations share the workspace).  Kernels are
  * launched one by one (no graph).  A residue not below its prime is reported
  * by hespmv_device_status, not by this call. */
 int hespmv_spmv_host_packed_async(hespmv_ctx *ctx, const hespmv_cssc *m, const uint64_t *A_packed,
