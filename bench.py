@@ -698,7 +698,7 @@ def main():
         dt_sync = max_over_ranks(time.perf_counter() - t0)
         assert np.array_equal(ctx.ct_unpack(qY).reshape(y.download().shape), y.download())
         # pipelined: each step's upload overlaps the previous step's compute
-        # (two staging slots); every step still uploads its inputs and
+        # (three staging slots); every step still uploads its inputs and
         # downloads its result
         qY[:] = 0
         for _ in range(3):

@@ -403,7 +403,7 @@ def test_spmv_host_packed_matches_device_path():
 
 def test_spmv_host_packed_async_pipeline():
     """Pipelined packed evaluations: calls on two instances in flight at once
-    (both staging slots reused several times, uploads overlapping earlier
+    (every staging slot reused, uploads overlapping earlier
     calls' compute) give the device path's results bit for bit; a bad residue
     shows up in the device status."""
     logn, L, K, dnum, t = synth.RING["c1"]
