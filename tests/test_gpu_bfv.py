@@ -97,6 +97,23 @@ def test_bfv_partitions_and_ragged_batches():
     for p in range(len(ores)):
         assert np.array_equal(gy[p], ores[p]), p
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+    # host-buffer paths: 64-bit words, packed (BFV groups are unpacked by
+    # their own kernel before the tensor), pipelined packed
+    hy = np.zeros_like(gy)
+    ctx.spmv_host(m, ca.download(), cx.download(), hy)
+    assert np.array_equal(hy, gy)
+    words, _ = ctx.ct_packed_words()
+    pA, pX = ctx.ct_pack(ca.download()), ctx.ct_pack(cx.download())
+    py = np.zeros((m.n_parts, words), dtype=np.uint64)
+    ctx.spmv_host_packed(m, pA, pX, py)
+    assert np.array_equal(ctx.ct_unpack(py), gy)
+    py[:] = 0
+    stream = torch.cuda.Stream()
+    for _ in range(4):
+        ctx.spmv_host_packed_async(m, pA, pX, py, stream=stream)
+    stream.synchronize()
+    ctx.device_status()
+    assert np.array_equal(ctx.ct_unpack(py), gy)
 
 
 def test_bfv_c3_stencil_full_size():
