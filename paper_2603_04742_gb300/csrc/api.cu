@@ -654,6 +654,20 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                                           gscr, gs));
                 continue;
             }
+            if (bgv && ks_fused_supported(c) && !pp.pkA) {
+                // chunks of several SpMVs: the fused tensor reads each item's
+                // operands through a table of addresses (in the unused tensor buffer)
+                std::vector<const uint64_t *> ptrs(2 * gn);
+                for (size_t u = 0; u < gn; ++u) {
+                    const size_t ii = all[g0 + u].first, kk = all[g0 + u].second;
+                    ptrs[u] = A[ii] + kk * CT;
+                    ptrs[gn + u] = X[ii] + kk * CT;
+                }
+                const uint64_t **tab = (const uint64_t **)gd;
+                CK(op_write_ptrs(c, tab, ptrs, gs));
+                CK(relin_tensor_fused_ptrs(c, tab, tab + gn, ctx->rlk, prod + g0 * CT, gn, gscr, gs));
+                continue;
+            }
             if (pp.pkA)
                 CK(op_ct_unpack(c, pp.pkA + g0 * pp.pk_words, (uint64_t *)A[0] + g0 * CT,
                                 pp.pkX + g0 * pp.pk_words, (uint64_t *)X[0] + g0 * CT, gn, gs));

@@ -80,6 +80,15 @@ cudaError_t op_ct_pack(const Ctx &c, const uint64_t *in, uint64_t *out, size_t n
 cudaError_t keyswitch_fused(const Ctx &c, const uint64_t *d, int64_t d_stride, const uint64_t *key,
                             uint64_t *out, const uint64_t *add, int64_t add_is, int64_t add_cs,
                             int add_mask, size_t n, uint64_t *scratch, cudaStream_t st);
+// relin_tensor_fused with item i's operands at ta[i] and tb[i] (device
+// tables of ciphertext addresses): HE-Mult groups across several SpMVs
+cudaError_t relin_tensor_fused_ptrs(const Ctx &c, const uint64_t *const *ta, const uint64_t *const *tb,
+                                    const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
+                                    cudaStream_t st);
+// dst[0..n) = ptrs[0..n) (device table of addresses, written on the stream
+// from launch parameters, so a captured graph replays it)
+cudaError_t op_write_ptrs(const Ctx &c, const uint64_t **dst, const std::vector<const uint64_t *> &ptrs,
+                          cudaStream_t st);
 // HE-Rot of n ciphertexts in place, fused (requires ks_fused_supported):
 // slot idx[i] of cts [..][2][L][N] becomes its image under the Galois
 // automorphism of permutation perm (NTT domain), key-switched with gk; the

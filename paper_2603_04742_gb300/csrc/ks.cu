@@ -60,7 +60,19 @@ struct KsSrc {
     int64_t pk_lw = 0;
     const int32_t *idx = nullptr;
     const int32_t *perm = nullptr;
+    // per-item ciphertext addresses (device tables) instead of ta/tb + i*ts:
+    // HE-Mult groups that span several SpMVs of a batched evaluation
+    const uint64_t *const *tap = nullptr;
+    const uint64_t *const *tbp = nullptr;
 };
+
+// the HE-Mult operands of item i
+__device__ __forceinline__ const uint64_t *src_a(const KsSrc &s, int64_t i) {
+    return s.tap ? s.tap[i] : s.ta + i * s.ts;
+}
+__device__ __forceinline__ const uint64_t *src_b(const KsSrc &s, int64_t i) {
+    return s.tbp ? s.tbp[i] : s.tb + i * s.ts;
+}
 
 // residue k of a packed limb; one not below q is reduced and flagged
 __device__ __forceinline__ uint64_t packed_residue(const uint64_t *limb, int64_t k, int W, uint64_t q,
@@ -156,15 +168,15 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
         load8(v, s.d + (int64_t)(s.idx ? s.idx[item] : item) * s.ds + off + 8 * j);
     } else if (s.pk_bits) {  // d2 = a1 * b1 from packed operands
         const int64_t limb = (int64_t)(L + k) * s.pk_lw, c0 = (int64_t)row * M + 8 * j;
-        const uint64_t *pa = s.ta + item * s.ts + limb, *pb = s.tb + item * s.ts + limb;
+        const uint64_t *pa = src_a(s, item) + limb, *pb = src_b(s, item) + limb;
 #pragma unroll
         for (int e = 0; e < 8; ++e)
             v[e] = mul_mod(packed_residue(pa, c0 + e, s.pk_bits, mc.q, a.err),
                            packed_residue(pb, c0 + e, s.pk_bits, mc.q, a.err), mc);
     } else {  // d2 = a1 * b1
         uint64_t x[8], y[8];
-        load8(x, s.ta + item * s.ts + LN + off + 8 * j);
-        load8(y, s.tb + item * s.ts + LN + off + 8 * j);
+        load8(x, src_a(s, item) + LN + off + 8 * j);
+        load8(y, src_b(s, item) + LN + off + 8 * j);
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = mul_mod(x[e], y[e], mc);
     }
@@ -370,24 +382,25 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
     if (l < a.L) {
         ulonglong2 y0 = make_ulonglong2(0, 0), y1 = make_ulonglong2(0, 0);
         uint64_t pm = a.pmont[l];
-        if (s.ta) {
+        if (s.ta || s.tap) {
             ulonglong2 a0, b0, a1, b1;
             if (s.pk_bits) {
                 const uint64_t q = mc.q;
                 const int W = s.pk_bits;
-                const uint64_t *pa0 = s.ta + item * s.ts + (int64_t)l * s.pk_lw;
-                const uint64_t *pb0 = s.tb + item * s.ts + (int64_t)l * s.pk_lw;
+                const uint64_t *pa0 = src_a(s, item) + (int64_t)l * s.pk_lw;
+                const uint64_t *pb0 = src_b(s, item) + (int64_t)l * s.pk_lw;
                 const uint64_t *pa1 = pa0 + (int64_t)a.L * s.pk_lw, *pb1 = pb0 + (int64_t)a.L * s.pk_lw;
                 a0 = make_ulonglong2(packed_residue(pa0, k, W, q, a.err), packed_residue(pa0, k + 1, W, q, a.err));
                 b0 = make_ulonglong2(packed_residue(pb0, k, W, q, a.err), packed_residue(pb0, k + 1, W, q, a.err));
                 a1 = make_ulonglong2(packed_residue(pa1, k, W, q, a.err), packed_residue(pa1, k + 1, W, q, a.err));
                 b1 = make_ulonglong2(packed_residue(pb1, k, W, q, a.err), packed_residue(pb1, k + 1, W, q, a.err));
             } else {
-                const int64_t o = item * s.ts + (int64_t)l * N + k, LN = (int64_t)a.L * N;
-                a0 = *(const ulonglong2 *)(s.ta + o);
-                b0 = *(const ulonglong2 *)(s.tb + o);
-                a1 = *(const ulonglong2 *)(s.ta + o + LN);
-                b1 = *(const ulonglong2 *)(s.tb + o + LN);
+                const int64_t o = (int64_t)l * N + k, LN = (int64_t)a.L * N;
+                const uint64_t *ia = src_a(s, item), *ib = src_b(s, item);
+                a0 = *(const ulonglong2 *)(ia + o);
+                b0 = *(const ulonglong2 *)(ib + o);
+                a1 = *(const ulonglong2 *)(ia + o + LN);
+                b1 = *(const ulonglong2 *)(ib + o + LN);
             }
             own = make_ulonglong2(mul_mod(a1.x, b1.x, mc), mul_mod(a1.y, b1.y, mc));
             // y0, y1 as Montgomery residues (times 2^-64, in [0, 2q)); their
@@ -674,6 +687,23 @@ cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *
     for (size_t i0 = 0; i0 < n; i0 += maxn) {
         const int m = (int)std::min(maxn, n - i0);
         KsSrc s{nullptr, 0, A + i0 * TS, B + i0 * TS, TS, pk_bits, lw};
+        cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, KsAdd{nullptr, 0, 0, 0}, m, scratch, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t relin_tensor_fused_ptrs(const Ctx &c, const uint64_t *const *ta, const uint64_t *const *tb,
+                                    const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
+                                    cudaStream_t st) {
+    const KsArgs a = ks_args(c);
+    const int64_t CT = 2 * (int64_t)c.L * c.N;
+    const size_t maxn = ks_max_items(c);
+    for (size_t i0 = 0; i0 < n; i0 += maxn) {
+        const int m = (int)std::min(maxn, n - i0);
+        KsSrc s{nullptr, 0, nullptr, nullptr, CT};
+        s.tap = ta + i0;
+        s.tbp = tb + i0;
         cudaError_t e = ks_dispatch(c, a, s, rlk, out + i0 * CT, KsAdd{nullptr, 0, 0, 0}, m, scratch, st);
         if (e != cudaSuccess) return e;
     }

@@ -624,6 +624,30 @@ __global__ void k_wait_probe(int *err) {
     mbar_wait(&bar, 0, 1024, err);
 }
 
+// a table of device addresses from launch parameters
+constexpr int kPtrBatch = 256;
+struct PtrBatch {
+    const uint64_t *p[kPtrBatch];
+};
+__global__ void k_write_ptrs(const uint64_t **dst, PtrBatch b, int n) {
+    if ((int)threadIdx.x < n) dst[threadIdx.x] = b.p[threadIdx.x];
+}
+
+cudaError_t op_write_ptrs(const Ctx &c, const uint64_t **dst, const std::vector<const uint64_t *> &ptrs,
+                          cudaStream_t st) {
+    for (size_t i0 = 0; i0 < ptrs.size(); i0 += kPtrBatch) {
+        const int n = (int)std::min<size_t>(kPtrBatch, ptrs.size() - i0);
+        PtrBatch b{};
+        for (int i = 0; i < n; ++i) b.p[i] = ptrs[i0 + i];
+        const int r = prof_begin(c, "k_write_ptrs", st);
+        k_write_ptrs<<<1, kPtrBatch, 0, st>>>(dst + i0, b, n);
+        prof_end(c, r, st);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t op_wait_probe(const Ctx &c, cudaStream_t st) {
     k_wait_probe<<<1, 32, 0, st>>>(c.c->d.err);
     return cudaGetLastError();
