@@ -6,6 +6,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <initializer_list>
 #include <mutex>
 #include <set>
 #include <thread>
@@ -102,10 +103,11 @@ bool upload(hespmv_ctx *ctx, T *&dst, const std::vector<T> &src) {
 uint64_t *workspace(hespmv_ctx *ctx, size_t bytes) {
     if (ctx->ws_bytes >= bytes) return (uint64_t *)ctx->ws;
     cudaDeviceSynchronize();
+    const size_t old = ctx->ws_bytes;  // grow by at least half, so creeping sizes reallocate rarely
     dev_free(ctx, ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
-    size_t want = std::max(bytes, ctx->ws_bytes * 3 / 2);
+    size_t want = std::max(bytes, old * 3 / 2);
     ctx->ws = dev_alloc(ctx, want);
     if (!ctx->ws) {
         ctx->ws = dev_alloc(ctx, bytes);
@@ -210,6 +212,12 @@ int check_ctx(hespmv_ctx *ctx) { return ctx ? HESPMV_OK : HESPMV_E_INVALID; }
 
 // device buffers handed to the key switch are read with 16-byte vector loads
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+// every device buffer of a call: the kernels move 16-byte words through all of them
+bool aligned16(std::initializer_list<const void *> ps) {
+    for (const void *p : ps)
+        if (!aligned16(p)) return false;
+    return true;
+}
 
 // CKKS encoder tables of the context, made on first use
 CkksCodec *get_codec(hespmv_ctx *ctx) {
@@ -2080,6 +2088,7 @@ int hespmv_he_add(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_
                   void *stream) {
     if (!ctx || !a || !b || !out) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16({a, b, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     CK(op_add(view(ctx), a, b, out, 2 * n, (cudaStream_t)stream));
     return HESPMV_OK;
@@ -2089,6 +2098,7 @@ int hespmv_he_tensor(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint
                      void *stream) {
     if (!ctx || !a || !b || !d) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16({a, b, d})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     uint64_t *scr = nullptr;
@@ -2104,7 +2114,7 @@ int hespmv_he_relin(hespmv_ctx *ctx, const uint64_t *d, uint64_t *out, size_t n,
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
-    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (!aligned16({d, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N;
@@ -2120,7 +2130,7 @@ int hespmv_he_mult(hespmv_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64
     if (!ctx || !a || !b || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
-    if (!aligned16(a)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (!aligned16({a, b, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N;
@@ -2137,7 +2147,7 @@ int hespmv_he_rotate(hespmv_ctx *ctx, const uint64_t *ct, int32_t k, uint64_t *o
     if (!ctx || !ct || !out || ct == out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
-    if (!aligned16(ct)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (!aligned16({ct, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const Ctx c = view(ctx);
     const int64_t CT = 2 * (int64_t)c.L * c.N;
@@ -2150,6 +2160,7 @@ int hespmv_he_cmult_mask(hespmv_ctx *ctx, const uint64_t *ct, int32_t r, uint64_
                          void *stream) {
     if (!ctx || !ct || !out || r < 0) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
+    if (!aligned16({ct, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const uint64_t *m = mask_plaintext(ctx, r, (cudaStream_t)stream);
     if (!m) FAIL(HESPMV_E_NOMEM, "mask creation failed");
@@ -2162,7 +2173,7 @@ int hespmv_keyswitch(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois_elt, ui
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     NEED_DEVICE(ctx);
-    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (!aligned16({d, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     const uint64_t *key = ctx->rlk;
     if (galois_elt) {
@@ -2501,7 +2512,7 @@ extern "C" int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint
                                         uint64_t *out, size_t n, void *stream) {
     if (!ctx || !d || !out) return HESPMV_E_INVALID;
     NEED_DEVICE(ctx);
-    if (!aligned16(d)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (!aligned16({d, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
     if (!ctx->have_keys) FAIL(HESPMV_E_INVALID, "keygen first");
     DeviceGuard g(ctx->device);
     const uint64_t *key = ctx->rlk;
@@ -2513,10 +2524,9 @@ extern "C" int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint
     const Ctx c = view(ctx);
     const size_t per = ks_words(c, 1);
     if (n == 0) return HESPMV_OK;
-    if (ks_words(c, n) > kNoAllocScratchWords)
+    if (n > kNoAllocScratchWords / per)  // divided, not multiplied: a huge n cannot wrap past the check
         FAIL(HESPMV_E_INVALID, "hespmv_keyswitch_noalloc: " + std::to_string(n) +
-                                   " ciphertexts need " + std::to_string(ks_words(c, n) * 8) +
-                                   " bytes of scratch, more than the reserved " +
+                                   " ciphertexts need more scratch than the reserved " +
                                    std::to_string(kNoAllocScratchBytes) + "; at most " +
                                    std::to_string(kNoAllocScratchWords / per) +
                                    " per call with these parameters");

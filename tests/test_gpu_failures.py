@@ -52,6 +52,14 @@ def test_bad_arguments_are_refused_before_any_launch():
     rc = lib.hespmv_keyswitch(ctx.h, ctypes.c_void_p(buf.data_ptr() + 8), 0,
                               ctypes.c_void_p(buf.data_ptr()), 1, None)
     assert rc == B.HESPMV_E_INVALID
+    # misaligned output buffer: refused on the host, before any 16-byte store
+    rc = lib.hespmv_keyswitch(ctx.h, ctypes.c_void_p(buf.data_ptr()), 0,
+                              ctypes.c_void_p(buf.data_ptr() + 8), 1, None)
+    assert rc == B.HESPMV_E_INVALID
+    for fn in (lib.hespmv_he_mult, lib.hespmv_he_tensor, lib.hespmv_he_add):
+        rc = fn(ctx.h, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(buf.data_ptr() + 8),
+                ctypes.c_void_p(buf.data_ptr()), 1, None)
+        assert rc == B.HESPMV_E_INVALID
     # a Galois element without a key
     rc = lib.hespmv_keyswitch(ctx.h, ctypes.c_void_p(buf.data_ptr()), 3,
                               ctypes.c_void_p(buf.data_ptr()), 1, None)

@@ -71,3 +71,12 @@ def test_keyswitch_noalloc_rejects_oversized_requests():
                                       ctypes.c_void_p(buf.data_ptr()), 2, None)
     assert rc == B.HESPMV_E_INVALID
     assert b"at most 1 per call" in lib.hespmv_last_error(ctx.h)
+    # a count so large that its scratch size would wrap a 64-bit product
+    rc = lib.hespmv_keyswitch_noalloc(ctx.h, ctypes.c_void_p(buf.data_ptr()), 0,
+                                      ctypes.c_void_p(buf.data_ptr()), 1 << 62, None)
+    assert rc == B.HESPMV_E_INVALID
+    # a misaligned output is refused on the host (the kernels store 16 bytes at a time)
+    rc = lib.hespmv_keyswitch_noalloc(ctx.h, ctypes.c_void_p(buf.data_ptr()), 0,
+                                      ctypes.c_void_p(buf.data_ptr() + 8), 1, None)
+    assert rc == B.HESPMV_E_INVALID
+    assert b"16-byte aligned" in lib.hespmv_last_error(ctx.h)
