@@ -489,6 +489,14 @@ typedef struct hespmv_tuning {
                            (N = 2^LC x 2^LR with LC and LR exchanged or shifted by one)  */
     int32_t rows_tma;   /* fused key switch forward row pass: 0 = one CTA per tile,
                            1 = persistent CTAs fed by bulk asynchronous copies      */
+    int32_t persistent; /* 1: each evaluation of device-resident operands is ONE
+                           persistent launch (Algorithm 1's HE-Mults in groups of
+                           mult_batch (0: 16) chunks, every chunk's Algorithm 4
+                           totalSum chain and masked sum as a program of
+                           dependent tiles taken from a device work queue);
+                           0: staged launches.  Rings with alpha <= 2, K <= 2,
+                           N = 2^11 .. 2^15; not BFV.                              */
+    int32_t persist_blocks; /* CTAs of the persistent launch (0: all resident)     */
     double ms;          /* hespmv_autotune: device time of one evaluation             */
 } hespmv_tuning;
 
@@ -516,9 +524,10 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
  * and replayed afterwards (one launch per evaluation).  enable = 0 makes
  * every evaluation launch its kernels one by one.  Graphs are not used while
  * profiling is enabled.  Default: enabled. */
-/* Device-side waits (the bulk-copy barriers of the key-switch row pass) poll
- * a bounded number of times; one that runs out records an error code in the
- * context and its kernel stops early.  This call reads and clears it:
+/* Device-side waits (the bulk-copy barriers of the key-switch row pass, and
+ * the dependency waits of the persistent evaluation, which give up after 4 s)
+ * are bounded; one that runs out records an error code in the context (1:
+ * copy barrier, 3: persistent dependency) and its kernel stops early.  This call reads and clears it:
  * HESPMV_E_TIMEOUT if set (results since the last check are invalid), else
  * HESPMV_OK.  Decryption calls it first.  Synchronous. */
 int hespmv_device_status(hespmv_ctx *ctx, int32_t *code);
@@ -526,6 +535,12 @@ int hespmv_device_status(hespmv_ctx *ctx, int32_t *code);
  * barrier expecting bytes no copy delivers), which gives up after a few
  * polls; returns HESPMV_E_TIMEOUT and leaves the context usable. */
 int hespmv_selftest_wait_timeout(hespmv_ctx *ctx, int32_t *code);
+/* The same for the persistent evaluation's dependency waits: a launch of one
+ * CTA whose second work tile depends on a third that it can never reach; the
+ * wait gives up after 2 ms, records code 3 and every CTA stops.  Returns
+ * HESPMV_E_TIMEOUT with *code = 3 (read and cleared as above); the context
+ * stays usable.  HESPMV_E_UNSUPPORTED on rings without the persistent form. */
+int hespmv_selftest_persist_timeout(hespmv_ctx *ctx, int32_t *code);
 
 int hespmv_set_graphs(hespmv_ctx *ctx, int32_t enable);
 

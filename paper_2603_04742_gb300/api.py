@@ -296,15 +296,16 @@ class Context:
         return out
 
     # ---- schedule tuning ----
-    def set_tuning(self, mult_batch=0, rot_batch=0, ntt_split=0, rows_tma=0):
-        t = B.hespmv_tuning(mult_batch, rot_batch, ntt_split, rows_tma, 0.0)
+    def set_tuning(self, mult_batch=0, rot_batch=0, ntt_split=0, rows_tma=0, persistent=0,
+                   persist_blocks=0):
+        t = B.hespmv_tuning(mult_batch, rot_batch, ntt_split, rows_tma, persistent, persist_blocks, 0.0)
         self.check(self.lib.hespmv_set_tuning(self.h, byref(t)))
 
     def get_tuning(self):
         t = B.hespmv_tuning()
         self.check(self.lib.hespmv_get_tuning(self.h, byref(t)))
         return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch, "ntt_split": t.ntt_split,
-                "rows_tma": t.rows_tma}
+                "rows_tma": t.rows_tma, "persistent": t.persistent, "persist_blocks": t.persist_blocks}
 
     def tuning_key(self, ms):
         """Cache key of a workload: device, ring and the stage sizes that the
@@ -330,7 +331,8 @@ class Context:
                 table = json.load(f)
             if key in table:
                 b = table[key]["best"]
-                self.set_tuning(b["mult_batch"], b["rot_batch"], b["ntt_split"], b.get("rows_tma", 0))
+                self.set_tuning(b["mult_batch"], b["rot_batch"], b["ntt_split"], b.get("rows_tma", 0),
+                                b.get("persistent", 0), b.get("persist_blocks", 0))
                 return {"best": b, "tried": table[key].get("tried", []), "cached": True}
         n = len(ms)
         arr = c_void_p * n
@@ -346,7 +348,8 @@ class Context:
 
         def as_dict(t):
             return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch,
-                    "ntt_split": t.ntt_split, "rows_tma": t.rows_tma, "ms": t.ms}
+                    "ntt_split": t.ntt_split, "rows_tma": t.rows_tma, "persistent": t.persistent,
+                    "persist_blocks": t.persist_blocks, "ms": t.ms}
         out = {"best": as_dict(best), "tried": [as_dict(tried[i]) for i in range(min(cap, nt.value))],
                "cached": False}
         if cache:
@@ -365,6 +368,11 @@ class Context:
     def selftest_wait_timeout(self):
         code = c_int32()
         rc = self.lib.hespmv_selftest_wait_timeout(self.h, byref(code))
+        return rc, code.value
+
+    def selftest_persist_timeout(self):
+        code = c_int32()
+        rc = self.lib.hespmv_selftest_persist_timeout(self.h, byref(code))
         return rc, code.value
 
     def set_graphs(self, on=True):

@@ -52,7 +52,8 @@ class hespmv_params(ctypes.Structure):
 
 class hespmv_tuning(ctypes.Structure):
     _fields_ = [("mult_batch", c_int32), ("rot_batch", c_int32), ("ntt_split", c_int32),
-                ("rows_tma", c_int32), ("ms", ctypes.c_double)]
+                ("rows_tma", c_int32), ("persistent", c_int32), ("persist_blocks", c_int32),
+                ("ms", ctypes.c_double)]
 
 
 u64p = POINTER(c_uint64)
@@ -91,6 +92,7 @@ SIGNATURES = {
     "hespmv_keys_serialize": (c_int, [c_void_p, c_int32, c_void_p, c_size_t, szp]),
     "hespmv_device_status": (c_int, [c_void_p, i32p]),
     "hespmv_selftest_wait_timeout": (c_int, [c_void_p, i32p]),
+    "hespmv_selftest_persist_timeout": (c_int, [c_void_p, i32p]),
     "hespmv_keys_deserialize": (c_int, [c_void_p, c_void_p, c_size_t]),
     "hespmv_encrypt_real": (c_int, [c_void_p, c_void_p, c_int32, f64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_encode_matrix_plain_real": (c_int, [c_void_p, c_void_p, f64p, POINTER(c_void_p)]),

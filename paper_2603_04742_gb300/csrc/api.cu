@@ -18,10 +18,24 @@
 
 using namespace hespmv;
 
+namespace hespmv {
+// A persistent evaluation program in one device block: the context's
+// key-switch constants, phases, tile offsets, dependencies, key-switch
+// instances, mask jobs, pointer tables and counters (PProg points into it).
+struct PersistPlan {
+    void *blob = nullptr;
+    size_t bytes = 0;
+    PProg prog{};
+    int64_t n_ks = 0, n_phases = 0;  // key switches and phases of the program
+};
+}  // namespace hespmv
+
 namespace {
 
 const uint64_t kSecretStream = 1, kPkAStream = 2, kPkEStream = 3;
 const uint64_t kEncBase = 1ull << 62;
+// a dependency wait of the persistent kernel gives up after this long
+const int64_t kPersistWaitNs = 4000000000ll;
 uint64_t ksk_a_stream(uint64_t kid, uint64_t j) { return 16 + 2 * (kid * 64 + j); }
 
 struct DeviceGuard {
@@ -488,6 +502,8 @@ std::vector<size_t> upload_group_sizes(const hespmv_ctx *ctx, size_t nc, bool pi
 int status_of_code(hespmv_ctx *ctx, int v) {
     if (v == 0) return HESPMV_OK;
     if (v == kErrBadResidue) FAIL(HESPMV_E_INVALID, "a packed input residue was not below its prime");
+    if (v == kErrSchedTimeout)
+        FAIL(HESPMV_E_TIMEOUT, "a dependency wait of the persistent evaluation ran out; its results are incomplete");
     FAIL(HESPMV_E_TIMEOUT, "a device-side wait ran out (code " + std::to_string(v) + ")");
 }
 
@@ -586,6 +602,323 @@ int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, S
         pp.rp = rotation_plan(ctx, n_inst, ms, (int)pp.GR);
         if (!pp.rp) FAIL(HESPMV_E_NOMEM, "rotation schedule upload failed");
     }
+    return HESPMV_OK;
+}
+
+// ------------------------------------------------------------ persistent evaluation
+
+// HE-Mult group of a persistent evaluation: ciphertexts per key switch
+size_t persist_group(const hespmv_ctx *ctx, size_t total) {
+    const size_t G = ctx->tune_G ? ctx->tune_G : 16;
+    return std::max<size_t>(1, std::min(G, std::max<size_t>(total, 1)));
+}
+
+// Workspace words of a persistent evaluation: the HE-Mult products, the
+// key-switch scratch of every HE-Mult group, and per rotating chunk its
+// running sum, its rotation buffer and its own key-switch scratch (the
+// chunks' totalSum chains run concurrently).
+size_t persist_ws_words(const Ctx &c, size_t total, size_t rot, size_t G) {
+    const size_t CT = 2 * (size_t)c.L * c.N;
+    size_t w = total * CT;
+    for (size_t g0 = 0; g0 < total; g0 += G) w += ks_words(c, std::min(G, total - g0));
+    return w + rot * (2 * CT + ks_words(c, 1));
+}
+
+bool persist_usable(const hespmv_ctx *ctx, bool pt_matrix, const uint64_t *hA) {
+    return ctx->persistent && !pt_matrix && !hA && ctx->h.scheme != HESPMV_SCHEME_BFV &&
+           persist_supported(view(ctx));
+}
+
+void persist_free(hespmv_ctx *ctx, PersistPlan *P) {
+    if (!P) return;
+    dev_free(ctx, P->blob);
+    delete P;
+}
+
+void drop_persist_plans(hespmv_ctx *ctx) {
+    if (ctx->persist_plans.empty()) return;
+    cudaDeviceSynchronize();  // no launch may still read a program
+    for (auto &kv : ctx->persist_plans) persist_free(ctx, kv.second);
+    ctx->persist_plans.clear();
+}
+
+// host form of a phase while the program is built
+struct HostPhase {
+    PPhase p{};
+    std::vector<int32_t> deps;
+};
+
+// Program of one evaluation (Algorithm 1 cloud lines and Algorithm 4 for
+// every chunk of every matrix given):
+//  * HE-Mult with relinearisation: one fused key switch per group of G
+//    consecutive chunks (operands through tables of addresses), results in
+//    the product buffers;
+//  * totalSum of each chunk with c > 1: its chain of rotations, one key
+//    switch per Galois element (power-of-two policy: one per set bit, least
+//    significant first), each step's last key switch adding the running sum
+//    (or, for the first step, the product) as it writes the new running sum;
+//  * one masked accumulation per partition into the result.
+// Every phase depends on the phases that write what it reads (a key
+// switch's first stage on the one before it in its chunk's chain, each
+// further stage on the previous stage; a masked sum on the last key switch
+// of each of its chunks).  Phases are ordered by depth, deeper remaining
+// chains first at equal depth, so every dependency precedes its user.
+int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, const uint64_t *const *A,
+                  const uint64_t *const *X, uint64_t *const *Y, uint64_t *ws, size_t G, PersistPlan *P) {
+    const Ctx c = view(ctx);
+    const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
+    std::vector<HostPhase> ph;
+    std::vector<PInst> inst;
+    std::vector<PMask> mask;
+    std::vector<std::vector<const uint64_t *>> tabs;  // address tables, placed in the blob
+    std::vector<size_t> inst_tab, mask_tab;           // first of each one's two tables
+    int32_t gx[7], gy[7];
+    auto add_ks = [&](const PInst &I, std::vector<int32_t> deps0, size_t tab) -> int32_t {
+        persist_stage_tiles(c, I.n, gx, gy);
+        const int32_t ii = (int32_t)inst.size();
+        inst.push_back(I);
+        inst_tab.push_back(tab);
+        int32_t prev = -1;
+        for (int s = 0; s < 7; ++s) {
+            HostPhase h;
+            h.p.kind = kPhIntt + s;
+            h.p.inst = ii;
+            h.p.gx = gx[s];
+            h.p.tiles = gx[s] * gy[s];
+            if (s == 0)
+                h.deps = deps0;
+            else
+                h.deps.assign(1, prev);
+            prev = (int32_t)ph.size();
+            ph.push_back(std::move(h));
+        }
+        return prev;
+    };
+    std::vector<std::pair<size_t, size_t>> all;  // (matrix, chunk)
+    for (size_t i = 0; i < n_inst; ++i)
+        for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
+    const size_t total = all.size();
+    uint64_t *prod = ws, *cur = ws + total * CT;
+    // HE-Mult groups
+    std::vector<int32_t> last_ph(total, -1);
+    for (size_t g0 = 0; g0 < total; g0 += G) {
+        const size_t gn = std::min(G, total - g0);
+        const size_t ta = tabs.size();
+        tabs.emplace_back();
+        tabs.emplace_back();
+        for (size_t u = 0; u < gn; ++u) {
+            const size_t i = all[g0 + u].first, k = all[g0 + u].second;
+            tabs[ta].push_back(A[i] + k * CT);
+            tabs[ta + 1].push_back(X[i] + k * CT);
+        }
+        PInst I{};
+        I.s = KsSrc{nullptr, 0, nullptr, nullptr, CT};
+        I.ad = KsAdd{nullptr, 0, 0, 0};
+        I.key = ctx->rlk;
+        I.out = prod + g0 * CT;
+        I.scratch = cur;
+        I.n = (int32_t)gn;
+        cur += ks_words(c, gn);
+        const int32_t f = add_ks(I, {}, ta);
+        for (size_t u = 0; u < gn; ++u) last_ph[g0 + u] = f;
+    }
+    // totalSum chains
+    std::vector<const uint64_t *> term(total);
+    for (size_t g = 0; g < total; ++g) {
+        const Chunk &ch = ms[all[g].first]->plan.chunks[all[g].second];
+        uint64_t *Pg = prod + g * CT;
+        const uint64_t *w = Pg;  // running sum (Algorithm 4: w = ctV first)
+        std::vector<int32_t> steps;
+        std::vector<uint8_t> orig;
+        total_sum_steps(ch.h, ch.c, steps, orig);
+        if (!steps.empty()) {
+            uint64_t *Wg = cur, *Cg = cur + CT, *scr = cur + 2 * CT;
+            cur += 2 * CT + ks_words(c, 1);
+            int32_t prev = last_ph[g];
+            for (size_t r = 0; r < steps.size(); ++r) {
+                const std::vector<uint32_t> chain = rotation_chain(ctx, steps[r]);
+                const uint64_t *src = orig[r] ? Pg : w;
+                for (size_t j = 0; j < chain.size(); ++j) {
+                    auto kit = ctx->gk.find(chain[j]);
+                    if (kit == ctx->gk.end())
+                        FAIL(HESPMV_E_INVALID, "missing Galois key for element " + std::to_string(chain[j]));
+                    auto pit = ctx->perms.find(chain[j]);
+                    if (pit == ctx->perms.end()) FAIL(HESPMV_E_INVALID, "missing Galois permutation");
+                    const bool last = j + 1 == chain.size();
+                    const uint64_t *in = j == 0 ? src : Cg;
+                    PInst I{};
+                    I.s = KsSrc{in + LN, CT, nullptr, nullptr, 0};
+                    I.s.perm = pit->second;
+                    I.ad = KsAdd{in, CT, LN, 1, nullptr, pit->second};
+                    I.key = kit->second;
+                    I.out = last ? Wg : Cg;
+                    I.post = last ? w : nullptr;
+                    I.scratch = scr;
+                    I.n = 1;
+                    prev = add_ks(I, {prev}, SIZE_MAX);
+                }
+                w = Wg;
+            }
+            last_ph[g] = prev;
+        }
+        term[g] = w;
+    }
+    // masked accumulation per partition
+    const int32_t mask_tiles = (int32_t)(CT / kMaskTileWords);
+    for (size_t i = 0, g0 = 0; i < n_inst; g0 += ms[i]->plan.chunks.size(), ++i) {
+        const Plan &pl = ms[i]->plan;
+        for (size_t p = 0; p < pl.parts.size(); ++p) {
+            const Partition &Pt = pl.parts[p];
+            const size_t tt = tabs.size();
+            tabs.emplace_back();
+            tabs.emplace_back();
+            HostPhase h;
+            for (int32_t q = 0; q < Pt.n_chunks; ++q) {
+                const size_t g = g0 + Pt.chunk0 + q;
+                tabs[tt].push_back(term[g]);
+                tabs[tt + 1].push_back(ctx->masks.at(pl.chunks[Pt.chunk0 + q].h));
+                h.deps.push_back(last_ph[g]);
+            }
+            std::sort(h.deps.begin(), h.deps.end());
+            h.deps.erase(std::unique(h.deps.begin(), h.deps.end()), h.deps.end());
+            PMask J{};
+            J.out = Y[i] + p * CT;
+            J.nterms = Pt.n_chunks;
+            h.p.kind = kPhMask;
+            h.p.inst = (int32_t)mask.size();
+            h.p.gx = mask_tiles;
+            h.p.tiles = mask_tiles;
+            mask.push_back(J);
+            mask_tab.push_back(tt);
+            ph.push_back(std::move(h));
+        }
+    }
+    // order: depth first, then the longer remaining chain, then creation
+    const size_t nph = ph.size();
+    std::vector<int32_t> level(nph, 0), tail(nph, 1), order(nph), pos(nph);
+    for (size_t p = 0; p < nph; ++p)
+        for (int32_t d : ph[p].deps) level[p] = std::max(level[p], level[d] + 1);
+    for (size_t p = nph; p-- > 0;)
+        for (int32_t d : ph[p].deps) tail[d] = std::max(tail[d], tail[p] + 1);
+    for (size_t p = 0; p < nph; ++p) order[p] = (int32_t)p;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (level[a] != level[b]) return level[a] < level[b];
+        if (tail[a] != tail[b]) return tail[a] > tail[b];
+        return a < b;
+    });
+    for (size_t k = 0; k < nph; ++k) pos[order[k]] = (int32_t)k;
+    std::vector<PPhase> fph(nph);
+    std::vector<int32_t> off(nph + 1, 0), deps;
+    int64_t tiles = 0;
+    for (size_t k = 0; k < nph; ++k) {
+        const HostPhase &h = ph[order[k]];
+        fph[k] = h.p;
+        fph[k].dep0 = (int32_t)deps.size();
+        fph[k].ndep = (int32_t)h.deps.size();
+        for (int32_t d : h.deps) {
+            if (pos[d] >= (int32_t)k) FAIL(HESPMV_E_INVALID, "persistent program: a dependency follows its user");
+            deps.push_back(pos[d]);
+        }
+        off[k] = (int32_t)tiles;
+        tiles += h.p.tiles;
+        if (tiles >= (int64_t)INT32_MAX) FAIL(HESPMV_E_UNSUPPORTED, "persistent program: too many tiles");
+    }
+    off[nph] = (int32_t)tiles;
+    // one device block: args | phases | offsets | deps | instances | masks | tables | counters
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    size_t ntab = 0;
+    for (const auto &t : tabs) ntab += t.size();
+    const size_t o_args = 0, o_ph = al(o_args + sizeof(KsArgs)), o_off = al(o_ph + nph * sizeof(PPhase)),
+                 o_dep = al(o_off + (nph + 1) * sizeof(int32_t)), o_inst = al(o_dep + deps.size() * sizeof(int32_t)),
+                 o_mask = al(o_inst + inst.size() * sizeof(PInst)), o_tab = al(o_mask + mask.size() * sizeof(PMask)),
+                 o_ctr = al(o_tab + ntab * sizeof(void *)), bytes = al(o_ctr + (nph + 2) * sizeof(uint32_t));
+    P->blob = dev_alloc(ctx, bytes);
+    if (!P->blob) FAIL(HESPMV_E_NOMEM, "persistent program allocation failed");
+    P->bytes = bytes;
+    char *base = (char *)P->blob;
+    std::vector<size_t> tab_off(tabs.size());
+    std::vector<const uint64_t *> flat;
+    for (size_t t = 0; t < tabs.size(); ++t) {
+        tab_off[t] = o_tab + flat.size() * sizeof(void *);
+        flat.insert(flat.end(), tabs[t].begin(), tabs[t].end());
+    }
+    for (size_t i = 0; i < inst.size(); ++i)
+        if (inst_tab[i] != SIZE_MAX) {
+            inst[i].s.tap = (const uint64_t *const *)(base + tab_off[inst_tab[i]]);
+            inst[i].s.tbp = (const uint64_t *const *)(base + tab_off[inst_tab[i] + 1]);
+        }
+    for (size_t j = 0; j < mask.size(); ++j) {
+        mask[j].terms = (const uint64_t *const *)(base + tab_off[mask_tab[j]]);
+        mask[j].masks = (const uint64_t *const *)(base + tab_off[mask_tab[j] + 1]);
+    }
+    std::vector<char> img(bytes, 0);
+    KsArgs args;
+    persist_args(c, &args);
+    memcpy(img.data() + o_args, &args, sizeof(KsArgs));
+    memcpy(img.data() + o_ph, fph.data(), nph * sizeof(PPhase));
+    memcpy(img.data() + o_off, off.data(), (nph + 1) * sizeof(int32_t));
+    if (!deps.empty()) memcpy(img.data() + o_dep, deps.data(), deps.size() * sizeof(int32_t));
+    if (!inst.empty()) memcpy(img.data() + o_inst, inst.data(), inst.size() * sizeof(PInst));
+    if (!mask.empty()) memcpy(img.data() + o_mask, mask.data(), mask.size() * sizeof(PMask));
+    if (!flat.empty()) memcpy(img.data() + o_tab, flat.data(), flat.size() * sizeof(void *));
+    CK(cudaMemcpy(P->blob, img.data(), bytes, cudaMemcpyHostToDevice));
+    PProg &g = P->prog;
+    g.args = (const KsArgs *)(base + o_args);
+    g.ph = (const PPhase *)(base + o_ph);
+    g.off = (const int32_t *)(base + o_off);
+    g.deps = (const int32_t *)(base + o_dep);
+    g.inst = (const PInst *)(base + o_inst);
+    g.mask = (const PMask *)(base + o_mask);
+    g.ctr = (uint32_t *)(base + o_ctr);
+    g.nph = (int32_t)nph;
+    g.total = (int32_t)tiles;
+    g.wait_ns = kPersistWaitNs;
+    P->n_ks = (int64_t)inst.size();
+    P->n_phases = (int64_t)nph;
+    return HESPMV_OK;
+}
+
+// The program of this evaluation (built on first use; cached per matrices,
+// buffers, workspace, HE-Mult group and NTT split).
+int persist_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, const uint64_t *const *A,
+                 const uint64_t *const *X, uint64_t *const *Y, uint64_t *ws, size_t G, PersistPlan **out) {
+    std::vector<uint64_t> key{(uint64_t)(uintptr_t)ws, (uint64_t)G, (uint64_t)ctx->ks_split};
+    for (size_t i = 0; i < n_inst; ++i) {
+        key.push_back(ms[i]->uid);
+        key.push_back((uint64_t)(uintptr_t)A[i]);
+        key.push_back((uint64_t)(uintptr_t)X[i]);
+        key.push_back((uint64_t)(uintptr_t)Y[i]);
+    }
+    auto it = ctx->persist_plans.find(key);
+    if (it != ctx->persist_plans.end()) {
+        *out = it->second;
+        return HESPMV_OK;
+    }
+    if (ctx->persist_plans.size() >= 64) {  // cached graphs may use the plans
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+        drop_persist_plans(ctx);
+    }
+    PersistPlan *P = new PersistPlan();
+    const int rc = persist_build(ctx, n_inst, ms, A, X, Y, ws, G, P);
+    if (rc) {
+        persist_free(ctx, P);
+        return rc;
+    }
+    ctx->persist_plans[key] = P;
+    *out = P;
+    return HESPMV_OK;
+}
+
+// Launch the program on st: counters cleared, then one persistent launch.
+int persist_enqueue(hespmv_ctx *ctx, const PersistPlan *P, cudaStream_t st) {
+    const Ctx c = view(ctx);
+    Range r("hespmv: persistent evaluation");
+    CK(cudaMemsetAsync(P->prog.ctr, 0, (P->prog.nph + 2) * sizeof(uint32_t), st));
+    const int pr = prof_begin(c, "k_ks_persist", st);
+    CK(persist_launch(c, P->prog, ctx->persist_blocks, st));
+    prof_end(c, pr, st);
     return HESPMV_OK;
 }
 
@@ -753,6 +1086,49 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     return HESPMV_OK;
 }
 
+// Persistent evaluation on `st` (one launch; see persist_build), replayed
+// from a CUDA graph of the memset and the launch when graphs are enabled.
+int spmv_persistent(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, const uint64_t *const *A,
+                    const uint64_t *const *X, uint64_t *const *Y, cudaStream_t st) {
+    const Ctx c = view(ctx);
+    size_t total = 0, rot = 0;
+    for (size_t i = 0; i < n_inst; ++i) {
+        const int rc = prepare_matrix(ctx, ms[i], st);
+        if (rc) return rc;
+        total += ms[i]->plan.chunks.size();
+        for (const Chunk &ch : ms[i]->plan.chunks) rot += ch.c > 1;
+    }
+    const size_t G = persist_group(ctx, total);
+    uint64_t *ws = workspace(ctx, std::max<size_t>(256, persist_ws_words(c, total, rot, G) * 8));
+    if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    PersistPlan *P = nullptr;
+    int rc = persist_plan(ctx, n_inst, ms, A, X, Y, ws, G, &P);
+    if (rc) return rc;
+    const bool profiling = ctx->prof && ctx->prof->on;
+    if (!ctx->use_graphs || profiling) return persist_enqueue(ctx, P, st);
+    const std::vector<uint64_t> key{~0ull, (uint64_t)(uintptr_t)P, (uint64_t)ctx->persist_blocks};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = persist_enqueue(ctx, P, ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = ctx->graphs.emplace(key, exec).first;
+    }
+    CK(cudaGraphLaunch(it->second, st));
+    return HESPMV_OK;
+}
+
 // Evaluate on `st`: replays a CUDA graph of the same evaluation (same
 // matrices, buffers and workspace) when one is cached, else captures one on
 // the context's capture stream; runs eagerly while profiling is on or when
@@ -763,6 +1139,7 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
               const uint64_t *hX = nullptr, const std::vector<size_t> *gsz = nullptr,
               uint64_t *pkA = nullptr, uint64_t *pkX = nullptr, bool pipelined = false,
               cudaEvent_t copy_after = nullptr) {
+    if (persist_usable(ctx, pt_matrix, hA)) return spmv_persistent(ctx, n_inst, ms, A, X, Y, st);
     SpmvPrep pp;
     size_t max_G = 0;
     if (gsz)
@@ -926,6 +1303,7 @@ void hespmv_destroy(hespmv_ctx *ctx) {
         delete kv.second;
     }
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    drop_persist_plans(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -2197,21 +2575,25 @@ namespace {
 void drop_graphs(hespmv_ctx *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
+    drop_persist_plans(ctx);  // the device is idle (callers synchronise first)
 }
 
 struct TuneState {
     size_t G, GR;
     int split, rows_tma;
+    int persistent = 0, blocks = 0;
 };
 
 void apply_tuning(hespmv_ctx *ctx, const TuneState &s) {
     if (ctx->tune_G != s.G || ctx->tune_GR != s.GR || ctx->ks_split != s.split ||
-        ctx->rows_tma != s.rows_tma)
+        ctx->rows_tma != s.rows_tma || ctx->persistent != s.persistent || ctx->persist_blocks != s.blocks)
         drop_graphs(ctx);
     ctx->tune_G = s.G;
     ctx->tune_GR = s.GR;
     ctx->ks_split = s.split;
     ctx->rows_tma = s.rows_tma;
+    ctx->persistent = s.persistent;
+    ctx->persist_blocks = s.blocks;
 }
 
 }  // namespace
@@ -2226,7 +2608,11 @@ int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t) {
         FAIL(HESPMV_E_INVALID, "no such NTT split for this ring");
     if (t->rows_tma < 0 || t->rows_tma > (ks_fused_supported(view(ctx)) ? 1 : 0))
         FAIL(HESPMV_E_INVALID, "no such row-pass form for this ring");
-    const TuneState ts{(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split, t->rows_tma};
+    if (t->persistent < 0 || t->persistent > 1 || (t->persistent && !persist_supported(view(ctx))))
+        FAIL(HESPMV_E_INVALID, "no persistent evaluation for this ring");
+    if (t->persist_blocks < 0) FAIL(HESPMV_E_INVALID, "persist_blocks must be >= 0");
+    const TuneState ts{(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split, t->rows_tma, t->persistent,
+                       t->persist_blocks};
     if (ctx->device >= 0) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
@@ -2256,6 +2642,8 @@ int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t) {
     t->rot_batch = (int32_t)ctx->tune_GR;
     t->ntt_split = ctx->ks_split;
     t->rows_tma = ctx->rows_tma;
+    t->persistent = ctx->persistent;
+    t->persist_blocks = ctx->persist_blocks;
     t->ms = 0;
     return HESPMV_OK;
 }
@@ -2316,6 +2704,14 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         rec.rot_batch = (int32_t)pp.GR;
         rec.ntt_split = s.split;
         rec.rows_tma = s.rows_tma;
+        rec.persistent = s.persistent;
+        rec.persist_blocks = s.blocks;
+        if (s.persistent) {  // one launch: HE-Mult group G, concurrent totalSum chains
+            const size_t Gp = persist_group(ctx, total);
+            pp.need_bytes = persist_ws_words(c, total, rot, Gp) * 8;
+            rec.mult_batch = (int32_t)Gp;
+            rec.rot_batch = 0;
+        }
         if (pp.need_bytes > ctx->ws_bytes && pp.need_bytes - ctx->ws_bytes > free_b / 10 * 9) {
             rec.ms = -1;
             log.push_back(rec);
@@ -2374,6 +2770,16 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         const TuneState base = bestS;
         for (size_t v : grs) consider({base.G, v, base.split, base.rows_tma});
     }
+    // the persistent form: HE-Mult groups of 4, 16, 64 (capped), then the other NTT split
+    if (persist_supported(c) && ctx->h.scheme != HESPMV_SCHEME_BFV) {
+        const TuneState staged = bestS;
+        std::set<size_t> pg;
+        for (size_t v : {4, 16, 64}) pg.insert(std::max<size_t>(1, std::min(v, total)));
+        for (size_t v : pg) consider({v, 0, staged.split, 0, 1, 0});
+        if (bestS.persistent)
+            for (int v = 0; v < ks_split_variants(c); ++v)
+                if (v != bestS.split) consider({bestS.G, 0, v, 0, 1, 0});
+    }
     if (st) cudaStreamSynchronize(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -2388,6 +2794,12 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
     best->rot_batch = (int32_t)bestS.GR;
     best->ntt_split = bestS.split;
     best->rows_tma = bestS.rows_tma;
+    best->persistent = bestS.persistent;
+    best->persist_blocks = bestS.blocks;
+    if (bestS.persistent) {
+        best->mult_batch = (int32_t)persist_group(ctx, total);
+        best->rot_batch = 0;
+    }
     best->ms = best_ms;
     if (n_tried) *n_tried = log.size();
     for (size_t i = 0; tried && i < log.size() && i < cap; ++i) tried[i] = log[i];
@@ -2411,6 +2823,45 @@ int hespmv_selftest_wait_timeout(hespmv_ctx *ctx, int32_t *code) {
     DeviceGuard g(ctx->device);
     CK(op_wait_probe(view(ctx), 0));
     CK(cudaDeviceSynchronize());
+    return hespmv_device_status(ctx, code);
+}
+
+int hespmv_selftest_persist_timeout(hespmv_ctx *ctx, int32_t *code) {
+    if (!ctx) return HESPMV_E_INVALID;
+    NEED_DEVICE(ctx);
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    if (!persist_supported(c)) FAIL(HESPMV_E_UNSUPPORTED, "no persistent evaluation for this ring");
+    // three one-tile phases without work; the second waits for the third,
+    // which the launch's only CTA can never reach: the wait must give up
+    const PPhase ph[3] = {{kPhNone, 0, 1, 1, 0, 0}, {kPhNone, 0, 1, 1, 0, 1}, {kPhNone, 0, 1, 1, 1, 0}};
+    const int32_t off[4] = {0, 1, 2, 3}, deps[1] = {2};
+    KsArgs args;
+    persist_args(c, &args);
+    const size_t o_ph = 256, o_off = o_ph + sizeof(ph), o_dep = o_off + sizeof(off), o_ctr = o_dep + 16,
+                 bytes = o_ctr + 5 * sizeof(uint32_t);
+    std::vector<char> img(bytes, 0);
+    static_assert(sizeof(KsArgs) <= 256, "KsArgs fits its slot");
+    memcpy(img.data(), &args, sizeof(args));
+    memcpy(img.data() + o_ph, ph, sizeof(ph));
+    memcpy(img.data() + o_off, off, sizeof(off));
+    memcpy(img.data() + o_dep, deps, sizeof(deps));
+    char *blob = (char *)dev_alloc(ctx, bytes);
+    if (!blob) FAIL(HESPMV_E_NOMEM, "self-test allocation failed");
+    PProg P{};
+    P.args = (const KsArgs *)blob;
+    P.ph = (const PPhase *)(blob + o_ph);
+    P.off = (const int32_t *)(blob + o_off);
+    P.deps = (const int32_t *)(blob + o_dep);
+    P.ctr = (uint32_t *)(blob + o_ctr);
+    P.nph = 3;
+    P.total = 3;
+    P.wait_ns = 2000000;  // 2 ms
+    cudaError_t e = cudaMemcpy(blob, img.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = persist_launch(c, P, 1, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    dev_free(ctx, blob);
+    if (e != cudaSuccess) FAIL(HESPMV_E_CUDA, std::string("persistent self-test: ") + cudaGetErrorString(e));
     return hespmv_device_status(ctx, code);
 }
 

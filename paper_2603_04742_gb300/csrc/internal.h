@@ -198,6 +198,8 @@ struct RotOp {
     int m = 0;              // items
     int64_t a = -1, b = -1; // offsets of the index lists in d_idx (-1: identity)
 };
+// A persistent evaluation program resident on the device (api.cu builds it).
+struct PersistPlan;
 struct RotPlan {
     int GR = 0;             // group capacity
     std::vector<RotOp> ops;
@@ -240,6 +242,10 @@ struct hespmv_ctx {
     size_t tune_GR = 0;  // totalSum round width: ciphertexts per rotation round
     int ks_split = 0;    // fused key switch: NTT split variant (column/row pass sizes)
     int rows_tma = 0;    // fused key switch: persistent TMA-fed forward row pass
+    int persistent = 0;  // 1: one persistent launch per evaluation (tune_G = its HE-Mult group)
+    int persist_blocks = 0;  // CTAs of the persistent launch (0: every resident CTA)
+    // persistent evaluation programs, keyed by matrices, buffers, workspace and group
+    std::map<std::vector<uint64_t>, hespmv::PersistPlan *> persist_plans;
     // staging for evaluations from host buffers, and the side stream and
     // events that overlap their uploads with the HE-Mult groups
     void *io = nullptr;

@@ -2,6 +2,7 @@
 // encode/decrypt kernels.  All run on the given stream; sizes in words.
 #pragma once
 #include "internal.h"
+#include "persist.h"
 
 namespace hespmv {
 
@@ -102,6 +103,15 @@ cudaError_t rotate_fused_inplace(const Ctx &c, uint64_t *cts, const int32_t *idx
 cudaError_t relin_tensor_fused(const Ctx &c, const uint64_t *A, const uint64_t *B,
                                const uint64_t *rlk, uint64_t *out, size_t n, uint64_t *scratch,
                                cudaStream_t st, int pk_bits = 0);
+// persistent evaluation (ks.cu): rings with N = 2^11 .. 2^15, alpha <= 2, K <= 2
+bool persist_supported(const Ctx &c);
+// one launch of the program P (counters zeroed beforehand), at most
+// max_blocks CTAs (0: every resident CTA of the GPU)
+cudaError_t persist_launch(const Ctx &c, const PProg &P, int max_blocks, cudaStream_t st);
+// the key-switch constants a persistent program keeps a device copy of
+void persist_args(const Ctx &c, KsArgs *out);
+// virtual grid (x, y) of each of the 7 stages of a persistent key switch of n items
+void persist_stage_tiles(const Ctx &c, int n, int32_t gx[7], int32_t gy[7]);
 // x <- x * 2^64 mod q over n_items x (L+K) limbs (keys to Montgomery form)
 cudaError_t op_to_mont(const Ctx &c, uint64_t *x, size_t n_items, cudaStream_t st);
 

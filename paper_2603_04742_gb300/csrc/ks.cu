@@ -25,46 +25,10 @@
 #include "async_copy.cuh"
 #include "kernels.h"
 #include "ntt_core.cuh"
+#include "persist.h"
 
 namespace hespmv {
 
-struct KsArgs {
-    const ModConst *mc;
-    const uint64_t *tw;        // [modulus][4][N]
-    const uint64_t *zc;        // [L][4]  fold constants of step 2
-    const uint64_t *yc;        // [K][4]  fold constants of step 5
-    const uint64_t *modup_mod; // [dnum][alpha][L+K][2]
-    const uint64_t *phat_t;    // [K][L][2]  Phat_k * t mod q_i
-    const uint64_t *pinv;      // [L][2]
-    const uint64_t *pmont;     // [L]     P * 2^64 mod q_i
-    const uint64_t *pmont2;    // [L]     P * 2^128 mod q_i
-    int *err;                  // device error word (bounded waits)
-    int log2n, L, K, dnum, alpha;
-};
-
-// Input of a key switch: d (NTT domain, item stride ds), or, fused with the
-// tensor product of HE-Mult, d = a1 * b1 for ciphertexts a = ta + i*ts,
-// b = tb + i*ts, whose (a0 b0, a0 b1 + a1 b0) is then the addend.
-// With pk_bits > 0, ta and tb hold packed ciphertexts (pk_bits bits per
-// residue, limbs of pk_lw words, ts words per ciphertext), read and checked
-// here instead of in a separate unpack pass.
-// With idx, item i reads slot idx[i] of d (stride ds); with perm, coefficient
-// c of each limb reads coefficient perm[c] (a Galois automorphism in the NTT
-// domain), so a rotation's permutation needs no separate pass.
-struct KsSrc {
-    const uint64_t *d;
-    int64_t ds;
-    const uint64_t *ta, *tb;
-    int64_t ts;
-    int pk_bits = 0;
-    int64_t pk_lw = 0;
-    const int32_t *idx = nullptr;
-    const int32_t *perm = nullptr;
-    // per-item ciphertext addresses (device tables) instead of ta/tb + i*ts:
-    // HE-Mult groups that span several SpMVs of a batched evaluation
-    const uint64_t *const *tap = nullptr;
-    const uint64_t *const *tbp = nullptr;
-};
 
 // the HE-Mult operands of item i
 __device__ __forceinline__ const uint64_t *src_a(const KsSrc &s, int64_t i) {
@@ -89,17 +53,6 @@ __device__ __forceinline__ uint64_t packed_residue(const uint64_t *limb, int64_t
     }
     return v;
 }
-
-// Addend of the key switch's output: component c (add_mask bit c) of
-// add + item * is + c * cs, [L][N] each (item -> idx[item], coefficient
-// c -> perm[c] when given, as for KsSrc).
-struct KsAdd {
-    const uint64_t *p;
-    int64_t is, cs;
-    int mask;
-    const int32_t *idx = nullptr;
-    const int32_t *perm = nullptr;
-};
 
 // (a b + c d) * 2^-64 mod q, left in [0, 2q) (a, b, c, d < q < 2^50, so
 // the 128-bit sum stays below q * 2^64)
@@ -126,18 +79,18 @@ __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, u
 // conversion kernels and the key product stay at 3 CTAs per SM (at 64
 // registers they spill and gain nothing).
 
-// inverse row pass: src (item stride ss, limb k at +k*N) -> dst (stride ds)
+// inverse row pass: src (item stride ss, limb k at +k*N) -> dst (stride ds);
+// tile (bx, by): row block bx of limb by % nl of item by / nl
 template <int LR>
-__global__ __launch_bounds__(kNttThreads, 5) void k_ks_intt_rows(KsArgs a, const uint64_t *src,
-                                                              int64_t ss, uint64_t *dst,
-                                                              int64_t ds, int nl, int prime0) {
+__device__ __forceinline__ void ks_intt_rows_tile(const KsArgs &a, const uint64_t *src, int64_t ss,
+                                                  uint64_t *dst, int64_t ds, int nl, int prime0, int bx,
+                                                  int by, uint64_t *sm) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
-    __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR;
-    const int item = blockIdx.y / nl, k = blockIdx.y - item * nl, prime = prime0 + k;
+    const int item = by / nl, k = by - item * nl, prime = prime0 + k;
     const uint64_t q = a.mc[prime].q;
     const TwPair *itw = (const TwPair *)(a.tw + (int64_t)prime * 4 * N + 2 * N);
-    const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
+    const int t = threadIdx.x, rr = t / P, j = t % P, row = bx * TR + rr;
     const uint64_t *in = src + item * ss + (int64_t)k * N + (int64_t)row * M;
     uint64_t *out = dst + item * ds + (int64_t)k * N + (int64_t)row * M;
     uint64_t v[8];
@@ -147,16 +100,24 @@ __global__ __launch_bounds__(kNttThreads, 5) void k_ks_intt_rows(KsArgs a, const
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
 }
 
+template <int LR>
+__global__ __launch_bounds__(kNttThreads, 5) void k_ks_intt_rows(KsArgs a, const uint64_t *src,
+                                                              int64_t ss, uint64_t *dst,
+                                                              int64_t ds, int nl, int prime0) {
+    __shared__ uint64_t sm[kRowTileWords];
+    ks_intt_rows_tile<LR>(a, src, ss, dst, ds, nl, prime0, blockIdx.x, blockIdx.y, sm);
+}
+
 // first inverse row pass of the key switch: from the input (or a1 * b1)
 template <int LR>
-__global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSrc s, uint64_t *dst) {
+__device__ __forceinline__ void ks_intt_rows_src_tile(const KsArgs &a, const KsSrc &s, uint64_t *dst, int bx,
+                                                      int by, uint64_t *sm) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
-    __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L;
-    const int item = blockIdx.y / L, k = blockIdx.y - item * L;
+    const int item = by / L, k = by - item * L;
     const ModConst mc = a.mc[k];
     const TwPair *itw = (const TwPair *)(a.tw + (int64_t)k * 4 * N + 2 * N);
-    const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
+    const int t = threadIdx.x, rr = t / P, j = t % P, row = bx * TR + rr;
     const int64_t off = (int64_t)k * N + (int64_t)row * M, LN = (int64_t)L * N;
     uint64_t v[8];
     if (s.d && s.perm) {  // rotation: d through the Galois permutation
@@ -186,19 +147,24 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
 }
 
+template <int LR>
+__global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSrc s, uint64_t *dst) {
+    __shared__ uint64_t sm[kRowTileWords];
+    ks_intt_rows_src_tile<LR>(a, s, dst, blockIdx.x, blockIdx.y, sm);
+}
+
 // ModUp of digit jd to every prime outside it, fused with the forward column
 // pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, unreduced:
 // conversion sums below 4 alpha q <= 16q, then 4q per stage)
 template <int LC, int AMAX>
-__global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
-                                                               uint64_t *ext) {
+__device__ __forceinline__ void ks_modup_cols_tile(const KsArgs &a, const uint64_t *z, uint64_t *ext, int bx,
+                                                   int by, uint64_t *sm) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
-    __shared__ uint64_t sm[kNttTile];
     const int N = 1 << a.log2n, C = N >> LC, L = a.L, LK = a.L + a.K;
-    const int item = blockIdx.y / a.dnum, jd = blockIdx.y - item * a.dnum;
+    const int item = by / a.dnum, jd = by - item * a.dnum;
     const int i0 = jd * a.alpha, i1 = min(L, i0 + a.alpha), na = i1 - i0;
     const int t = threadIdx.x, cc = t % TC, j = t / TC;
-    const int64_t cofs = blockIdx.x * TC + cc;
+    const int64_t cofs = (int64_t)bx * TC + cc;
     // the digit's own limbs: inverse column pass of the row-pass output, with
     // N^-1 * Qhat^-1 folded in (coefficients of d times the ModUp factor)
     uint64_t zs[AMAX][8];
@@ -238,26 +204,41 @@ __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_col
     }
 }
 
+template <int LC, int AMAX>
+__global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
+                                                                                 uint64_t *ext) {
+    __shared__ uint64_t sm[kNttTile];
+    ks_modup_cols_tile<LC, AMAX>(a, z, ext, blockIdx.x, blockIdx.y, sm);
+}
+
 // Forward row pass, in place, of every raised limb: ext[item][jd][l] for the
 // primes l outside digit jd (output unreduced, < 80q).
+// tile: row block bx of raised limb l of digit jd of `item` (l outside the digit)
 template <int LR>
-__global__ __launch_bounds__(kNttThreads, 5) void k_ks_rows_fwd(KsArgs a, uint64_t *ext) {
+__device__ __forceinline__ void ks_rows_fwd_tile(const KsArgs &a, uint64_t *ext, int bx, int64_t item, int jd,
+                                                 int l, uint64_t *sm) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
-    __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, LK = a.L + a.K;
-    const int l = blockIdx.y % LK, jd = (blockIdx.y / LK) % a.dnum;
-    const int64_t item = blockIdx.y / (LK * a.dnum);
-    const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
-    if (l >= i0 && l < i1) return;  // the digit's own primes keep d itself
     const uint64_t q = a.mc[l].q;
     const TwPair *tw = (const TwPair *)(a.tw + (int64_t)l * 4 * N);
-    const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
+    const int t = threadIdx.x, rr = t / P, j = t % P, row = bx * TR + rr;
     uint64_t *x = ext + ((item * a.dnum + jd) * LK + l) * N + (int64_t)row * M;
     uint64_t v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = x[Pass<LR>::first(j, e)];
     fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
     store8(x + 8 * j, v);
+}
+
+template <int LR>
+__global__ __launch_bounds__(kNttThreads, 5) void k_ks_rows_fwd(KsArgs a, uint64_t *ext) {
+    __shared__ uint64_t sm[kRowTileWords];
+    const int LK = a.L + a.K;
+    const int l = blockIdx.y % LK, jd = (blockIdx.y / LK) % a.dnum;
+    const int64_t item = blockIdx.y / (LK * a.dnum);
+    const int i0 = jd * a.alpha, i1 = min(a.L, i0 + a.alpha);
+    if (l >= i0 && l < i1) return;  // the digit's own primes keep d itself
+    ks_rows_fwd_tile<LR>(a, ext, blockIdx.x, item, jd, l, sm);
 }
 
 // The same row pass with persistent CTAs walking the 2048-word row tiles:
@@ -359,15 +340,15 @@ cudaError_t rows_fwd_prepare() {
 // DN > 0: dnum known at compile time, every digit's loads issued before the
 // first product; DN = 0: any dnum, one digit at a time.
 template <int DN, int IT>
-__global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc s, KsAdd ad, const uint64_t *ext,
-                                                const uint64_t *key, uint64_t *acc, int n) {
-    // grid: x = coefficient pairs, y = l * ceil(n / IT) + item group; IT
-    // items per thread share the key loads
+__device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, const KsAdd &ad, const uint64_t *ext,
+                                            const uint64_t *key, uint64_t *acc, int n, int bx, int by) {
+    // tiles: x = blocks of 256 coefficient pairs, y = l * ceil(n / IT) + item
+    // group; IT items per thread share the key loads
     const int N = 1 << a.log2n, LK = a.L + a.K;
     const int ng = (n + IT - 1) / IT;
-    const int l = blockIdx.y / ng;
-    const int64_t item0 = (int64_t)(blockIdx.y - l * ng) * IT;
-    const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int l = by / ng;
+    const int64_t item0 = (int64_t)(by - l * ng) * IT;
+    const int64_t k = 2 * ((int64_t)bx * 256 + threadIdx.x);
     if (k >= N) return;
     const ModConst mc = a.mc[l];
 #pragma unroll 1
@@ -461,17 +442,22 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
     }
 }
 
+template <int DN, int IT>
+__global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc s, KsAdd ad, const uint64_t *ext,
+                                                                 const uint64_t *key, uint64_t *acc, int n) {
+    ks_mac_tile<DN, IT>(a, s, ad, ext, key, acc, n, blockIdx.x, blockIdx.y);
+}
+
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
 // with t folded in, fused with the forward column pass: -> dh [n][2][L][N]
 template <int LC, int KMAX>
-__global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
-                                                                 uint64_t *dh) {
+__device__ __forceinline__ void ks_moddown_cols_tile(const KsArgs &a, const uint64_t *acc, uint64_t *dh, int bx,
+                                                     int by, uint64_t *sm) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
-    __shared__ uint64_t sm[kNttTile];
     const int N = 1 << a.log2n, C = N >> LC, L = a.L, K = a.K, LK = L + K;
-    const int ic = blockIdx.y;  // item * 2 + component
+    const int ic = by;  // item * 2 + component
     const int t = threadIdx.x, cc = t % TC, j = t / TC;
-    const int64_t cofs = blockIdx.x * TC + cc;
+    const int64_t cofs = (int64_t)bx * TC + cc;
     // the P limbs: inverse column pass of the row-pass output, with
     // t^-1 * Phat^-1 * N^-1 folded in
     uint64_t ys[KMAX][8];
@@ -508,19 +494,27 @@ __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_c
     }
 }
 
+template <int LC, int KMAX>
+__global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
+                                                                                   uint64_t *dh) {
+    __shared__ uint64_t sm[kNttTile];
+    ks_moddown_cols_tile<LC, KMAX>(a, acc, dh, blockIdx.x, blockIdx.y, sm);
+}
+
 // Forward row pass of delta, then out = (acc - delta) * P^-1 (the addend is
 // already in acc, times P).
+// With `post` (a ciphertext batch like out, read at the same words), its
+// residues are added to the result: w + Rot(x) in one pass.
 template <int LR>
-__global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
-                                                               const uint64_t *dh, uint64_t *out,
-                                                               const int32_t *oidx) {
+__device__ __forceinline__ void ks_rows_final_tile(const KsArgs &a, const uint64_t *acc, const uint64_t *dh,
+                                                   uint64_t *out, const int32_t *oidx, const uint64_t *post,
+                                                   int bx, int by, uint64_t *sm) {
     constexpr int M = 1 << LR, TR = kNttTile / M, P = M / 8;
-    __shared__ uint64_t sm[kRowTileWords];
     const int N = 1 << a.log2n, n1 = a.log2n - LR, L = a.L, LK = L + a.K;
-    const int ic = blockIdx.y / L, i = blockIdx.y - ic * L;  // ic = item * 2 + component
+    const int ic = by / L, i = by - ic * L;  // ic = item * 2 + component
     const uint64_t q = a.mc[i].q;
     const TwPair *tw = (const TwPair *)(a.tw + (int64_t)i * 4 * N);
-    const int t = threadIdx.x, rr = t / P, j = t % P, row = blockIdx.x * TR + rr;
+    const int t = threadIdx.x, rr = t / P, j = t % P, row = bx * TR + rr;
     const int64_t rofs = (int64_t)row * M;
     const uint64_t *src = dh + ((int64_t)ic * L + i) * N + rofs;
     // item ic / 2 writes ciphertext slot oidx[ic / 2] when given (uniform per CTA)
@@ -534,7 +528,22 @@ __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(
 #pragma unroll
     for (int e = 0; e < 8; ++e)  // delta < 80q unreduced: (acc + 128q - delta) * P^-1, fully reduced
         v[e] = mul_shoup(xa[e] + 128 * q - v[e], w, ws, q);
-    store8(out + (oc * L + i) * N + rofs + 8 * j, v);
+    const int64_t o = (oc * L + i) * N + rofs + 8 * j;
+    if (post) {
+        uint64_t pv[8];
+        load8(pv, post + o);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = add_mod(v[e], pv[e], q);
+    }
+    store8(out + o, v);
+}
+
+template <int LR>
+__global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(KsArgs a, const uint64_t *acc,
+                                                                               const uint64_t *dh, uint64_t *out,
+                                                                               const int32_t *oidx) {
+    __shared__ uint64_t sm[kRowTileWords];
+    ks_rows_final_tile<LR>(a, acc, dh, out, oidx, nullptr, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int LC, int LR>
@@ -599,6 +608,232 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Persistent evaluation (the program structures are described in persist.h).
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+static_assert(kMaskTileWords == 2 * 4 * kNttThreads, "a mask tile is 2 x 4 words per thread");
+
+// masked accumulation, one 2048-word tile of the output ciphertext [2][L][N]:
+// out = sum_k terms[k] * masks[k], the 128-bit sums reduced (Montgomery) once
+// per 4096 terms; each thread takes 2 x 4 consecutive words
+__device__ __forceinline__ void mask_tile(const KsArgs &a, const PMask &J, int bx) {
+    const int64_t LN = (int64_t)a.L << a.log2n;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int64_t i0 = (int64_t)bx * kMaskTileWords + half * (kMaskTileWords / 2) + 4 * threadIdx.x;
+        const int64_t r0 = i0 % LN;
+        const ModConst &mc = a.mc[(int)(r0 >> a.log2n)];
+        const uint64_t q = mc.q, qneg = mc.qneg;
+        uint64_t s[4] = {0, 0, 0, 0};
+        for (int k0 = 0; k0 < J.nterms; k0 += 4096) {
+            const int k1 = min(J.nterms, k0 + 4096);
+            uint64_t hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+            for (int k = k0; k < k1; ++k) {
+                const ulonglong2 *w = (const ulonglong2 *)(J.terms[k] + i0);
+                const ulonglong2 *m = (const ulonglong2 *)(J.masks[k] + r0);
+                const ulonglong2 w0 = w[0], w1 = w[1], m0 = m[0], m1 = m[1];
+                const uint64_t wv[4] = {w0.x, w0.y, w1.x, w1.y}, mv[4] = {m0.x, m0.y, m1.x, m1.y};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint64_t pl = wv[e] * mv[e];
+                    lo[e] += pl;
+                    hi[e] += __umul64hi(wv[e], mv[e]) + (lo[e] < pl);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s[e] = add_mod(s[e], redc(hi[e], lo[e], q, qneg), q);
+        }
+        ulonglong2 *o = (ulonglong2 *)(J.out + i0);
+        o[0] = make_ulonglong2(s[0], s[1]);
+        o[1] = make_ulonglong2(s[2], s[3]);
+    }
+}
+
+// raised limb e (0 <= e < dnum (L+K) - L, own primes skipped) -> (digit, prime)
+__device__ __forceinline__ void raised_limb(const KsArgs &a, int e, int &jd, int &l) {
+    const int LK = a.L + a.K;
+    for (jd = 0; jd < a.dnum; ++jd) {
+        const int i0 = jd * a.alpha, own = max(0, min(a.L, i0 + a.alpha) - i0);
+        if (e < LK - own) {
+            l = e < i0 ? e : e + own;
+            return;
+        }
+        e -= LK - own;
+    }
+    jd = a.dnum - 1;
+    l = LK - 1;  // not reached for e in range
+}
+
+// Each tile kind runs in a function of its own (not inlined): the register
+// allocation of one kind does not constrain another's, so the persistent
+// kernel needs no more registers than its largest stage.
+struct PScratch {
+    uint64_t *z, *ext, *acc, *dh;
+};
+__device__ __forceinline__ PScratch persist_scratch(const KsArgs &a, const PInst &I) {
+    const int64_t N = 1 << a.log2n, L = a.L, LK = a.L + a.K, n = I.n;
+    PScratch r;
+    r.z = I.scratch;
+    r.ext = r.z + n * L * N;
+    r.acc = r.ext + n * a.dnum * LK * N;
+    r.dh = r.acc + n * 2 * LK * N;
+    return r;
+}
+
+template <int LR>
+__device__ __noinline__ void pt_intt(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    ks_intt_rows_src_tile<LR>(a, I.s, persist_scratch(a, I).z, bx, by, sm);
+}
+template <int LC>
+__device__ __noinline__ void pt_modup(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    const PScratch w = persist_scratch(a, I);
+    ks_modup_cols_tile<LC, 2>(a, w.z, w.ext, bx, by, sm);
+}
+template <int LR>
+__device__ __noinline__ void pt_rows_fwd(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    const int ext_limbs = a.dnum * (a.L + a.K) - a.L;
+    const int item = by / ext_limbs;
+    int jd, l;
+    raised_limb(a, by - item * ext_limbs, jd, l);
+    ks_rows_fwd_tile<LR>(a, persist_scratch(a, I).ext, bx, item, jd, l, sm);
+}
+__device__ __noinline__ void pt_mac(const KsArgs &a, const PInst &I, int bx, int by) {
+    const PScratch w = persist_scratch(a, I);
+    ks_mac_tile<0, 2>(a, I.s, I.ad, w.ext, I.key, w.acc, I.n, bx, by);
+}
+template <int LR>
+__device__ __noinline__ void pt_intt_p(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    const int64_t LN = (int64_t)a.L << a.log2n, LKN = (int64_t)(a.L + a.K) << a.log2n;
+    uint64_t *acc = persist_scratch(a, I).acc;
+    ks_intt_rows_tile<LR>(a, acc + LN, LKN, acc + LN, LKN, a.K, a.L, bx, by, sm);
+}
+template <int LC>
+__device__ __noinline__ void pt_moddown(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    const PScratch w = persist_scratch(a, I);
+    ks_moddown_cols_tile<LC, 2>(a, w.acc, w.dh, bx, by, sm);
+}
+template <int LR>
+__device__ __noinline__ void pt_final(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+    const PScratch w = persist_scratch(a, I);
+    ks_rows_final_tile<LR>(a, w.acc, w.dh, I.out, I.oidx, I.post, bx, by, sm);
+}
+__device__ __noinline__ void pt_mask(const KsArgs &a, const PMask &J, int bx) { mask_tile(a, J, bx); }
+
+template <int LC, int LR>
+__device__ __forceinline__ void persist_tile(const KsArgs &a, const PProg &P, int kind, int inst, int bx, int by,
+                                             uint64_t *sm) {
+    switch (kind) {
+        case kPhIntt: pt_intt<LR>(a, P.inst[inst], bx, by, sm); break;
+        case kPhModUp: pt_modup<LC>(a, P.inst[inst], bx, by, sm); break;
+        case kPhRowsFwd: pt_rows_fwd<LR>(a, P.inst[inst], bx, by, sm); break;
+        case kPhMac: pt_mac(a, P.inst[inst], bx, by); break;
+        case kPhInttP: pt_intt_p<LR>(a, P.inst[inst], bx, by, sm); break;
+        case kPhModDown: pt_moddown<LC>(a, P.inst[inst], bx, by, sm); break;
+        case kPhFinal: pt_final<LR>(a, P.inst[inst], bx, by, sm); break;
+        case kPhMask: pt_mask(a, P.mask[inst], bx); break;
+        default: break;  // kPhNone
+    }
+}
+
+template <int LC, int LR>
+__global__ __launch_bounds__(kNttThreads, 3) void k_ks_persist(PProg P) {
+    const KsArgs &a = *P.args;  // in global memory: tile functions take it by reference
+    __shared__ __align__(16) uint64_t sm[kRowTileWords];
+    __shared__ int s_t, s_p;
+    uint32_t *const next = P.ctr + P.nph, *const stop = P.ctr + P.nph + 1;
+    int p = 0;  // phase of this CTA's last tile: tiles are taken in increasing order
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = -1;
+            if (*(volatile uint32_t *)stop == 0) {
+                t = (int)atomicAdd(next, 1u);
+                if (t >= P.total) t = -1;
+            }
+            if (t >= 0) {
+                int lo = p, hi = P.nph - 1;  // last phase whose first tile is <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (P.off[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                p = lo;
+                const PPhase &ph = P.ph[p];
+                const uint64_t t0 = global_ns();
+                for (int d = 0; d < ph.ndep && t >= 0; ++d) {
+                    const int q = P.deps[ph.dep0 + d];
+                    const uint32_t need = (uint32_t)(P.off[q + 1] - P.off[q]);
+                    for (uint32_t spin = 0; ld_acquire_u32(P.ctr + q) < need; ++spin) {
+                        if (*(volatile uint32_t *)stop) {
+                            t = -1;
+                            break;
+                        }
+                        if (global_ns() - t0 > (uint64_t)P.wait_ns) {
+                            atomicExch(a.err, kErrSchedTimeout);
+                            atomicExch(stop, 1u);
+                            t = -1;
+                            break;
+                        }
+                        __nanosleep(spin < 16 ? 64 : 512);
+                    }
+                }
+                __threadfence();  // as a grid barrier does after its wait
+            }
+            s_t = t;
+            s_p = p;
+        }
+        __syncthreads();
+        const int t = s_t;
+        if (t < 0) break;
+        p = s_p;
+        const PPhase &ph = P.ph[p];
+        const int local = t - P.off[p], gx = ph.gx;
+        persist_tile<LC, LR>(a, P, ph.kind, ph.inst, local % gx, local / gx, sm);
+        __syncthreads();  // every thread's writes of the tile precede the count
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(P.ctr + p, 1u);
+        }
+    }
+}
+
+// resident CTAs of the persistent kernel on the whole GPU, per NTT split
+// (set by ks_prepare, outside any stream capture)
+template <int LC, int LR>
+int &persist_blocks() {
+    static int blocks = 152 * 3;
+    return blocks;
+}
+
+template <int LC, int LR>
+cudaError_t persist_prepare() {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ks_persist<LC, LR>, kNttThreads, 0)))
+        return e;
+    persist_blocks<LC, LR>() = std::max(1, per_sm) * std::max(1, sms);
+    return cudaSuccess;
+}
+
+template <int LC, int LR>
+static cudaError_t persist_run(const PProg &P, int max_blocks, cudaStream_t st) {
+    int grid = std::min(P.total, persist_blocks<LC, LR>());
+    if (max_blocks > 0) grid = std::min(grid, max_blocks);
+    k_ks_persist<LC, LR><<<std::max(1, grid), kNttThreads, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
 bool ks_fused_supported(const Ctx &c) {
     return c.log2n >= 11 && c.log2n <= 15 && c.alpha <= 4 && c.K <= 4;
 }
@@ -625,14 +860,21 @@ int ks_split_variants(const Ctx &c) { return ks_fused_supported(c) ? 2 : 1; }
 
 cudaError_t ks_prepare(const Ctx &c) {
     if (!ks_fused_supported(c)) return cudaSuccess;
-    switch (c.log2n) {  // the row-pass sizes of both NTT splits
-        case 15: { cudaError_t e = rows_fwd_prepare<8>(); return e ? e : rows_fwd_prepare<7>(); }
-        case 14: { cudaError_t e = rows_fwd_prepare<7>(); return e ? e : rows_fwd_prepare<8>(); }
-        case 13: { cudaError_t e = rows_fwd_prepare<7>(); return e ? e : rows_fwd_prepare<6>(); }
-        case 12: { cudaError_t e = rows_fwd_prepare<6>(); return e ? e : rows_fwd_prepare<7>(); }
-        case 11: { cudaError_t e = rows_fwd_prepare<6>(); return e ? e : rows_fwd_prepare<5>(); }
-        default: return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    switch (c.log2n) {  // the row-pass sizes of both NTT splits, and the persistent kernel's
+        case 15: (e = rows_fwd_prepare<8>()) || (e = rows_fwd_prepare<7>()) ||
+                 (e = persist_prepare<7, 8>()) || (e = persist_prepare<8, 7>()); break;
+        case 14: (e = rows_fwd_prepare<7>()) || (e = rows_fwd_prepare<8>()) ||
+                 (e = persist_prepare<7, 7>()) || (e = persist_prepare<6, 8>()); break;
+        case 13: (e = rows_fwd_prepare<7>()) || (e = rows_fwd_prepare<6>()) ||
+                 (e = persist_prepare<6, 7>()) || (e = persist_prepare<7, 6>()); break;
+        case 12: (e = rows_fwd_prepare<6>()) || (e = rows_fwd_prepare<7>()) ||
+                 (e = persist_prepare<6, 6>()) || (e = persist_prepare<5, 7>()); break;
+        case 11: (e = rows_fwd_prepare<6>()) || (e = rows_fwd_prepare<5>()) ||
+                 (e = persist_prepare<5, 6>()) || (e = persist_prepare<6, 5>()); break;
+        default: break;
     }
+    return e;
 }
 
 static KsArgs ks_args(const Ctx &c) {
@@ -654,6 +896,47 @@ static KsArgs ks_args(const Ctx &c) {
     a.dnum = c.dnum;
     a.alpha = c.alpha;
     return a;
+}
+
+// key-switch arguments of the context, for the persistent program (which keeps a
+// copy in device memory)
+void persist_args(const Ctx &c, KsArgs *out) { *out = ks_args(c); }
+
+bool persist_supported(const Ctx &c) { return ks_fused_supported(c) && c.alpha <= 2 && c.K <= 2; }
+
+cudaError_t persist_launch(const Ctx &c, const PProg &P, int max_blocks, cudaStream_t st) {
+    if (!persist_supported(c) || !P.args) return cudaErrorInvalidValue;
+    const bool alt = c.ks_split == 1;
+    switch (c.log2n) {
+        case 15: return alt ? persist_run<8, 7>(P, max_blocks, st) : persist_run<7, 8>(P, max_blocks, st);
+        case 14: return alt ? persist_run<6, 8>(P, max_blocks, st) : persist_run<7, 7>(P, max_blocks, st);
+        case 13: return alt ? persist_run<7, 6>(P, max_blocks, st) : persist_run<6, 7>(P, max_blocks, st);
+        case 12: return alt ? persist_run<5, 7>(P, max_blocks, st) : persist_run<6, 6>(P, max_blocks, st);
+        case 11: return alt ? persist_run<6, 5>(P, max_blocks, st) : persist_run<5, 6>(P, max_blocks, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// tiles of each stage of a persistent key switch of n items, in stage order
+void persist_stage_tiles(const Ctx &c, int n, int32_t gx[7], int32_t gy[7]) {
+    const bool alt = c.ks_split == 1;
+    int LC = 0;
+    switch (c.log2n) {
+        case 15: LC = alt ? 8 : 7; break;
+        case 14: LC = alt ? 6 : 7; break;
+        case 13: LC = alt ? 7 : 6; break;
+        case 12: LC = alt ? 5 : 6; break;
+        default: LC = alt ? 6 : 5; break;
+    }
+    const int LR = c.log2n - LC, N = c.N, LK = c.L + c.K;
+    const int gc = (N >> LC) / (kNttTile >> LC), gr = (N >> LR) / (kNttTile >> LR);
+    const int ext = c.dnum * LK - c.L;
+    const int32_t x[7] = {gr, gc, gr, (N / 2 + 255) / 256, gr, gc, gr};
+    const int32_t y[7] = {n * c.L, n * c.dnum, n * ext, ((n + 1) / 2) * LK, n * 2 * c.K, 2 * n, 2 * n * c.L};
+    for (int i = 0; i < 7; ++i) {
+        gx[i] = x[i];
+        gy[i] = y[i];
+    }
 }
 
 // grid.y of the widest launch is n * dnum * (L+K): items per launch

@@ -159,19 +159,27 @@ def test_server_needs_a_device_context():
 
 def test_tuning_round_trip_and_validation():
     ctx = host_ctx("c3")
-    assert ctx.get_tuning() == {"mult_batch": 0, "rot_batch": 0, "ntt_split": 0, "rows_tma": 0}
+    zero = {"mult_batch": 0, "rot_batch": 0, "ntt_split": 0, "rows_tma": 0, "persistent": 0,
+            "persist_blocks": 0}
+    assert ctx.get_tuning() == zero
     ctx.set_tuning(8, 16, 1, 1)
-    assert ctx.get_tuning() == {"mult_batch": 8, "rot_batch": 16, "ntt_split": 1, "rows_tma": 1}
-    for bad in [(-1, 0, 0), (0, -2, 0), (0, 0, 2), (5000, 0, 0), (0, 0, 0, 2)]:
+    want = dict(zero, mult_batch=8, rot_batch=16, ntt_split=1, rows_tma=1)
+    assert ctx.get_tuning() == want
+    for bad in [(-1, 0, 0), (0, -2, 0), (0, 0, 2), (5000, 0, 0), (0, 0, 0, 2), (0, 0, 0, 0, 2),
+                (0, 0, 0, 0, 1, -1)]:
         with pytest.raises(B.HespmvError) as e:
             ctx.set_tuning(*bad)
         assert e.value.code == B.HESPMV_E_INVALID
-    assert ctx.get_tuning() == {"mult_batch": 8, "rot_batch": 16, "ntt_split": 1, "rows_tma": 1}
+    assert ctx.get_tuning() == want
+    ctx.set_tuning(16, 0, 0, 0, 1, 7)   # the persistent form (alpha = 2, K = 2: supported)
+    assert ctx.get_tuning() == dict(zero, mult_batch=16, persistent=1, persist_blocks=7)
     small = Context(10, 3, 1, 3, 40961, device=-1, torch_alloc=False)   # unfused key switch
     with pytest.raises(B.HespmvError):
         small.set_tuning(0, 0, 1)
     with pytest.raises(B.HespmvError):
         small.set_tuning(0, 0, 0, 1)
+    with pytest.raises(B.HespmvError):
+        small.set_tuning(0, 0, 0, 0, 1)   # no persistent form below N = 2^11
 
 
 def test_autotune_needs_a_device():

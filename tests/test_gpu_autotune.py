@@ -50,9 +50,10 @@ def test_autotune_results_identical_and_cached(logn, tmp_path):
     assert res["best"]["ms"] == min(r["ms"] for r in timed)
     assert {r["ntt_split"] for r in timed} == {0, 1}
     assert {r["rows_tma"] for r in timed} == {0, 1}
+    assert {r["persistent"] for r in timed} == {0, 1}
     # every schedule timed gives the same ciphertexts
     for r in timed:
-        ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"])
+        ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"])
         ys = ctx.spmv_batched(ms, As, Xs)
         torch.cuda.synchronize()
         for y, z in zip(ys, ref_bytes):
@@ -63,6 +64,7 @@ def test_autotune_results_identical_and_cached(logn, tmp_path):
     assert res2["cached"] and res2["best"] == res["best"]
     b = res["best"]
     assert ctx.get_tuning() == {"mult_batch": b["mult_batch"], "rot_batch": b["rot_batch"],
-                                "ntt_split": b["ntt_split"], "rows_tma": b["rows_tma"]}
+                                "ntt_split": b["ntt_split"], "rows_tma": b["rows_tma"],
+                                "persistent": b["persistent"], "persist_blocks": b["persist_blocks"]}
     ctx.device_status()
     assert os.path.exists(cache)

@@ -95,6 +95,14 @@ def test_batched_ring_parity(batched_ring):
         assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
     # the plain per-instance calls too
     _assert_equal_results([ctx.spmv(m, a, x) for m, a, x in zip(ms, As, Xs)], want, "plain")
+    # one persistent launch for the whole batch (HE-Mult groups of 16, then of 1)
+    try:
+        for G in (16, 1):
+            ctx.set_tuning(G, 0, 0, 0, 1)
+            _assert_equal_results(ctx.spmv_batched(ms, As, Xs), want, ("persistent", G))
+    finally:
+        ctx.set_tuning(0, 0, 0, 0)
+    ctx.device_status()
 
 
 def test_batched_ring_every_autotuned_schedule_matches_oracle(batched_ring):
@@ -104,7 +112,7 @@ def test_batched_ring_every_autotuned_schedule_matches_oracle(batched_ring):
     assert len(timed) >= 3
     try:
         for r in timed:
-            ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"])
+            ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"])
             ys = ctx.spmv_batched(ms, As, Xs)
             torch.cuda.synchronize()
             _assert_equal_results(ys, want, r)
@@ -144,6 +152,13 @@ def test_serving_ring_rotations_parity(serving_ring):
     _assert_equal_results([y], want[:1], "c>=3 at N=2^15")
     A, x = insts[0]
     assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+    # the persistent launch: the chunks' rotation chains run concurrently
+    try:
+        ctx.set_tuning(0, 0, 0, 0, 1)
+        _assert_equal_results([ctx.spmv(m, As[0], Xs[0])], want[:1], "persistent at N=2^15")
+    finally:
+        ctx.set_tuning(0, 0, 0, 0)
+    ctx.device_status()
 
 
 def test_serving_ring_served_mix_matches_oracle(serving_ring):
