@@ -40,13 +40,13 @@ CONFIGS = {
 }
 # ALU roofline of a 64-bit modular product: a Shoup product needs 10 32x32-bit
 # partial products (3 + 3 for two low halves, 4 for a high half), all on the
-# heavy multiply pipe, which completes 32 of them per clock per SM; 152 SMs at
-# the 2070 MHz maximum clock.  (A microbenchmark of independent Shoup chains
-# reaches 1.01 T/s with that pipe 94% busy.)
+# heavy multiply pipe, which completes 32 of them per clock per SM (half of the
+# SM's 128 FP32 lanes); times the SM count (device properties) and the maximum
+# SM clock (MEASURED_PEAKS.json).  (A microbenchmark of independent Shoup
+# chains reaches 1.01 T/s with that pipe 94% busy.)
 IMAD_PER_SM_CLK = 32
-SMS = 152
-SM_MAX_MHZ = 2070.0
 IMAD_PER_MULMOD = 10
+FALLBACK_SM_MAX_MHZ = 2070.0   # the GB300's maximum SM clock, when no measured file exists
 KS_SOURCES = ["paper_2603_04742_gb300/csrc/ks.cu", "paper_2603_04742_gb300/csrc/ntt_core.cuh",
               "paper_2603_04742_gb300/csrc/modarith.cuh"]
 
@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="c3: skip the batched, serving, rotation and boundary-call blocks")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="serving block of the default run: Poisson requests")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--scheme", default="bgv", choices=["bgv", "bfv", "ckks"],
@@ -119,6 +123,21 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def alu_peak():
+    """(mulmod/s, description): SMs x heavy-IMAD/clk x max SM clock / IMADs
+    per Shoup product."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks, kind = measured_peaks()
+    mhz = peaks.get("sm_max_mhz")
+    src = "%s sm_max_mhz" % kind
+    if not mhz:
+        mhz, src = FALLBACK_SM_MAX_MHZ, "nominal maximum clock"
+    rate = sms * IMAD_PER_SM_CLK * float(mhz) * 1e6 / IMAD_PER_MULMOD
+    return rate, ("derived: %d SMs (device properties) x %d heavy-IMAD/clk x %.0f MHz (%s) / %d per "
+                  "Shoup mulmod" % (sms, IMAD_PER_SM_CLK, float(mhz), src, IMAD_PER_MULMOD))
 
 
 class Clocks:
@@ -291,6 +310,91 @@ class OracleSample:
         return time.perf_counter() - t0
 
 
+def _allcores_worker(w, nw, A, x, ring, seeds, go, out):
+    """Worker w of nw: the oracle's cloud evaluation (HE-Mult with
+    relinearisation, totalSum, mask product, partial sum per partition) of
+    chunks w, w + nw, ...; keys and encryptions are made first, the
+    evaluation starts when `go` is set and its end time (the system's
+    monotonic clock) is reported with the partial sums."""
+    from oracle import spmv as S
+    from oracle.bgv import Oracle
+    from oracle.params import Params
+    logn, L, K, dnum, t = ring
+    orc = Oracle(Params(log2n=logn, L=L, K=K, dnum=dnum, t=t))
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    chunks = plan.chunks
+    part_of = [p for p, part in enumerate(plan.parts) for _ in part.chunks]
+    sel = [i for i in range(len(chunks)) if i % nw == w]
+    gels = set()
+    for i in sel:
+        for k in S.rotation_steps(chunks[i].c, chunks[i].h):
+            gels.update(orc.rotation_elements(k))
+    orc.keygen(seeds[0], sorted(gels))
+    reorg = S.reorg_vector(x, chunks)   # the same encryptions as encrypt_matrix / encrypt_vector
+    work = [(part_of[i], chunks[i], orc.encrypt(orc.encode(chunks[i].values), seeds[1], i),
+             orc.encrypt(orc.encode(reorg[i]), seeds[2], i)) for i in sel]
+    out.put(("ready", w, None))
+    go.wait()
+    sums = {}
+    for p, ch, a, b in work:   # Algorithm 1 (HE-Mult), Algorithm 4 (totalSum, mask)
+        v = S.total_sum(orc, orc.mult(a, b), ch.h, ch.c)
+        v = orc.cmult(v, S.mask_ntt(orc, ch.h))
+        sums[p] = orc.add(sums[p], v) if p in sums else v
+    out.put(("done", time.perf_counter(), {p: v.tobytes() for p, v in sums.items()}))
+
+
+def _collect(out, procs, n, kind, limit_s):
+    got = []
+    t0 = time.time()
+    while len(got) < n:
+        try:
+            m = out.get(timeout=1.0)
+        except Exception:
+            if not all(p.is_alive() or p.exitcode == 0 for p in procs) or time.time() - t0 > limit_s:
+                raise RuntimeError("all-core oracle worker failed")
+            continue
+        if m[0] == kind:
+            got.append(m)
+    return got
+
+
+def oracle_allcores(A, x, ring, seeds, cores=None, limit_s=900):
+    """The oracle's cloud evaluation of a whole SpMV on every host core:
+    one spawned process per core, chunks dealt round robin, partial sums
+    added per partition.  Returns (seconds from the start signal to the last
+    worker's end, cores, result ciphertexts [n_parts][2][L][N])."""
+    import multiprocessing as mp
+    from oracle import spmv as S
+    from oracle.bgv import Oracle
+    from oracle.params import Params
+    logn, L, K, dnum, t = ring
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    go, out = ctx.Event(), ctx.Queue()
+    procs = [ctx.Process(target=_allcores_worker, args=(w, cores, A, x, ring, seeds, go, out), daemon=True)
+             for w in range(cores)]
+    try:
+        for p in procs:
+            p.start()
+        _collect(out, procs, cores, "ready", limit_s)
+        t0 = time.perf_counter()
+        go.set()
+        done = _collect(out, procs, cores, "done", limit_s)
+    finally:
+        for p in procs:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+    dt = max(m[1] for m in done) - t0
+    orc = Oracle(Params(log2n=logn, L=L, K=K, dnum=dnum, t=t))
+    n_parts = len(S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots).parts)
+    res = [np.zeros((2, L, 1 << logn), dtype=np.uint64) for _ in range(n_parts)]
+    for m in done:
+        for p, b in m[2].items():
+            res[p] = orc.add(res[p], np.frombuffer(b, dtype=np.uint64).reshape(2, L, 1 << logn))
+    return dt, cores, res
+
+
 REFERENCE_SECONDS = 150.0
 
 
@@ -375,16 +479,14 @@ def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"
     launch_ms = kt["ms_per_step"] / kt["launches_per_step"]
     mm_launch = kt["mulmods_per_step"] / kt["launches_per_step"]
     by_launch = kt["bytes_per_step"] / kt["launches_per_step"]
-    alu_peak = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / IMAD_PER_MULMOD   # mulmod/s
+    alu_rate, alu_src = alu_peak()   # mulmod/s
     hbm_peak = peaks["hbm_gbs"] * 1e9
-    t_alu, t_hbm = mm_launch / alu_peak, by_launch / hbm_peak
+    t_alu, t_hbm = mm_launch / alu_rate, by_launch / hbm_peak
     if t_alu >= t_hbm:
         ach = mm_launch / (launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tmulmod/s",
-                "frac": ach / (alu_peak / 1e12), "kernel": top,
-                "traffic": measured_traffic(top, config),
-                "peak_source": "derived: %d SMs x %d heavy-IMAD/clk x %.0f MHz / %d per Shoup "
-                               "mulmod" % (SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD)}
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_rate / 1e12, "unit": "Tmulmod/s",
+                "frac": ach / (alu_rate / 1e12), "kernel": top,
+                "traffic": measured_traffic(top, config), "peak_source": alu_src}
     else:
         ach = by_launch / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -398,18 +500,168 @@ def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"
     return kernels, roof
 
 
-def run_serving(args):
+def boundary_block(ctx, inst, stream, reps=5):
+    """The client-side boundary calls around one SpMV of the workload (the
+    paper's Table 1 times Encrypt and Decrypt per ciphertext): CSR -> CSSC,
+    partitions and chunks on the host (hespmv_encode_cssc); encryption of
+    the matrix chunks and of the reorganised vector (hespmv_encrypt);
+    decryption of the result with the row map undone (hespmv_decrypt).
+    Median wall time of `reps` synchronised calls each."""
+    import torch
+    from paper_2603_04742_gb300 import binding as B
+    A, x = inst
+
+    def med(fn):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts)), r
+    t_cssc, m = med(lambda: ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals))
+    t_ea, ca = med(lambda: ctx.encrypt(m, B.HESPMV_MATRIX, seed=2))
+    t_ex, cx = med(lambda: ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3))
+    y = ctx.spmv(m, ca, cx, stream=stream)
+    t_dec, out = med(lambda: ctx.decrypt(m, y))
+    return {"encode_cssc_ms": t_cssc, "encrypt_matrix_ms": t_ea, "encrypt_vector_ms": t_ex,
+            "decrypt_ms": t_dec, "ciphertexts_per_operand": m.n_chunks, "result_ciphertexts": m.n_parts,
+            "encrypt_ms_per_ciphertext": (t_ea + t_ex) / (2 * m.n_chunks),
+            "decrypt_ms_per_ciphertext": t_dec / m.n_parts,
+            "correct": bool(list(out) == list(A.matvec(x))),
+            "timing": "median of %d calls, wall clock, device synchronised before and after" % reps}
+
+
+def batched_block(args, stream, persistent=True):
+    """The batched workload (64 uneven SpMVs at N = 2^14): one batched
+    evaluation per step under the autotuned schedule, against 64 plain
+    hespmv_spmv calls per step and against the persistent form (one launch
+    per step); the three give identical ciphertexts, which decrypt to A.x."""
+    import torch
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300 import synth
+    from paper_2603_04742_gb300.api import Context
+    insts = synth.workload("c4", count=args.instances)
+    logn, L, K, dnum, t = synth.RING["c4"]
+    ctx = Context(logn, L, K, dnum, t)
+    ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in insts]
+    ctx.keygen(1, sorted({s for m in ms for s in m.rotation_steps()}))
+    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=2 + i) for i, m in enumerate(ms)]
+    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=xx, seed=3 + i) for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
+    t0 = time.perf_counter()
+    tune = ctx.autotune(ms, As, Xs, reps=2)
+    tune["seconds"] = time.perf_counter() - t0
+    steps = max(3, min(args.steps, 20))
+    ys = ctx.spmv_batched(ms, As, Xs)
+    torch.cuda.synchronize()
+    correct = all(list(ctx.decrypt(m, y)) == list(a.matvec(xx)) for m, y, (a, xx) in zip(ms, ys, insts))
+    ref = [y.download() for y in ys]
+
+    def batched():
+        ctx.spmv_batched(ms, As, Xs, ys, stream=stream)
+    for _ in range(3):
+        batched()
+    ms_b = time_steps(batched, stream, steps, lambda: None)
+    ctx.profile_enable(True)
+    time_steps(batched, stream, 1, lambda: None)
+    launches = sum(v[0] for v in ctx.profile_read().values())
+    ctx.profile_enable(False)
+    yp = [ctx.spmv(m, a, xx) for m, a, xx in zip(ms, As, Xs)]
+
+    def plain():
+        for m, a, xx, y in zip(ms, As, Xs, yp):
+            ctx.spmv(m, a, xx, y=y, stream=stream)
+    for _ in range(3):
+        plain()
+    ms_p = time_steps(plain, stream, steps, lambda: None)
+    same = all(np.array_equal(y.download(), r) for y, r in zip(yp, ref))
+    n = len(insts)
+    nnz = sum(a.nnz for a, _ in insts)
+    out = {"workload": CONFIGS["c4"], "instances": n, "steps": steps, "nnz": nnz,
+           "chunks": sum(m.n_chunks for m in ms), "rotations": sum(m.n_rot for m in ms),
+           "keyswitches": sum(m.n_chunks + m.n_keyswitch for m in ms),
+           "value": n * 1000.0 / ms_b, "unit": "SpMV/s", "ms_per_step": ms_b,
+           "nnz_per_s": nnz * 1000.0 / ms_b, "schedule": tune["best"], "gpu_launches_per_step": launches,
+           "correct": bool(correct),
+           "plain": {"value": n * 1000.0 / ms_p, "unit": "SpMV/s", "ms_per_step": ms_p,
+                     "form": "%d hespmv_spmv calls per step" % n},
+           "batched_vs_plain": ms_p / ms_b, "autotune": tune}
+    if persistent:
+        cur = ctx.get_tuning()
+        ctx.set_tuning(16, 0, 0, 0, 1)
+        yq = ctx.spmv_batched(ms, As, Xs)
+
+        def pers():
+            ctx.spmv_batched(ms, As, Xs, yq, stream=stream)
+        for _ in range(3):
+            pers()
+        ms_q = time_steps(pers, stream, steps, lambda: None)
+        same = same and all(np.array_equal(y.download(), r) for y, r in zip(yq, ref))
+        out["persistent"] = {"value": n * 1000.0 / ms_q, "unit": "SpMV/s", "ms_per_step": ms_q,
+                             "gpu_launches_per_step": 1,
+                             "form": "hespmv_spmv_batched with tuning.persistent = 1: one launch per "
+                                     "step, HE-Mult groups of 16"}
+        ctx.set_tuning(cur["mult_batch"], cur["rot_batch"], cur["ntt_split"], cur["rows_tma"],
+                       cur["persistent"], cur["persist_blocks"])
+    out["identical_results"] = bool(same)
+    ctx.device_status()
+    return out
+
+
+def rotation_block(args, stream):
+    """A rotation-bearing SpMV at N = 2^15 (the Figure 8 sweep point with
+    2^18 non-zeros: 16384 x 16384 uniform positions, power-of-two keys):
+    time per SpMV, its kernels and the roofline of the top one."""
+    import torch
+    from paper_2603_04742_gb300 import binding as B
+    from paper_2603_04742_gb300 import synth
+    from paper_2603_04742_gb300.api import Context
+    ring = synth.RING["c5"]
+    logn, L, K, dnum, t = ring
+    ctx = Context(logn, L, K, dnum, t)
+    g = np.random.default_rng(108)
+    A = synth.uniform_positions(g, 16384, 16384, 1 << 18, -15, 15)
+    x = g.integers(-15, 16, size=16384, dtype=np.int64)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals, max_abs_x=15)
+    ctx.keygen(1, m.rotation_steps())
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=18)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=118)
+    y = ctx.spmv(m, ca, cx)
+    torch.cuda.synchronize()
+    correct = list(ctx.decrypt(m, y)) == list(A.matvec(x))
+
+    def step():
+        ctx.spmv(m, ca, cx, y=y, stream=stream)
+    for _ in range(3):
+        step()
+    steps = max(10, min(args.steps, 50))
+    ms_step = time_steps(step, stream, steps, lambda: None)
+    ctx.profile_enable(True)
+    time_steps(step, stream, steps, lambda: None)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    n_ks = m.n_chunks + m.n_keyswitch
+    kernels, roof = roofline(ctx, prof, steps, ring, n_ks, m.n_chunks, m.n_parts, m.n_rot, "rot")
+    return {"workload": "16384x16384, 2^18 non-zeros at uniform positions, integers [-15,15]; BGV "
+                        "N=2^15, 8+2 primes, dnum 4, t=1179649, power-of-two Galois keys",
+            "value": 1000.0 / ms_step, "unit": "SpMV/s", "ms_per_step": ms_step, "steps": steps,
+            "nnz_per_s": A.nnz * 1000.0 / ms_step, "chunks": m.n_chunks, "rotations": m.n_rot,
+            "keyswitches": n_ks, "correct": bool(correct), "roofline": roof, "kernels": kernels,
+            "gpu_launches_per_step": sum(v[0] for v in prof.values()) / steps}
+
+
+def serving_measure(args, requests, sat_requests, serial_requests):
     """c5: Poisson arrivals of SpMV requests drawn from a pool of distinct
-    pre-encrypted instances, served with continuous batching; compared with a
-    serial server (one request at a time) on the same arrival process."""
+    pre-encrypted instances, served with continuous batching at 0.7 x the
+    saturated throughput; compared with a serial server (one request at a
+    time) on the same arrival process."""
     import torch
 
     from paper_2603_04742_gb300 import binding as B
     from paper_2603_04742_gb300 import synth
     from paper_2603_04742_gb300.api import Context, Server
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return 0
     pool = synth.workload("c5", pool=args.pool)
     ring = synth.RING["c5"]
     logn, L, K, dnum, t = ring
@@ -453,21 +705,31 @@ def run_serving(args):
                 "mean_ms": float(lat.mean()), "batches": st["batches"],
                 "max_inflight": st["max_inflight"], "slots": slots, "max_batch": max_batch}
 
-    sat = serve(args.sat_requests, None, args.slots, args.max_batch)
+    sat = serve(sat_requests, None, args.slots, args.max_batch)
     rate = 0.7 * sat["throughput"]
-    cont = serve(args.requests, rate, args.slots, args.max_batch)
-    serial = serve(args.serial_requests, rate, 1, 1)
-    line = {"metric": METRIC, "value": cont["throughput"], "unit": "SpMV/s", "n_gpus": 1,
-            "steps": args.requests, "warmup": 0, "ms_per_step": 1e3 / cont["throughput"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
-            "config": {"workload": "c5 serving: Poisson arrivals at %.1f req/s (0.7 x saturated), "
-                                   "requests drawn from %d distinct pre-encrypted instances, "
-                                   "N=2^15, 8+2 primes, dnum 4, t=1179649" % (rate, len(pool)),
-                       "pool_chunks": sum(m.n_chunks for m in ms)},
+    cont = serve(requests, rate, args.slots, args.max_batch)
+    serial = serve(serial_requests, rate, 1, 1)
+    return {"workload": "Poisson arrivals at %.1f req/s (0.7 x saturated), requests drawn from %d "
+                        "distinct pre-encrypted instances (n log-U[512,16384], density "
+                        "log-U[5e-4,1e-2]), N=2^15, 8+2 primes, dnum 4, t=1179649" % (rate, len(pool)),
+            "pool_chunks": sum(m.n_chunks for m in ms), "rate": rate,
             "correct": bool(correct), "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},
-            "nnz_per_s": cont["nnz_per_s"], "continuous_batching": cont, "saturated": sat,
-            "serial": serial}
+            "value": cont["throughput"], "unit": "SpMV/s", "nnz_per_s": cont["nnz_per_s"],
+            "continuous_batching": cont, "saturated": sat, "serial": serial}
+
+
+def run_serving(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    r = serving_measure(args, args.requests, args.sat_requests, args.serial_requests)
+    line = {"metric": METRIC, "value": r["value"], "unit": "SpMV/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "ms_per_step": 1e3 / r["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "c5 serving: " + r["workload"],
+                                            "pool_chunks": r["pool_chunks"]},
+            "correct": r["correct"], "latency_ms": r["latency_ms"], "nnz_per_s": r["nnz_per_s"],
+            "continuous_batching": r["continuous_batching"], "saturated": r["saturated"],
+            "serial": r["serial"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -628,6 +890,14 @@ def main():
     clocks.start()
     ms_step = max_over_ranks(time_steps(step, stream, args.steps, barrier))
     clk = clocks.stop()
+    # a sustained pass of the same step (about 2 s) with its own clock samples
+    clocks_sus = Clocks(local)
+    clocks_sus.start()
+    n_sus = max(1, int(2000.0 / max(ms_step, 1e-3)))
+    ms_sus = time_steps(step, stream, n_sus, lambda: None)
+    clk_sus = clocks_sus.stop()
+    if clk_sus:
+        clk_sus.update({"steps": n_sus, "ms_per_step": ms_sus})
     n_spmv = len(insts)
     nnz = sum(a.nnz for a, _ in insts)
     value = world * n_spmv * 1000.0 / ms_step
@@ -757,6 +1027,20 @@ def main():
                "sample": "oracle cloud evaluation of %d of %d chunks of instance 0 (%.1f s), "
                          "scaled to one SpMV%s" % (n_s, n_total, dt,
                                                    " of the batch by chunk count" if batched else "")}
+        if args.config == "c3":
+            # every host core: the whole SpMV, one process per core; its result
+            # ciphertext is compared with the GPU's
+            try:
+                dta, cores, res = oracle_allcores(A0, x0, ring, (1 + rank, 2 + 1000 * rank, 3 + 1000 * rank))
+                gy = ys[0].download()
+                cpu["all_cores"] = {"value": 1.0 / dta, "unit": "SpMV/s", "cores": cores, "kind": "oracle",
+                                    "seconds": dta, "nproc": os.cpu_count(),
+                                    "matches_gpu": bool(all(np.array_equal(gy[p], r) for p, r in enumerate(res))),
+                                    "sample": "the whole SpMV (all %d chunks), chunks dealt round robin to "
+                                              "one spawned process per core, keys and encryptions made "
+                                              "before the timed region" % n_total}
+            except Exception as e:   # reported, not fatal: the baseline is context
+                cpu["all_cores"] = {"error": str(e)[:200]}
 
     workload = CONFIGS[args.config]
     if args.scheme == "bfv":
@@ -790,7 +1074,22 @@ def main():
         "kernels": kernels,
     }
     line["autotune"] = tune
+    line["clocks_sustained"] = clk_sus
     line.update(extra)
+    if args.config == "c3" and args.scheme == "bgv" and not args.no_extra:
+        # the rest of the metric: batched vs plain, serving latency, rotations
+        # at N = 2^15, and the client-side boundary calls
+        blocks = (("boundary_calls", lambda: boundary_block(ctx, insts[0], stream)),
+                  ("batched", lambda: batched_block(args, stream)),
+                  ("serving", lambda: serving_measure(args, args.serve_requests, 400, 300)),
+                  ("rotations", lambda: rotation_block(args, stream)))
+        for name, fn in blocks:
+            t0 = time.perf_counter()
+            try:
+                line[name] = fn()
+            except Exception as e:   # reported in the line; the headline stands
+                line[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+            line[name]["seconds"] = time.perf_counter() - t0
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

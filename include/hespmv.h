@@ -484,7 +484,9 @@ int hespmv_keyswitch_noalloc(hespmv_ctx *ctx, const uint64_t *d, uint32_t galois
 typedef struct hespmv_tuning {
     int32_t mult_batch; /* HE-Mult stage: ciphertexts per fused key switch (0: 32)        */
     int32_t rot_batch;  /* totalSum: ciphertexts per batched rotation round
-                           (0: 32 at N = 2^15, else 64)                                  */
+                           (0: 32 at N = 2^15, else 64); in the persistent form: the
+                           levels by which consecutive HE-Mult groups are staggered
+                           in the work queue (0: none)                                */
     int32_t ntt_split;  /* fused key switch NTT split: 0 = default, 1 = alternative
                            (N = 2^LC x 2^LR with LC and LR exchanged or shifted by one)  */
     int32_t rows_tma;   /* fused key switch forward row pass: 0 = one CTA per tile,

@@ -607,6 +607,10 @@ int spmv_prepare(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, S
 
 // ------------------------------------------------------------ persistent evaluation
 
+// levels by which consecutive HE-Mult groups of a persistent program are
+// staggered in its work queue (tune_GR overrides it)
+constexpr int kPersistStagger = 0;
+
 // HE-Mult group of a persistent evaluation: ciphertexts per key switch
 size_t persist_group(const hespmv_ctx *ctx, size_t total) {
     const size_t G = ctx->tune_G ? ctx->tune_G : 16;
@@ -646,6 +650,7 @@ void drop_persist_plans(hespmv_ctx *ctx) {
 struct HostPhase {
     PPhase p{};
     std::vector<int32_t> deps;
+    int32_t grp = 0;  // HE-Mult group it belongs to (the latest one, for masked sums)
 };
 
 // Program of one evaluation (Algorithm 1 cloud lines and Algorithm 4 for
@@ -664,7 +669,8 @@ struct HostPhase {
 // of each of its chunks).  Phases are ordered by depth, deeper remaining
 // chains first at equal depth, so every dependency precedes its user.
 int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, const uint64_t *const *A,
-                  const uint64_t *const *X, uint64_t *const *Y, uint64_t *ws, size_t G, PersistPlan *P) {
+                  const uint64_t *const *X, uint64_t *const *Y, uint64_t *ws, size_t G, int stagger,
+                  PersistPlan *P) {
     const Ctx c = view(ctx);
     const int64_t LN = (int64_t)c.L * c.N, CT = 2 * LN;
     std::vector<HostPhase> ph;
@@ -673,7 +679,7 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
     std::vector<std::vector<const uint64_t *>> tabs;  // address tables, placed in the blob
     std::vector<size_t> inst_tab, mask_tab;           // first of each one's two tables
     int32_t gx[7], gy[7];
-    auto add_ks = [&](const PInst &I, std::vector<int32_t> deps0, size_t tab) -> int32_t {
+    auto add_ks = [&](const PInst &I, std::vector<int32_t> deps0, size_t tab, int32_t grp) -> int32_t {
         persist_stage_tiles(c, I.n, gx, gy);
         const int32_t ii = (int32_t)inst.size();
         inst.push_back(I);
@@ -681,6 +687,7 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
         int32_t prev = -1;
         for (int s = 0; s < 7; ++s) {
             HostPhase h;
+            h.grp = grp;
             h.p.kind = kPhIntt + s;
             h.p.inst = ii;
             h.p.gx = gx[s];
@@ -719,7 +726,7 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
         I.scratch = cur;
         I.n = (int32_t)gn;
         cur += ks_words(c, gn);
-        const int32_t f = add_ks(I, {}, ta);
+        const int32_t f = add_ks(I, {}, ta, (int32_t)(g0 / G));
         for (size_t u = 0; u < gn; ++u) last_ph[g0 + u] = f;
     }
     // totalSum chains
@@ -755,7 +762,7 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
                     I.post = last ? w : nullptr;
                     I.scratch = scr;
                     I.n = 1;
-                    prev = add_ks(I, {prev}, SIZE_MAX);
+                    prev = add_ks(I, {prev}, SIZE_MAX, (int32_t)(g / G));
                 }
                 w = Wg;
             }
@@ -778,6 +785,7 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
                 tabs[tt].push_back(term[g]);
                 tabs[tt + 1].push_back(ctx->masks.at(pl.chunks[Pt.chunk0 + q].h));
                 h.deps.push_back(last_ph[g]);
+                h.grp = std::max(h.grp, (int32_t)(g / G));
             }
             std::sort(h.deps.begin(), h.deps.end());
             h.deps.erase(std::unique(h.deps.begin(), h.deps.end()), h.deps.end());
@@ -793,7 +801,11 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
             ph.push_back(std::move(h));
         }
     }
-    // order: depth first, then the longer remaining chain, then creation
+    // order: by depth, group g's phases `stagger` levels behind group g-1's
+    // (so a phase's inputs were usually finished well before a CTA takes
+    // it), then the longer remaining chain, then creation.  Depth grows and
+    // the group never shrinks along a dependency, so every dependency keeps
+    // a smaller key than its user.
     const size_t nph = ph.size();
     std::vector<int32_t> level(nph, 0), tail(nph, 1), order(nph), pos(nph);
     for (size_t p = 0; p < nph; ++p)
@@ -801,8 +813,9 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
     for (size_t p = nph; p-- > 0;)
         for (int32_t d : ph[p].deps) tail[d] = std::max(tail[d], tail[p] + 1);
     for (size_t p = 0; p < nph; ++p) order[p] = (int32_t)p;
+    auto key = [&](int32_t p) { return (int64_t)level[p] + (int64_t)stagger * ph[p].grp; };
     std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        if (level[a] != level[b]) return level[a] < level[b];
+        if (key(a) != key(b)) return key(a) < key(b);
         if (tail[a] != tail[b]) return tail[a] > tail[b];
         return a < b;
     });
@@ -824,14 +837,15 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
         if (tiles >= (int64_t)INT32_MAX) FAIL(HESPMV_E_UNSUPPORTED, "persistent program: too many tiles");
     }
     off[nph] = (int32_t)tiles;
-    // one device block: args | phases | offsets | deps | instances | masks | tables | counters
+    // one device block: phases | offsets | deps | instances | masks | tables | tile table | counters
     auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
     size_t ntab = 0;
     for (const auto &t : tabs) ntab += t.size();
-    const size_t o_args = 0, o_ph = al(o_args + sizeof(KsArgs)), o_off = al(o_ph + nph * sizeof(PPhase)),
+    const size_t o_ph = 0, o_off = al(o_ph + nph * sizeof(PPhase)),
                  o_dep = al(o_off + (nph + 1) * sizeof(int32_t)), o_inst = al(o_dep + deps.size() * sizeof(int32_t)),
                  o_mask = al(o_inst + inst.size() * sizeof(PInst)), o_tab = al(o_mask + mask.size() * sizeof(PMask)),
-                 o_ctr = al(o_tab + ntab * sizeof(void *)), bytes = al(o_ctr + (nph + 2) * sizeof(uint32_t));
+                 o_info = al(o_tab + ntab * sizeof(void *)), o_ctr = al(o_info + (size_t)tiles * sizeof(uint64_t)),
+                 bytes = al(o_ctr + (nph + 2) * sizeof(uint32_t));
     P->blob = dev_alloc(ctx, bytes);
     if (!P->blob) FAIL(HESPMV_E_NOMEM, "persistent program allocation failed");
     P->bytes = bytes;
@@ -852,20 +866,22 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
         mask[j].masks = (const uint64_t *const *)(base + tab_off[mask_tab[j] + 1]);
     }
     std::vector<char> img(bytes, 0);
-    KsArgs args;
-    persist_args(c, &args);
-    memcpy(img.data() + o_args, &args, sizeof(KsArgs));
-    memcpy(img.data() + o_ph, fph.data(), nph * sizeof(PPhase));
+    if (nph) memcpy(img.data() + o_ph, fph.data(), nph * sizeof(PPhase));
     memcpy(img.data() + o_off, off.data(), (nph + 1) * sizeof(int32_t));
     if (!deps.empty()) memcpy(img.data() + o_dep, deps.data(), deps.size() * sizeof(int32_t));
     if (!inst.empty()) memcpy(img.data() + o_inst, inst.data(), inst.size() * sizeof(PInst));
     if (!mask.empty()) memcpy(img.data() + o_mask, mask.data(), mask.size() * sizeof(PMask));
     if (!flat.empty()) memcpy(img.data() + o_tab, flat.data(), flat.size() * sizeof(void *));
+    {
+        uint64_t *info = (uint64_t *)(img.data() + o_info);
+        for (size_t k = 0; k < nph; ++k)
+            for (int32_t l = 0; l < fph[k].tiles; ++l) *info++ = ((uint64_t)k << 32) | (uint32_t)l;
+    }
     CK(cudaMemcpy(P->blob, img.data(), bytes, cudaMemcpyHostToDevice));
     PProg &g = P->prog;
-    g.args = (const KsArgs *)(base + o_args);
     g.ph = (const PPhase *)(base + o_ph);
     g.off = (const int32_t *)(base + o_off);
+    g.info = (const uint64_t *)(base + o_info);
     g.deps = (const int32_t *)(base + o_dep);
     g.inst = (const PInst *)(base + o_inst);
     g.mask = (const PMask *)(base + o_mask);
@@ -882,7 +898,8 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
 // buffers, workspace, HE-Mult group and NTT split).
 int persist_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, const uint64_t *const *A,
                  const uint64_t *const *X, uint64_t *const *Y, uint64_t *ws, size_t G, PersistPlan **out) {
-    std::vector<uint64_t> key{(uint64_t)(uintptr_t)ws, (uint64_t)G, (uint64_t)ctx->ks_split};
+    const int stagger = ctx->tune_GR ? (int)ctx->tune_GR : kPersistStagger;
+    std::vector<uint64_t> key{(uint64_t)(uintptr_t)ws, (uint64_t)G, (uint64_t)ctx->ks_split, (uint64_t)stagger};
     for (size_t i = 0; i < n_inst; ++i) {
         key.push_back(ms[i]->uid);
         key.push_back((uint64_t)(uintptr_t)A[i]);
@@ -901,7 +918,7 @@ int persist_plan(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, c
         drop_persist_plans(ctx);
     }
     PersistPlan *P = new PersistPlan();
-    const int rc = persist_build(ctx, n_inst, ms, A, X, Y, ws, G, P);
+    const int rc = persist_build(ctx, n_inst, ms, A, X, Y, ws, G, stagger, P);
     if (rc) {
         persist_free(ctx, P);
         return rc;
@@ -2710,7 +2727,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
             const size_t Gp = persist_group(ctx, total);
             pp.need_bytes = persist_ws_words(c, total, rot, Gp) * 8;
             rec.mult_batch = (int32_t)Gp;
-            rec.rot_batch = 0;
+            rec.rot_batch = s.GR ? (int32_t)s.GR : kPersistStagger;
         }
         if (pp.need_bytes > ctx->ws_bytes && pp.need_bytes - ctx->ws_bytes > free_b / 10 * 9) {
             rec.ms = -1;
@@ -2798,7 +2815,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
     best->persist_blocks = bestS.blocks;
     if (bestS.persistent) {
         best->mult_batch = (int32_t)persist_group(ctx, total);
-        best->rot_batch = 0;
+        best->rot_batch = bestS.GR ? (int32_t)bestS.GR : kPersistStagger;
     }
     best->ms = best_ms;
     if (n_tried) *n_tried = log.size();
@@ -2836,23 +2853,21 @@ int hespmv_selftest_persist_timeout(hespmv_ctx *ctx, int32_t *code) {
     // which the launch's only CTA can never reach: the wait must give up
     const PPhase ph[3] = {{kPhNone, 0, 1, 1, 0, 0}, {kPhNone, 0, 1, 1, 0, 1}, {kPhNone, 0, 1, 1, 1, 0}};
     const int32_t off[4] = {0, 1, 2, 3}, deps[1] = {2};
-    KsArgs args;
-    persist_args(c, &args);
-    const size_t o_ph = 256, o_off = o_ph + sizeof(ph), o_dep = o_off + sizeof(off), o_ctr = o_dep + 16,
-                 bytes = o_ctr + 5 * sizeof(uint32_t);
+    const uint64_t info[3] = {0, 1ull << 32, 2ull << 32};
+    const size_t o_ph = 0, o_off = o_ph + sizeof(ph), o_dep = o_off + sizeof(off), o_info = o_dep + 16,
+                 o_ctr = o_info + sizeof(info), bytes = o_ctr + 5 * sizeof(uint32_t);
     std::vector<char> img(bytes, 0);
-    static_assert(sizeof(KsArgs) <= 256, "KsArgs fits its slot");
-    memcpy(img.data(), &args, sizeof(args));
     memcpy(img.data() + o_ph, ph, sizeof(ph));
     memcpy(img.data() + o_off, off, sizeof(off));
     memcpy(img.data() + o_dep, deps, sizeof(deps));
+    memcpy(img.data() + o_info, info, sizeof(info));
     char *blob = (char *)dev_alloc(ctx, bytes);
     if (!blob) FAIL(HESPMV_E_NOMEM, "self-test allocation failed");
     PProg P{};
-    P.args = (const KsArgs *)blob;
     P.ph = (const PPhase *)(blob + o_ph);
     P.off = (const int32_t *)(blob + o_off);
     P.deps = (const int32_t *)(blob + o_dep);
+    P.info = (const uint64_t *)(blob + o_info);
     P.ctr = (uint32_t *)(blob + o_ctr);
     P.nph = 3;
     P.total = 3;

@@ -108,8 +108,6 @@ bool persist_supported(const Ctx &c);
 // one launch of the program P (counters zeroed beforehand), at most
 // max_blocks CTAs (0: every resident CTA of the GPU)
 cudaError_t persist_launch(const Ctx &c, const PProg &P, int max_blocks, cudaStream_t st);
-// the key-switch constants a persistent program keeps a device copy of
-void persist_args(const Ctx &c, KsArgs *out);
 // virtual grid (x, y) of each of the 7 stages of a persistent key switch of n items
 void persist_stage_tiles(const Ctx &c, int n, int32_t gx[7], int32_t gy[7]);
 // x <- x * 2^64 mod q over n_items x (L+K) limbs (keys to Montgomery form)

@@ -156,9 +156,12 @@ __global__ __launch_bounds__(kNttThreads) void k_ks_intt_rows_src(KsArgs a, KsSr
 // ModUp of digit jd to every prime outside it, fused with the forward column
 // pass: z [n][L][N] -> ext [n][dnum][L+K][N] (column-pass output, unreduced:
 // conversion sums below 4 alpha q <= 16q, then 4q per stage)
+// With nparts > 1 the digit's raised limbs are split into nparts ranges and
+// this tile makes range `part` (each part redoes the digit's inverse pass):
+// more CTAs for key switches of few ciphertexts.
 template <int LC, int AMAX>
 __device__ __forceinline__ void ks_modup_cols_tile(const KsArgs &a, const uint64_t *z, uint64_t *ext, int bx,
-                                                   int by, uint64_t *sm) {
+                                                   int by, uint64_t *sm, int part = 0, int nparts = 1) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     const int N = 1 << a.log2n, C = N >> LC, L = a.L, LK = a.L + a.K;
     const int item = by / a.dnum, jd = by - item * a.dnum;
@@ -181,8 +184,9 @@ __device__ __forceinline__ void ks_modup_cols_tile(const KsArgs &a, const uint64
         }
     }
     uint64_t *dst0 = ext + ((int64_t)item * a.dnum + jd) * LK * N + cofs;
-    for (int l = 0; l < LK; ++l) {
-        if (l >= i0 && l < i1) continue;
+    const int cnt = LK - na, e0 = part * cnt / nparts, e1 = (part + 1) * cnt / nparts;
+    for (int e = e0; e < e1; ++e) {
+        const int l = e < i0 ? e : e + na;  // the primes outside the digit, in order
         const uint64_t q = a.mc[l].q;
         const TwPair *tw = (const TwPair *)(a.tw + (int64_t)l * 4 * N);
         uint64_t v[8];
@@ -206,9 +210,9 @@ __device__ __forceinline__ void ks_modup_cols_tile(const KsArgs &a, const uint64
 
 template <int LC, int AMAX>
 __global__ __launch_bounds__(kNttThreads, AMAX <= 2 ? 3 : 2) void k_ks_modup_cols(KsArgs a, const uint64_t *z,
-                                                                                 uint64_t *ext) {
+                                                                                 uint64_t *ext, int nparts) {
     __shared__ uint64_t sm[kNttTile];
-    ks_modup_cols_tile<LC, AMAX>(a, z, ext, blockIdx.x, blockIdx.y, sm);
+    ks_modup_cols_tile<LC, AMAX>(a, z, ext, blockIdx.x, blockIdx.y / nparts, sm, blockIdx.y % nparts, nparts);
 }
 
 // Forward row pass, in place, of every raised limb: ext[item][jd][l] for the
@@ -450,9 +454,11 @@ __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc
 
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
 // with t folded in, fused with the forward column pass: -> dh [n][2][L][N]
+// nparts > 1: this tile makes the Q limbs of range `part` of nparts (each
+// part redoes the inverse pass of the P limbs).
 template <int LC, int KMAX>
 __device__ __forceinline__ void ks_moddown_cols_tile(const KsArgs &a, const uint64_t *acc, uint64_t *dh, int bx,
-                                                     int by, uint64_t *sm) {
+                                                     int by, uint64_t *sm, int part = 0, int nparts = 1) {
     constexpr int M = 1 << LC, TC = kNttTile / M;
     const int N = 1 << a.log2n, C = N >> LC, L = a.L, K = a.K, LK = L + K;
     const int ic = by;  // item * 2 + component
@@ -472,7 +478,7 @@ __device__ __forceinline__ void ks_moddown_cols_tile(const KsArgs &a, const uint
             inv_body<LC, true>(ys[s], j, 1, sm, ColIdx<TC>{cc}, itw, a.mc[L + s].q, f[0], f[1], f[2], f[3]);
         }
     }
-    for (int i = 0; i < L; ++i) {
+    for (int i = part * L / nparts, i1 = (part + 1) * L / nparts; i < i1; ++i) {
         const uint64_t q = a.mc[i].q;
         const TwPair *tw = (const TwPair *)(a.tw + (int64_t)i * 4 * N);
         uint64_t v[8];
@@ -496,9 +502,9 @@ __device__ __forceinline__ void ks_moddown_cols_tile(const KsArgs &a, const uint
 
 template <int LC, int KMAX>
 __global__ __launch_bounds__(kNttThreads, KMAX <= 2 ? 3 : 2) void k_ks_moddown_cols(KsArgs a, const uint64_t *acc,
-                                                                                   uint64_t *dh) {
+                                                                                   uint64_t *dh, int nparts) {
     __shared__ uint64_t sm[kNttTile];
-    ks_moddown_cols_tile<LC, KMAX>(a, acc, dh, blockIdx.x, blockIdx.y, sm);
+    ks_moddown_cols_tile<LC, KMAX>(a, acc, dh, blockIdx.x, blockIdx.y / nparts, sm, blockIdx.y % nparts, nparts);
 }
 
 // Forward row pass of delta, then out = (acc - delta) * P^-1 (the addend is
@@ -546,6 +552,22 @@ __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(
     ks_rows_final_tile<LR>(a, acc, dh, out, oidx, nullptr, blockIdx.x, blockIdx.y, sm);
 }
 
+// Parts of a column-pass launch of `ctas` CTAs that each make `outputs`
+// limbs: split (doubling) while the launch stays within one wave of 3 CTAs
+// per SM, so key switches of few ciphertexts are not left on a few SMs.
+static int col_parts(int ctas, int outputs) {
+    static int wave = 0;
+    if (!wave) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        wave = 3 * std::max(1, sms);
+    }
+    int parts = 1;
+    while (2 * parts <= outputs && 2 * parts * ctas <= wave) parts *= 2;
+    return parts;
+}
+
 template <int LC, int LR>
 static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const uint64_t *key,
                             uint64_t *out, const KsAdd &ad, const int32_t *oidx, int n, uint64_t *scratch,
@@ -561,10 +583,14 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     k_ks_intt_rows_src<LR><<<dim3(gr, n * L), kNttThreads, 0, st>>>(a, s, z);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_modup_cols", st);
-    if (c.alpha <= 2)
-        k_ks_modup_cols<LC, 2><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
-    else
-        k_ks_modup_cols<LC, 4><<<dim3(gc, n * c.dnum), kNttThreads, 0, st>>>(a, z, ext);
+    {
+        const int parts = col_parts(gc * n * c.dnum, (int)LK - c.alpha);
+        const dim3 g(gc, n * c.dnum * parts);
+        if (c.alpha <= 2)
+            k_ks_modup_cols<LC, 2><<<g, kNttThreads, 0, st>>>(a, z, ext, parts);
+        else
+            k_ks_modup_cols<LC, 4><<<g, kNttThreads, 0, st>>>(a, z, ext, parts);
+    }
     prof_end(c, r, st);
     if (c.rows_tma) {
         r = prof_begin(c, "k_ks_rows_fwd_tma", st);
@@ -597,10 +623,14 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
                                                                     (int)L);
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_moddown_cols", st);
-    if (c.K <= 2)
-        k_ks_moddown_cols<LC, 2><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
-    else
-        k_ks_moddown_cols<LC, 4><<<dim3(gc, n * 2), kNttThreads, 0, st>>>(a, acc, dh);
+    {
+        const int parts = col_parts(gc * n * 2, (int)L);
+        const dim3 g(gc, n * 2 * parts);
+        if (c.K <= 2)
+            k_ks_moddown_cols<LC, 2><<<g, kNttThreads, 0, st>>>(a, acc, dh, parts);
+        else
+            k_ks_moddown_cols<LC, 4><<<g, kNttThreads, 0, st>>>(a, acc, dh, parts);
+    }
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_rows_final", st);
     k_ks_rows_final<LR><<<dim3(gr, n * 2 * L), kNttThreads, 0, st>>>(a, acc, dh, out, oidx);
@@ -611,11 +641,19 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
 // ---------------------------------------------------------------------------
 // Persistent evaluation (the program structures are described in persist.h).
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+
+// count a finished tile: a release add, ordered after the CTA's writes of the
+// tile (they precede it by the CTA barrier)
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -676,9 +714,8 @@ __device__ __forceinline__ void raised_limb(const KsArgs &a, int e, int &jd, int
     l = LK - 1;  // not reached for e in range
 }
 
-// Each tile kind runs in a function of its own (not inlined): the register
-// allocation of one kind does not constrain another's, so the persistent
-// kernel needs no more registers than its largest stage.
+// The tile kinds of the persistent kernel (inlined: the key-switch constants
+// stay kernel parameters, read from the constant bank).
 struct PScratch {
     uint64_t *z, *ext, *acc, *dh;
 };
@@ -693,43 +730,43 @@ __device__ __forceinline__ PScratch persist_scratch(const KsArgs &a, const PInst
 }
 
 template <int LR>
-__device__ __noinline__ void pt_intt(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_intt(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     ks_intt_rows_src_tile<LR>(a, I.s, persist_scratch(a, I).z, bx, by, sm);
 }
 template <int LC>
-__device__ __noinline__ void pt_modup(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_modup(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     const PScratch w = persist_scratch(a, I);
     ks_modup_cols_tile<LC, 2>(a, w.z, w.ext, bx, by, sm);
 }
 template <int LR>
-__device__ __noinline__ void pt_rows_fwd(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_rows_fwd(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     const int ext_limbs = a.dnum * (a.L + a.K) - a.L;
     const int item = by / ext_limbs;
     int jd, l;
     raised_limb(a, by - item * ext_limbs, jd, l);
     ks_rows_fwd_tile<LR>(a, persist_scratch(a, I).ext, bx, item, jd, l, sm);
 }
-__device__ __noinline__ void pt_mac(const KsArgs &a, const PInst &I, int bx, int by) {
+__device__ __forceinline__ void pt_mac(const KsArgs &a, const PInst &I, int bx, int by) {
     const PScratch w = persist_scratch(a, I);
     ks_mac_tile<0, 2>(a, I.s, I.ad, w.ext, I.key, w.acc, I.n, bx, by);
 }
 template <int LR>
-__device__ __noinline__ void pt_intt_p(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_intt_p(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     const int64_t LN = (int64_t)a.L << a.log2n, LKN = (int64_t)(a.L + a.K) << a.log2n;
     uint64_t *acc = persist_scratch(a, I).acc;
     ks_intt_rows_tile<LR>(a, acc + LN, LKN, acc + LN, LKN, a.K, a.L, bx, by, sm);
 }
 template <int LC>
-__device__ __noinline__ void pt_moddown(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_moddown(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     const PScratch w = persist_scratch(a, I);
     ks_moddown_cols_tile<LC, 2>(a, w.acc, w.dh, bx, by, sm);
 }
 template <int LR>
-__device__ __noinline__ void pt_final(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
+__device__ __forceinline__ void pt_final(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {
     const PScratch w = persist_scratch(a, I);
     ks_rows_final_tile<LR>(a, w.acc, w.dh, I.out, I.oidx, I.post, bx, by, sm);
 }
-__device__ __noinline__ void pt_mask(const KsArgs &a, const PMask &J, int bx) { mask_tile(a, J, bx); }
+__device__ __forceinline__ void pt_mask(const KsArgs &a, const PMask &J, int bx) { mask_tile(a, J, bx); }
 
 template <int LC, int LR>
 __device__ __forceinline__ void persist_tile(const KsArgs &a, const PProg &P, int kind, int inst, int bx, int by,
@@ -747,62 +784,76 @@ __device__ __forceinline__ void persist_tile(const KsArgs &a, const PProg &P, in
     }
 }
 
+// 4 CTAs of 256 threads per SM (64 registers; the conversion kernels and the
+// key product spill a little, which measured faster than 3 or 2 CTAs).
 template <int LC, int LR>
-__global__ __launch_bounds__(kNttThreads, 3) void k_ks_persist(PProg P) {
-    const KsArgs &a = *P.args;  // in global memory: tile functions take it by reference
+__global__ __launch_bounds__(kNttThreads, 4) void k_ks_persist(const KsArgs a, PProg P) {
     __shared__ __align__(16) uint64_t sm[kRowTileWords];
-    __shared__ int s_t, s_p;
+    __shared__ int s_kind, s_inst, s_gx, s_local, s_p;
     uint32_t *const next = P.ctr + P.nph, *const stop = P.ctr + P.nph + 1;
-    int p = 0;  // phase of this CTA's last tile: tiles are taken in increasing order
+    // thread 0 holds the CTA's next two tiles: t0 with its table entry, and
+    // t1, claimed while the current tile runs (tiles are still taken in
+    // increasing order, so the lowest unfinished tile never waits on
+    // anything unfinished)
+    int t0 = 0, t1 = 0, cur = -1;
+    uint64_t i0 = 0;
+    if (threadIdx.x == 0) {
+        t0 = (int)atomicAdd(next, 1u);
+        t1 = (int)atomicAdd(next, 1u);
+        if (t0 < P.total) i0 = P.info[t0];
+    }
     for (;;) {
         if (threadIdx.x == 0) {
-            int t = -1;
-            if (*(volatile uint32_t *)stop == 0) {
-                t = (int)atomicAdd(next, 1u);
-                if (t >= P.total) t = -1;
-            }
-            if (t >= 0) {
-                int lo = p, hi = P.nph - 1;  // last phase whose first tile is <= t
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (P.off[mid] <= t) lo = mid; else hi = mid - 1;
-                }
-                p = lo;
-                const PPhase &ph = P.ph[p];
-                const uint64_t t0 = global_ns();
-                for (int d = 0; d < ph.ndep && t >= 0; ++d) {
-                    const int q = P.deps[ph.dep0 + d];
-                    const uint32_t need = (uint32_t)(P.off[q + 1] - P.off[q]);
-                    for (uint32_t spin = 0; ld_acquire_u32(P.ctr + q) < need; ++spin) {
-                        if (*(volatile uint32_t *)stop) {
-                            t = -1;
-                            break;
+            int p = -1;
+            if (t0 < P.total && *(volatile uint32_t *)stop == 0) {
+                p = (int)(i0 >> 32);
+                if (p != cur) {  // a new phase: its descriptor, then its dependencies
+                    const PPhase &ph = P.ph[p];
+                    s_kind = ph.kind;
+                    s_inst = ph.inst;
+                    s_gx = ph.gx;
+                    const uint64_t ns0 = global_ns();
+                    for (int d = 0; d < ph.ndep && p >= 0; ++d) {
+                        const int q = P.deps[ph.dep0 + d];
+                        const uint32_t need = (uint32_t)(P.off[q + 1] - P.off[q]);
+                        for (uint32_t spin = 0; ld_relaxed_u32(P.ctr + q) < need; ++spin) {
+                            if (*(volatile uint32_t *)stop) {
+                                p = -1;
+                                break;
+                            }
+                            if (global_ns() - ns0 > (uint64_t)P.wait_ns) {
+                                atomicExch(a.err, kErrSchedTimeout);
+                                atomicExch(stop, 1u);
+                                p = -1;
+                                break;
+                            }
+                            __nanosleep(spin < 32 ? 32 : 256);
                         }
-                        if (global_ns() - t0 > (uint64_t)P.wait_ns) {
-                            atomicExch(a.err, kErrSchedTimeout);
-                            atomicExch(stop, 1u);
-                            t = -1;
-                            break;
-                        }
-                        __nanosleep(spin < 16 ? 64 : 512);
                     }
+                    fence_acq_rel_gpu();  // acquire: the dependencies' writes are visible after this
+                    cur = p;
                 }
-                __threadfence();  // as a grid barrier does after its wait
             }
-            s_t = t;
             s_p = p;
+            s_local = (int)(uint32_t)i0;
         }
         __syncthreads();
-        const int t = s_t;
-        if (t < 0) break;
-        p = s_p;
-        const PPhase &ph = P.ph[p];
-        const int local = t - P.off[p], gx = ph.gx;
-        persist_tile<LC, LR>(a, P, ph.kind, ph.inst, local % gx, local / gx, sm);
+        const int p = s_p;
+        if (p < 0) break;
+        const int kind = s_kind, inst = s_inst, gx = s_gx, local = s_local;
+        uint64_t i1 = 0;
+        int t2 = 0;
+        if (threadIdx.x == 0) {  // both complete while the tile runs
+            if (t1 < P.total) i1 = P.info[t1];
+            t2 = (int)atomicAdd(next, 1u);
+        }
+        persist_tile<LC, LR>(a, P, kind, inst, local % gx, local / gx, sm);
         __syncthreads();  // every thread's writes of the tile precede the count
         if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(P.ctr + p, 1u);
+            red_release_add_u32(P.ctr + p, 1u);
+            t0 = t1;
+            i0 = i1;
+            t1 = t2;
         }
     }
 }
@@ -827,10 +878,10 @@ cudaError_t persist_prepare() {
 }
 
 template <int LC, int LR>
-static cudaError_t persist_run(const PProg &P, int max_blocks, cudaStream_t st) {
+static cudaError_t persist_run(const KsArgs &a, const PProg &P, int max_blocks, cudaStream_t st) {
     int grid = std::min(P.total, persist_blocks<LC, LR>());
     if (max_blocks > 0) grid = std::min(grid, max_blocks);
-    k_ks_persist<LC, LR><<<std::max(1, grid), kNttThreads, 0, st>>>(P);
+    k_ks_persist<LC, LR><<<std::max(1, grid), kNttThreads, 0, st>>>(a, P);
     return cudaGetLastError();
 }
 
@@ -898,21 +949,20 @@ static KsArgs ks_args(const Ctx &c) {
     return a;
 }
 
-// key-switch arguments of the context, for the persistent program (which keeps a
-// copy in device memory)
-void persist_args(const Ctx &c, KsArgs *out) { *out = ks_args(c); }
+static KsArgs ks_args(const Ctx &c);
 
 bool persist_supported(const Ctx &c) { return ks_fused_supported(c) && c.alpha <= 2 && c.K <= 2; }
 
 cudaError_t persist_launch(const Ctx &c, const PProg &P, int max_blocks, cudaStream_t st) {
-    if (!persist_supported(c) || !P.args) return cudaErrorInvalidValue;
+    if (!persist_supported(c)) return cudaErrorInvalidValue;
+    const KsArgs a = ks_args(c);
     const bool alt = c.ks_split == 1;
     switch (c.log2n) {
-        case 15: return alt ? persist_run<8, 7>(P, max_blocks, st) : persist_run<7, 8>(P, max_blocks, st);
-        case 14: return alt ? persist_run<6, 8>(P, max_blocks, st) : persist_run<7, 7>(P, max_blocks, st);
-        case 13: return alt ? persist_run<7, 6>(P, max_blocks, st) : persist_run<6, 7>(P, max_blocks, st);
-        case 12: return alt ? persist_run<5, 7>(P, max_blocks, st) : persist_run<6, 6>(P, max_blocks, st);
-        case 11: return alt ? persist_run<6, 5>(P, max_blocks, st) : persist_run<5, 6>(P, max_blocks, st);
+        case 15: return alt ? persist_run<8, 7>(a, P, max_blocks, st) : persist_run<7, 8>(a, P, max_blocks, st);
+        case 14: return alt ? persist_run<6, 8>(a, P, max_blocks, st) : persist_run<7, 7>(a, P, max_blocks, st);
+        case 13: return alt ? persist_run<7, 6>(a, P, max_blocks, st) : persist_run<6, 7>(a, P, max_blocks, st);
+        case 12: return alt ? persist_run<5, 7>(a, P, max_blocks, st) : persist_run<6, 6>(a, P, max_blocks, st);
+        case 11: return alt ? persist_run<6, 5>(a, P, max_blocks, st) : persist_run<5, 6>(a, P, max_blocks, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -110,9 +110,9 @@ struct PMask {
 };
 
 struct PProg {
-    const KsArgs *args;   // the context's key-switch constants (device copy)
     const PPhase *ph;
     const int32_t *off;   // [nph + 1]: first tile of each phase
+    const uint64_t *info; // [total]: tile -> phase << 32 | tile within the phase
     const int32_t *deps;
     const PInst *inst;
     const PMask *mask;
