@@ -48,7 +48,7 @@ IMAD_PER_SM_CLK = 32
 IMAD_PER_MULMOD = 10
 FALLBACK_SM_MAX_MHZ = 2070.0   # the GB300's maximum SM clock, when no measured file exists
 KS_SOURCES = ["paper_2603_04742_gb300/csrc/ks.cu", "paper_2603_04742_gb300/csrc/ntt_core.cuh",
-              "paper_2603_04742_gb300/csrc/modarith.cuh"]
+              "paper_2603_04742_gb300/csrc/modarith.cuh", "paper_2603_04742_gb300/csrc/persist.h"]
 
 
 def parse():
@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep"])
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep", "rot"])
+    ap.add_argument("--persistent", action="store_true",
+                    help="one persistent launch per evaluation (no autotuning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="c3: skip the batched, serving, rotation and boundary-call blocks")
@@ -276,6 +278,10 @@ def kernel_model(name, ring, n_ks, n_chunks, n_parts, n_rot, bfv=None):
                                          + wp * (L * wq + nB * wb)),
                             3 * n * (2 * L + nB) * w),
         })
+    if name == "k_ks_persist":   # the whole evaluation in one launch
+        parts = ["k_ks_intt_rows", "k_ks_modup_cols", "k_ks_rows_fwd", "k_ks_mac", "k_ks_moddown_cols",
+                 "k_ks_rows_final", "k_mask_acc"]
+        return (sum(m[k][0] for k in parts), sum(m[k][1] for k in parts))
     return m.get(name, (0, 0))
 
 
@@ -801,6 +807,14 @@ def main():
         return run_reference(args)
     if args.config == "sweep":
         return run_sweep(args)
+    if args.config == "rot":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0
+        import torch
+        r = rotation_block(args, torch.cuda.current_stream())
+        r.update({"metric": "encrypted SpMV/s (rotation-bearing SpMV at N=2^15)", "higher_is_better": True})
+        print(json.dumps(r), flush=True)
+        return 0
     if args.config == "c5":
         return run_serving(args)
     import torch
@@ -860,7 +874,9 @@ def main():
               for i, (m, (_, xx)) in enumerate(zip(ms, insts))]
     # schedule autotuning (batch sizes, NTT split; results are unchanged)
     tune = None
-    if not args.no_autotune:
+    if args.persistent:
+        ctx.set_tuning(0, 0, 0, 0, 1)
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         tune = ctx.autotune(ms, As, Xs, reps=3)
         tune["seconds"] = time.perf_counter() - t0
