@@ -67,6 +67,27 @@ __device__ __forceinline__ uint64_t mont_lazy(uint64_t a, uint64_t b, uint64_t c
     return hi + __umul64hi(t, m.q) + (lo != 0);
 }
 
+// A sum of products a * b with a < 2^57 and b < 2^51 (at most 64 of them),
+// kept as its three 32-bit partial-product columns: value = s0 + 2^32 sm +
+// 2^64 sh.  Each product costs four 32 x 32 -> 64-bit multiplies; the
+// column sums cannot overflow (a0 b1 + a1 b0 < 2^58 per product, and a carry
+// out of s0 moves 2^32 into sm).
+struct Acc3 {
+    uint64_t s0 = 0, sm = 0, sh = 0;
+};
+__device__ __forceinline__ void mac3(Acc3 &c, uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    const uint64_t p0 = (uint64_t)a0 * b0;
+    c.s0 += p0;
+    c.sm += (uint64_t)a0 * b1 + (uint64_t)a1 * b0 + ((uint64_t)(c.s0 < p0) << 32);
+    c.sh += (uint64_t)a1 * b1;
+}
+// the 128-bit value hi:lo of an Acc3
+__device__ __forceinline__ void fold3(const Acc3 &c, uint64_t &hi, uint64_t &lo) {
+    lo = c.s0 + (c.sm << 32);
+    hi = c.sh + (c.sm >> 32) + (lo < c.s0);
+}
+
 __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
     const uint64_t m = lo * qneg;
     uint64_t r = hi + __umul64hi(m, q) + (lo != 0);
@@ -361,7 +382,7 @@ __device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, con
     if (item >= n) break;
     constexpr int B = DN > 0 ? DN : 1;
     const int dnum = DN > 0 ? DN : a.dnum;
-    uint64_t h0a = 0, l0a = 0, h0b = 0, l0b = 0, h1a = 0, l1a = 0, h1b = 0, l1b = 0;
+    Acc3 c0a, c0b, c1a, c1b;  // (component, coefficient) sums
     // addend terms (Q primes only) and, fused, d = a1 b1
     ulonglong2 own = make_ulonglong2(0, 0);
     if (l < a.L) {
@@ -411,11 +432,10 @@ __device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, con
                 if (ad.mask & 2) y1 = *(const ulonglong2 *)(base + ad.cs);
             }
         }
-        uint64_t p;
-        p = y0.x * pm; l0a += p; h0a += __umul64hi(y0.x, pm) + (l0a < p);
-        p = y0.y * pm; l0b += p; h0b += __umul64hi(y0.y, pm) + (l0b < p);
-        p = y1.x * pm; l1a += p; h1a += __umul64hi(y1.x, pm) + (l1a < p);
-        p = y1.y * pm; l1b += p; h1b += __umul64hi(y1.y, pm) + (l1b < p);
+        mac3(c0a, y0.x, pm);
+        mac3(c0b, y0.y, pm);
+        mac3(c1a, y1.x, pm);
+        mac3(c1b, y1.y, pm);
     }
     for (int j0 = 0; j0 < dnum; j0 += B) {
         ulonglong2 e[B], w0[B], w1[B];
@@ -432,15 +452,19 @@ __device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, con
         }
 #pragma unroll
         for (int u = 0; u < B; ++u) {
-            uint64_t p;
-            p = e[u].x * w0[u].x; l0a += p; h0a += __umul64hi(e[u].x, w0[u].x) + (l0a < p);
-            p = e[u].y * w0[u].y; l0b += p; h0b += __umul64hi(e[u].y, w0[u].y) + (l0b < p);
-            p = e[u].x * w1[u].x; l1a += p; h1a += __umul64hi(e[u].x, w1[u].x) + (l1a < p);
-            p = e[u].y * w1[u].y; l1b += p; h1b += __umul64hi(e[u].y, w1[u].y) + (l1b < p);
+            mac3(c0a, e[u].x, w0[u].x);
+            mac3(c0b, e[u].y, w0[u].y);
+            mac3(c1a, e[u].x, w1[u].x);
+            mac3(c1b, e[u].y, w1[u].y);
         }
     }
     uint64_t *o0 = acc + (item * 2 * LK + l) * N + k;
     uint64_t *o1 = o0 + (int64_t)LK * N;
+    uint64_t h0a, l0a, h0b, l0b, h1a, l1a, h1b, l1b;
+    fold3(c0a, h0a, l0a);
+    fold3(c0b, h0b, l0b);
+    fold3(c1a, h1a, l1a);
+    fold3(c1b, h1b, l1b);
     *(ulonglong2 *)o0 = make_ulonglong2(redc(h0a, l0a, mc.q, mc.qneg), redc(h0b, l0b, mc.q, mc.qneg));
     *(ulonglong2 *)o1 = make_ulonglong2(redc(h1a, l1a, mc.q, mc.qneg), redc(h1b, l1b, mc.q, mc.qneg));
     }
