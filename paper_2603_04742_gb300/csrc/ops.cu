@@ -65,27 +65,47 @@ __global__ void k_cmult(const uint64_t *ct, const uint64_t *pt, uint64_t *out, i
 
 // out = sum_k w_k * mask_k over the nterms ciphertexts w_k = w0 + k * 2LN
 // (Algorithm 4, inter-chunk aggregation); masks in Montgomery form, 128-bit
-// sums reduced once per block of 4096 terms.
-__global__ void k_mask_acc(const uint64_t *w0, const uint64_t *const *masks, int nterms,
-                           uint64_t *out, int64_t total, int log2n, int L, const ModConst *mc) {
-    const int64_t LN = (int64_t)L << log2n;
-    GRID_STRIDE(i, total) {  // total = 2 * L * N
-        const int64_t r = i % LN;
-        const ModConst m = mc[(int)(r >> log2n)];
-        uint64_t s = 0;
-        for (int k0 = 0; k0 < nterms; k0 += 4096) {
-            const int k1 = min(nterms, k0 + 4096);
-            uint64_t hi = 0, lo = 0;
-            for (int k = k0; k < k1; ++k) {
-                const uint64_t a = w0[(int64_t)k * 2 * LN + i], b = masks[k][r];
-                const uint64_t pl = a * b;
-                lo += pl;
-                hi += __umul64hi(a, b) + (lo < pl);
+// sums reduced once per block of 4096 terms.  Each thread takes two
+// consecutive words (16-byte loads); the block stages the mask addresses in
+// shared memory, 256 at a time.
+__global__ __launch_bounds__(256) void k_mask_acc(const uint64_t *w0, const uint64_t *const *masks, int nterms,
+                                                  uint64_t *out, int64_t total, int log2n, int L,
+                                                  const ModConst *mc) {
+    __shared__ const uint64_t *sm_masks[256];
+    const int64_t LN = (int64_t)L << log2n, CT = 2 * LN;
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);  // total = 2LN, even
+    const bool active = i < total;
+    const int64_t r = active ? i % LN : 0;
+    const ModConst m = mc[(int)(r >> log2n)];
+    uint64_t s0 = 0, s1 = 0, h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+    for (int kb = 0; kb < nterms; kb += 256) {
+        const int kn = min(256, nterms - kb);
+        __syncthreads();
+        if ((int)threadIdx.x < kn) sm_masks[threadIdx.x] = masks[kb + threadIdx.x];
+        __syncthreads();
+        if (!active) continue;
+        const uint64_t *w = w0 + (int64_t)kb * CT + i;
+#pragma unroll 4
+        for (int k = 0; k < kn; ++k) {
+            const ulonglong2 a = *(const ulonglong2 *)(w + (int64_t)k * CT);
+            const ulonglong2 b = *(const ulonglong2 *)(sm_masks[k] + r);
+            uint64_t p = a.x * b.x;
+            l0 += p;
+            h0 += __umul64hi(a.x, b.x) + (l0 < p);
+            p = a.y * b.y;
+            l1 += p;
+            h1 += __umul64hi(a.y, b.y) + (l1 < p);
+            if (((kb + k + 1) & 4095) == 0) {  // 4096 terms: reduce before the sum could reach q * 2^64
+                s0 = add_mod(s0, mont_reduce(h0, l0, m.q, m.qneg), m.q);
+                s1 = add_mod(s1, mont_reduce(h1, l1, m.q, m.qneg), m.q);
+                h0 = l0 = h1 = l1 = 0;
             }
-            s = add_mod(s, mont_reduce(hi, lo, m.q, m.qneg), m.q);
         }
-        out[i] = s;
     }
+    if (!active) return;
+    s0 = add_mod(s0, mont_reduce(h0, l0, m.q, m.qneg), m.q);
+    s1 = add_mod(s1, mont_reduce(h1, l1, m.q, m.qneg), m.q);
+    *(ulonglong2 *)(out + i) = make_ulonglong2(s0, s1);
 }
 
 // dst[di[s]] (=, +=) src[si[s]] (through the Galois permutation if perm),
@@ -466,8 +486,12 @@ cudaError_t op_cmult(const Ctx &c, const uint64_t *ct, const uint64_t *pt, uint6
 
 cudaError_t op_mask_acc(const Ctx &c, const uint64_t *w0, const uint64_t *const *masks,
                         int nterms, uint64_t *out, cudaStream_t st) {
-    const int64_t total = (int64_t)2 * c.L * c.N;
-    LAUNCH(k_mask_acc, total, st, w0, masks, nterms, out, total, c.log2n, c.L, c.c->d.mc);
+    const int64_t total = (int64_t)2 * c.L * c.N;  // words; one thread per two
+    const int r = prof_begin(c, "k_mask_acc", st);
+    k_mask_acc<<<(unsigned)((total / 2 + 255) / 256), 256, 0, st>>>(w0, masks, nterms, out, total, c.log2n, c.L,
+                                                                    c.c->d.mc);
+    prof_end(c, r, st);
+    return cudaGetLastError();
 }
 
 cudaError_t op_ct_move(const Ctx &c, uint64_t *dst, const int32_t *di, const uint64_t *src,
