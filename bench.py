@@ -612,6 +612,14 @@ def batched_block(args, stream, persistent=True):
                        cur["persistent"], cur["persist_blocks"])
     out["identical_results"] = bool(same)
     ctx.device_status()
+    del ctx, As, Xs, ys, yp
+    if persistent:   # the key holder's choices: digits of the key switch, rotation keys
+        from paper_2603_04742_gb300.api import tune_keyswitch
+        cand = tune_keyswitch(synth.RING["c4"], insts, reps=3)
+        out["keyswitch_tuning"] = {
+            "candidates": cand,
+            "note": "each candidate has its own keys and ciphertexts (decryptions equal); dnum values "
+                    "with alpha > K are not offered; 'pow2' is the paper's policy and the value above"}
     return out
 
 

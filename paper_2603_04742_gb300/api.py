@@ -617,3 +617,70 @@ class CtBatch:
             self.close()
         except Exception:
             pass
+
+
+def galois_key_count(N, steps, policy):
+    """Galois keys a set of rotation steps needs: one per power of two
+    present in any step (power-of-two chains), or one per distinct step."""
+    half = N // 2
+    ks = {s % half for s in steps} - {0}
+    if policy == "exact":
+        return len(ks)
+    return len({b for s in ks for b in range(s.bit_length()) if (s >> b) & 1})
+
+
+def tune_keyswitch(ring, insts, dnums=None, policies=("pow2", "exact"), reps=3, seed=1, device=0,
+                   schedule=True):
+    """Key-switch decomposition (dnum digits of alpha = ceil(L / dnum) primes)
+    and rotation-key policy for a workload of SpMVs, chosen by measurement.
+
+    Both are the key holder's choices: each candidate gets its own keys and
+    ciphertexts (which differ between candidates; their decryptions do not).
+    For every candidate this creates a context, generates the keys the
+    workload's rotations need, encrypts the instances, applies the schedule
+    autotuner (`schedule`), times the batched evaluation (`reps` runs after a
+    warm-up, CUDA events) and checks that every result decrypts to A.x.
+    Candidates whose alpha exceeds K (the special primes must cover a digit
+    to keep the key-switching noise small) are skipped.  Returns the
+    candidates, fastest first: dnum, alpha, policy, Galois keys, key bytes on
+    the device, ms per batch, SpMV/s, correct."""
+    import torch
+    logn, L, K, dnum0, t = ring
+    N = 1 << logn
+    if dnums is None:
+        dnums = sorted({d for d in range(1, L + 1) if -(-L // d) <= K and -(-L // -(-L // d)) == d} | {dnum0})
+    out = []
+    for d in dnums:
+        alpha = -(-L // d)
+        if alpha > K:
+            continue
+        for pol in policies:
+            ctx = Context(logn, L, K, d, t, rot_policy=pol, device=device)
+            ms_ = [ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A, _ in insts]
+            steps = sorted({s for m in ms_ for s in m.rotation_steps()})
+            ctx.keygen(seed, steps)
+            As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=seed + 1 + i) for i, m in enumerate(ms_)]
+            Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=seed + 1001 + i)
+                  for i, (m, (_, x)) in enumerate(zip(ms_, insts))]
+            if schedule:
+                ctx.autotune(ms_, As, Xs, reps=2)
+            stream = torch.cuda.current_stream()
+            ys = ctx.spmv_batched(ms_, As, Xs, stream=stream)
+            torch.cuda.synchronize()
+            ok = all(list(ctx.decrypt(m, y)) == list(A.matvec(x)) for m, y, (A, x) in zip(ms_, ys, insts))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.spmv_batched(ms_, As, Xs, ys, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_batch = e0.elapsed_time(e1) / reps
+            n_gk = galois_key_count(N, steps, pol)
+            key_bytes = (1 + n_gk) * d * 2 * (L + K) * N * 8
+            out.append({"dnum": d, "alpha": alpha, "policy": pol, "galois_keys": n_gk,
+                        "key_bytes": key_bytes, "ms": ms_batch, "spmv_per_s": len(insts) * 1e3 / ms_batch,
+                        "keyswitches": sum(m.n_chunks + m.n_keyswitch for m in ms_),
+                        "schedule": ctx.get_tuning(), "correct": bool(ok)})
+            del ctx, As, Xs, ys
+    out.sort(key=lambda r: r["ms"])
+    return out
