@@ -18,9 +18,11 @@ rounded half away from zero.  The sum is taken with numpy's FFT (fp64) and
 every coefficient whose fp64 value lies within 2^-6 of a rounding boundary
 is recomputed from the sum itself: exact products z_j * cos (cosines to 40
 digits) summed by math.fsum, so the result is the exact rounding.  Decoding evaluates the centred coefficients at
-zeta^(5^j) (fp64 FFT) and divides by the scale.  There is no rescaling: every
-ciphertext keeps all L primes and the scales multiply (matrix x vector x
-mask), so a SpMV result carries scale 2^(2 scale_bits + mask_scale_bits).
+zeta^(5^j) (fp64 FFT) and divides by the scale.  The SpMV does not rescale:
+every ciphertext keeps all L primes and the scales multiply (matrix x vector
+x mask), so a SpMV result carries scale 2^(2 scale_bits + mask_scale_bits).
+`rescale` (division by the last prime, rounded) is the primitive a deeper
+circuit, or a smaller result to send back, would use.
 """
 import math
 from fractions import Fraction
@@ -28,7 +30,8 @@ from fractions import Fraction
 import mpmath
 import numpy as np
 
-from .bgv import Oracle
+from . import native
+from .bgv import Oracle, _addm
 from .params import Params
 
 # fp64 FFT error on a coefficient stays far below this at the sizes used
@@ -153,3 +156,49 @@ class CkksOracle(Oracle):
 
     def decode_ct(self, ct, n, scale_bits_total):
         return decode(self.decrypt_centered(ct), self.p.N, n, float(2 ** scale_bits_total))
+
+    def rescale(self, ct):
+        """Rescaling (the RNS form of dividing by the last prime; Cheon, Han,
+        Kim, Kim and Song 2018): a ciphertext over q_0..q_{l-1} (NTT domain,
+        l limbs) -> one over q_0..q_{l-2}, each component c replaced by
+        (c - r) / q_{l-1} with r the centred remainder of c mod q_{l-1}
+        (so the quotient is c / q_{l-1} rounded to nearest).  Limb-wise:
+        r is the last limb in coefficient form, centred, lifted to q_i and
+        transformed; c'_i = (c_i - r_i) * q_{l-1}^-1 mod q_i.  The plaintext
+        and the scale are divided by q_{l-1}.  (The SpMV circuit needs no
+        rescaling; this is the primitive a deeper circuit would use.)"""
+        p = self.p
+        nl = ct.shape[1]
+        assert nl >= 2
+        ql = p.q[nl - 1]
+        out = np.zeros((ct.shape[0], nl - 1, p.N), dtype=np.uint64)
+        for c in range(ct.shape[0]):
+            x = self.intt(ct[c, nl - 1], nl - 1)
+            r = [int(v) - ql if int(v) > ql // 2 else int(v) for v in x]
+            for i in range(nl - 1):
+                qi = p.q[i]
+                ri = self.ntt(np.array([v % qi for v in r], dtype=np.uint64), i)
+                inv = pow(ql, qi - 2, qi)
+                diff = [(int(a) - int(b)) % qi for a, b in zip(ct[c, i], ri)]
+                out[c, i] = np.array([d * inv % qi for d in diff], dtype=np.uint64)
+        return out
+
+    def decrypt_level(self, ct):
+        """[c0 + c1 s] over the first l = ct.shape[1] primes, centred, as
+        Python integers (the decryption of a rescaled ciphertext)."""
+        p = self.p
+        nl = ct.shape[1]
+        x = [self.intt(_addm(ct[0, l], native.mulmod(ct[1, l], self.s[l], p.q[l]), p.q[l]), l)
+             for l in range(nl)]
+        Q = 1
+        for l in range(nl):
+            Q *= p.q[l]
+        out = []
+        for k in range(p.N):
+            v = 0
+            for l in range(nl):
+                Qh = Q // p.q[l]
+                v += int(x[l][k]) * (Qh * pow(Qh, -1, p.q[l]) % Q)
+            v %= Q
+            out.append(v - Q if v > Q // 2 else v)
+        return out

@@ -135,3 +135,67 @@ def test_spmv_real_values_within_tolerance():
     ref = A.dense() @ x
     assert len(plan.parts) == 3
     assert np.max(np.abs(y - ref)) <= 1e-3 * max(1.0, np.max(np.abs(ref)))
+
+
+def _crt_centred(res, q):
+    """The integer in (-Q/2, Q/2] with the given residues (Python big ints)."""
+    Q = 1
+    for v in q:
+        Q *= v
+    x = 0
+    for r, v in zip(res, q):
+        Qh = Q // v
+        x += int(r) * Qh * pow(Qh, -1, v)
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+@pytest.mark.parametrize("logn,L", [(5, 3), (6, 4)])
+def test_rescale_is_exact_division_by_the_last_prime(logn, L):
+    """Each coefficient c of each component, as an integer over q_0..q_{L-1},
+    becomes (c - r) / q_{L-1} with r = c mod q_{L-1} centred: checked with
+    big-integer Chinese remaindering against the oracle's limb-wise form."""
+    orc = ckks_oracle(logn=logn, L=L, K=1, dnum=L, scale=20, mscale=10)
+    p = orc.p
+    g = np.random.default_rng(logn)
+    ct = np.stack([np.stack([g.integers(0, p.q[l], size=p.N, dtype=np.uint64) for l in range(L)])
+                   for _ in range(2)])
+    out = orc.rescale(ct)
+    assert out.shape == (2, L - 1, p.N)
+    ql = p.q[L - 1]
+    for c in range(2):
+        coef = [orc.intt(ct[c, l], l) for l in range(L)]
+        got = [orc.intt(out[c, l], l) for l in range(L - 1)]
+        for k in range(p.N):
+            x = _crt_centred([coef[l][k] for l in range(L)], p.q[:L])
+            r = x % ql
+            r = r - ql if r > ql // 2 else r
+            assert (x - r) % ql == 0
+            want = (x - r) // ql
+            for l in range(L - 1):
+                assert int(got[l][k]) == want % p.q[l], (c, k, l)
+
+
+def test_rescale_divides_the_plaintext():
+    """decrypt(rescale(c)) = decrypt(c) / q_{L-1} within (1 + ||s||_1) / 2
+    (the rounding of both components, the second times the ternary secret),
+    and slot values encoded at scale 2^20 q_{L-1} decode at scale 2^20."""
+    orc = ckks_oracle(logn=6, L=3, K=1, dnum=3, scale=20, mscale=10)
+    p = orc.p
+    N = p.N
+    orc.keygen(5, [])
+    ql = p.q[p.L - 1]
+    g = np.random.default_rng(3)
+    z = g.uniform(-1, 1, N // 2)
+    # slots at scale 2^20 * q_{L-1}: the encoding at 2^20 times q_{L-1}
+    # (coefficients of about 2^70, within Q of 3 x 50 bits)
+    m = [v * ql for v in ckks.encode(z, N, 20)]
+    ct = orc.encrypt(m, 4, 0)
+    d0 = orc.decrypt_level(ct)
+    out = orc.rescale(ct)
+    d1 = orc.decrypt_level(out)
+    s1 = int(sum(1 for v in orc.intt(orc.s[0], 0) if v != 0))   # ||s||_1 for a ternary secret
+    bound = (1 + s1) / 2
+    assert max(abs(b * ql - a) for a, b in zip(d0, d1)) <= bound * ql
+    zz = ckks.decode(np.array(d1, dtype=np.float64), N, N // 2, float(2 ** 20))
+    assert np.max(np.abs(zz - z)) < 1e-3
