@@ -383,6 +383,24 @@ int hespmv_decrypt_real_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t i
 int hespmv_decrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctbatch *y,
                         double *out_rows);
 
+/* CKKS rescaling (the paper evaluates one HE-Mult per chunk and keeps every
+ * ciphertext at the top level, so its SpMV needs none; Section 6 names CKKS,
+ * whose deeper circuits rescale after products -- the RNS form of Cheon,
+ * Han, Kim, Kim and Song 2018).  ct: n ciphertexts [n][2][L][N] on the
+ * device (NTT domain, all L primes); out: [n][2][L-1][N], each component c
+ * replaced by (c - r) / q_{L-1}, r the centred remainder of c mod q_{L-1}
+ * (the quotient rounded to nearest), so the plaintext and its scale are
+ * divided by q_{L-1}.  16-byte aligned, out must not alias ct.  CKKS
+ * contexts with L >= 2 only (E_INVALID otherwise).  Enqueued on stream; uses
+ * the context's workspace (3 n N words). */
+int hespmv_rescale(hespmv_ctx *ctx, const uint64_t *ct, uint64_t *out, size_t n, void *stream);
+/* Decrypt one CKKS ciphertext [2][limbs][N] on the device over the first
+ * `limbs` primes (a rescaled ciphertext has L - 1), exact CRT of
+ * [c0 + c1 s] centred, decode the N/2 slots and divide by `scale` (any
+ * positive value: a rescaled scale is 2^k / q_{L-1}).  Synchronous. */
+int hespmv_decrypt_real_level(hespmv_ctx *ctx, const uint64_t *ct, int32_t limbs, double scale,
+                              double *slots_out);
+
 int hespmv_decrypt_slots(hespmv_ctx *ctx, const hespmv_ctbatch *b, size_t index,
                          uint64_t *slots_out);
 

@@ -370,6 +370,19 @@ class Context:
         rc = self.lib.hespmv_selftest_wait_timeout(self.h, byref(code))
         return rc, code.value
 
+    def rescale(self, ct_ptr, out_ptr, n=1, stream=None):
+        """CKKS: out = ct divided by the last prime (hespmv_rescale); device
+        addresses of [n][2][L][N] and [n][2][L-1][N] words."""
+        self.check(self.lib.hespmv_rescale(self.h, c_void_p(ct_ptr), c_void_p(out_ptr), n,
+                                           _stream_handle(stream)))
+
+    def decrypt_real_level(self, ct_ptr, limbs, scale):
+        """CKKS: the N/2 slot values of one ciphertext over its first `limbs`
+        primes, divided by `scale`."""
+        out = np.zeros(self.N // 2, dtype=np.float64)
+        self.check(self.lib.hespmv_decrypt_real_level(self.h, c_void_p(ct_ptr), limbs, float(scale), _f64p(out)))
+        return out
+
     def selftest_persist_timeout(self):
         code = c_int32()
         rc = self.lib.hespmv_selftest_persist_timeout(self.h, byref(code))

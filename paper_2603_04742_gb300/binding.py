@@ -93,6 +93,8 @@ SIGNATURES = {
     "hespmv_device_status": (c_int, [c_void_p, i32p]),
     "hespmv_selftest_wait_timeout": (c_int, [c_void_p, i32p]),
     "hespmv_selftest_persist_timeout": (c_int, [c_void_p, i32p]),
+    "hespmv_rescale": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "hespmv_decrypt_real_level": (c_int, [c_void_p, c_void_p, c_int32, ctypes.c_double, f64p]),
     "hespmv_keys_deserialize": (c_int, [c_void_p, c_void_p, c_size_t]),
     "hespmv_encrypt_real": (c_int, [c_void_p, c_void_p, c_int32, f64p, c_uint64, POINTER(c_void_p)]),
     "hespmv_encode_matrix_plain_real": (c_int, [c_void_p, c_void_p, f64p, POINTER(c_void_p)]),

@@ -2426,6 +2426,73 @@ int hespmv_decrypt_real(hespmv_ctx *ctx, const hespmv_cssc *m, const hespmv_ctba
     return HESPMV_OK;
 }
 
+int hespmv_rescale(hespmv_ctx *ctx, const uint64_t *ct, uint64_t *out, size_t n, void *stream) {
+    if (!ctx || !ct || !out) return HESPMV_E_INVALID;
+    if (ctx->h.scheme != HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "rescaling is defined here for CKKS contexts");
+    if (ctx->h.L < 2) FAIL(HESPMV_E_INVALID, "a rescaled ciphertext needs at least one prime left");
+    NEED_DEVICE(ctx);
+    if (!aligned16({ct, out})) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    if (n == 0) return HESPMV_OK;
+    DeviceGuard g(ctx->device);
+    const Ctx c = view(ctx);
+    const int L = c.L, nl1 = L - 1;
+    const int64_t N = c.N;
+    const uint64_t ql = ctx->h.q[L - 1];
+    if (!ctx->rescale_inv) {  // q_{L-1}^-1 mod q_i, Shoup pairs
+        std::vector<uint64_t> t(2 * nl1);
+        for (int i = 0; i < nl1; ++i) {
+            const uint64_t qi = ctx->h.q[i];
+            uint64_t r = 1, b = ql % qi;
+            for (uint64_t e = qi - 2; e; e >>= 1) {
+                if (e & 1) r = (uint64_t)((unsigned __int128)r * b % qi);
+                b = (uint64_t)((unsigned __int128)b * b % qi);
+            }
+            t[2 * i] = r;
+            t[2 * i + 1] = (uint64_t)(((unsigned __int128)r << 64) / qi);
+        }
+        if (!upload(ctx, ctx->rescale_inv, t)) FAIL(HESPMV_E_NOMEM, "rescale constants upload failed");
+    }
+    const size_t nc = 2 * n;  // components
+    uint64_t *x = workspace(ctx, (nc * N + nc * nl1 * N) * 8);
+    if (!x) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    uint64_t *y = x + nc * N;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the last limb of every component, to coefficient form mod q_{L-1}
+    CK(op_copy_strided(c, ct + (int64_t)nl1 * N, (int64_t)L * N, x, N, N, nc, st));
+    CK(launch_ntt(c, x, L - 1, 1, (int)nc, N, true, st));
+    // centred, lifted to q_0 .. q_{L-2} and back to the NTT domain
+    CK(op_rescale_lift(c, x, y, nc, nl1, ql, st));
+    CK(launch_ntt(c, y, 0, nl1, (int)nc, (int64_t)nl1 * N, false, st));
+    CK(op_rescale_final(c, ct, y, out, nc, nl1, ctx->rescale_inv, st));
+    return HESPMV_OK;
+}
+
+int hespmv_decrypt_real_level(hespmv_ctx *ctx, const uint64_t *ct, int32_t limbs, double scale,
+                              double *slots_out) {
+    if (!ctx || !ct || !slots_out || !(scale > 0)) return HESPMV_E_INVALID;
+    if (ctx->h.scheme != HESPMV_SCHEME_CKKS) FAIL(HESPMV_E_INVALID, "not a CKKS context");
+    if (limbs < 1 || limbs > ctx->h.L) FAIL(HESPMV_E_INVALID, "limbs must be in [1, L]");
+    if (!ctx->have_keys || !ctx->has_sk) FAIL(HESPMV_E_INVALID, "the secret key is needed");
+    NEED_DEVICE(ctx);
+    if (!aligned16(ct)) FAIL(HESPMV_E_INVALID, "device buffers must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    Ctx c = view(ctx);
+    c.L = limbs;  // the first `limbs` primes (and secret-key limbs)
+    const int64_t N = c.N, LN = (int64_t)limbs * N;
+    uint64_t *x = workspace(ctx, LN * 8);
+    if (!x) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
+    CK(op_dec_phase(c, ct, ctx->sk, x, 0));
+    CK(launch_ntt(c, x, 0, limbs, 1, LN, true, 0));
+    std::vector<uint64_t> res(LN);
+    CK(cudaMemcpy(res.data(), x, LN * 8, cudaMemcpyDeviceToHost));
+    CrtReal *crt = crt_real(ctx->h.q.data(), limbs);
+    std::vector<double> coef(N);
+    crt_to_double(*crt, res.data(), (int)N, coef.data());
+    crt_real_free(crt);
+    ckks_decode(*get_codec(ctx), coef.data(), N / 2, 1.0 / scale, slots_out);
+    return HESPMV_OK;
+}
+
 int hespmv_ckks_encode(hespmv_ctx *ctx, const double *z, size_t n, int32_t scale_bits, int64_t *coef) {
     if (!ctx || (!z && n) || !coef || ctx->h.q.empty()) return HESPMV_E_INVALID;
     if (n > (size_t)ctx->h.N / 2) FAIL(HESPMV_E_INVALID, "more values than N/2 slots");

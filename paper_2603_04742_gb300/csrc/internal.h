@@ -268,6 +268,8 @@ struct hespmv_ctx {
     cudaEvent_t slot_free[kSlots] = {};
     bool slot_used[kSlots] = {};
     int aslot = 0;
+    // CKKS rescale: q_{L-1}^-1 mod q_i with Shoup companions, [L-1][2] (device, first use)
+    uint64_t *rescale_inv = nullptr;
     // CKKS encoder tables and CRT constants (host, made on first use)
     hespmv::CkksCodec *codec = nullptr;
     hespmv::CrtReal *crt = nullptr;

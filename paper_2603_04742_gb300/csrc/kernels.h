@@ -142,6 +142,14 @@ cudaError_t op_lift(const Ctx &c, const uint64_t *m, uint64_t *out, size_t n, cu
 // x [L][N] = c0 + c1*s
 cudaError_t op_dec_phase(const Ctx &c, const uint64_t *ct, const uint64_t *s, uint64_t *x,
                          cudaStream_t st);
+// CKKS rescale: x [n_comp][N] last limbs in coefficient form -> y
+// [n_comp][nl1][N] their centred values mod q_0..q_{nl1-1}; then out =
+// (ct - y) * ql^-1 (ct: nl1 + 1 limbs per component, y already in the NTT
+// domain), qinv [nl1][2] Shoup pairs
+cudaError_t op_rescale_lift(const Ctx &c, const uint64_t *x, uint64_t *y, size_t n_comp, int nl1, uint64_t ql,
+                            cudaStream_t st);
+cudaError_t op_rescale_final(const Ctx &c, const uint64_t *ct, const uint64_t *y, uint64_t *out, size_t n_comp,
+                             int nl1, const uint64_t *qinv, cudaStream_t st);
 // x coef [L][N] -> m [N] = ([x]_Q centred) mod t
 cudaError_t op_crt_to_t(const Ctx &c, const uint64_t *x, uint64_t *m, cudaStream_t st);
 // slots[j] = E[slot_idx[j]] for j < N

@@ -447,6 +447,41 @@ __global__ void k_gather_slots(const uint64_t *E, uint64_t *slots, int N, const 
     GRID_STRIDE(j, (int64_t)N) { slots[j] = E[slot_idx[j]]; }
 }
 
+// CKKS rescale, step 2: x [2n][N] holds the last limb of every component in
+// coefficient form ([0, ql)); y [2n][nl1][N] receives its centred value
+// (x - ql when x > ql / 2) reduced mod q_i for i < nl1
+__global__ void k_rescale_lift(const uint64_t *x, uint64_t *y, int64_t total, int log2n, int nl1, uint64_t ql,
+                               const ModConst *mc) {
+    const int64_t N = (int64_t)1 << log2n;
+    GRID_STRIDE(j, total) {  // total = 2n * nl1 * N
+        const int64_t ic = j / (nl1 * N), rem = j - ic * nl1 * N;
+        const int i = (int)(rem >> log2n);
+        const uint64_t v = x[ic * N + (rem & (N - 1))], qi = mc[i].q;
+        uint64_t r;
+        if (v > ql / 2) {  // negative representative v - ql
+            const uint64_t m = (ql - v) % qi;
+            r = m ? qi - m : 0;
+        } else {
+            r = v % qi;
+        }
+        y[j] = r;
+    }
+}
+
+// CKKS rescale, step 4: out[ic][i] = (ct[ic][i] - y[ic][i]) * ql^-1 mod q_i,
+// out [2n][nl1][N]; ct has nl1 + 1 limbs per component; qinv [nl1][2] holds
+// ql^-1 mod q_i with its Shoup companion
+__global__ void k_rescale_final(const uint64_t *ct, const uint64_t *y, uint64_t *out, int64_t total, int log2n,
+                                int nl1, const uint64_t *qinv, const ModConst *mc) {
+    const int64_t N = (int64_t)1 << log2n;
+    GRID_STRIDE(j, total) {
+        const int64_t ic = j / (nl1 * N), rem = j - ic * nl1 * N;
+        const int i = (int)(rem >> log2n);
+        const uint64_t q = mc[i].q, c = ct[ic * (nl1 + 1) * N + rem], v = y[j];
+        out[j] = mul_shoup(c >= v ? c - v : c + q - v, qinv[2 * i], qinv[2 * i + 1], q);
+    }
+}
+
 }  // namespace
 
 #define LAUNCH(kern, total, st, ...)                                  \
@@ -623,6 +658,18 @@ cudaError_t op_dec_phase(const Ctx &c, const uint64_t *ct, const uint64_t *s, ui
                          cudaStream_t st) {
     const int64_t total = (int64_t)c.L * c.N;
     LAUNCH(k_dec_phase, total, st, ct, s, x, total, c.log2n, c.L, c.c->d.mc);
+}
+
+cudaError_t op_rescale_lift(const Ctx &c, const uint64_t *x, uint64_t *y, size_t n_comp, int nl1, uint64_t ql,
+                            cudaStream_t st) {
+    const int64_t total = (int64_t)n_comp * nl1 * c.N;
+    LAUNCH(k_rescale_lift, total, st, x, y, total, c.log2n, nl1, ql, c.c->d.mc);
+}
+
+cudaError_t op_rescale_final(const Ctx &c, const uint64_t *ct, const uint64_t *y, uint64_t *out, size_t n_comp,
+                             int nl1, const uint64_t *qinv, cudaStream_t st) {
+    const int64_t total = (int64_t)n_comp * nl1 * c.N;
+    LAUNCH(k_rescale_final, total, st, ct, y, out, total, c.log2n, nl1, qinv, c.c->d.mc);
 }
 
 cudaError_t op_crt_to_t(const Ctx &c, const uint64_t *x, uint64_t *m, cudaStream_t st) {

@@ -140,3 +140,36 @@ def test_ckks_c3_stencil_float_full_size():
     y = ctx.spmv(m, ca, cx)
     torch.cuda.synchronize()
     assert check_result(ctx, m, y, A, x) < 1e-6
+
+
+def test_ckks_rescale_bit_exact_and_divides_the_scale():
+    """hespmv_rescale of SpMV results equals the oracle's rescale residue for
+    residue (two partitions at once), and the rescaled ciphertexts decrypt
+    over the remaining primes to the same slot values at scale / q_{L-1}."""
+    ctx, orc = pair(10, 3, 1, 3, scale=36, mscale=24, slots=250)
+    A, _ = synth.small_matrix(12, 400, 300, 2000)
+    A, x = real_workload(A, 13)
+    m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    keys(ctx, orc, m, 7)
+    assert m.n_parts == 2
+    ca = ctx.encrypt_real(m, B.HESPMV_MATRIX, A.vals, seed=4)
+    cx = ctx.encrypt_real(m, B.HESPMV_VECTOR, x, seed=5)
+    y = ctx.spmv(m, ca, cx)
+    torch.cuda.synchronize()
+    N, L = 1 << 10, 3
+    out = torch.full((2 * 2 * (L - 1) * N,), -1, dtype=torch.int64, device="cuda")
+    ctx.rescale(y.ptr, out.data_ptr(), n=2)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint64).reshape(2, 2, L - 1, N)
+    gy = y.download()
+    for p in range(2):
+        assert np.array_equal(got[p], orc.rescale(gy[p])), p
+    total = 2 * 36 + 24
+    ql = orc.p.q[L - 1]
+    for p in range(2):
+        before = ctx.decrypt_real_slots(y, p, total)
+        after = ctx.decrypt_real_level(out.data_ptr() + p * 2 * (L - 1) * N * 8, L - 1, 2.0 ** total / ql)
+        assert np.max(np.abs(after - before)) < 1e-6 * max(1.0, np.max(np.abs(before)))
+    # non-CKKS contexts and misaligned buffers are refused on the host
+    with pytest.raises(B.HespmvError):
+        ctx.rescale(y.ptr + 8, out.data_ptr(), n=1)
