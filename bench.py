@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5", "sweep", "rot"])
     ap.add_argument("--persistent", action="store_true",
                     help="one persistent launch per evaluation (no autotuning)")
+    ap.add_argument("--tuning", default=None,
+                    help="a fixed schedule instead of autotuning: mult_batch,rot_batch,ntt_split,rows_tma,"
+                         "persistent,streams (e.g. 14,0,0,0,0,2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="c3: skip the batched, serving, rotation and boundary-call blocks")
@@ -500,9 +503,12 @@ def roofline(ctx, prof, steps, ring, n_ks, n_chunks, n_parts, n_rot, config="c3"
                 "kernel": top,
                 "peak_source": "%s hbm_gbs" % peak_kind}
     roof["algorithmic_per_launch"] = {"mulmods": mm_launch, "bytes": by_launch}
+    step_mm = sum(v["mulmods_per_step"] for v in kernels.values())
+    roof["whole_step"] = {"mulmods": step_mm, "alu_frac_at_profiled_time":
+                          step_mm / (total_ms / steps * 1e-3) / alu_rate if total_ms else None}
     roof["mulmod_rate_measured_T"] = ctx.mulmod_rate(0) / 1e12
     roof["timing"] = ("average launch time of %s over a second pass of the timed steps with "
-                      "CUDA events around each kernel on the launch stream" % top)
+                      "CUDA events around each kernel on the launch stream (one compute stream)" % top)
     return kernels, roof
 
 
@@ -609,7 +615,7 @@ def batched_block(args, stream, persistent=True):
                              "form": "hespmv_spmv_batched with tuning.persistent = 1: one launch per "
                                      "step, HE-Mult groups of 16"}
         ctx.set_tuning(cur["mult_batch"], cur["rot_batch"], cur["ntt_split"], cur["rows_tma"],
-                       cur["persistent"], cur["persist_blocks"])
+                       cur["persistent"], cur["persist_blocks"], cur["streams"])
     out["identical_results"] = bool(same)
     ctx.device_status()
     del ctx, As, Xs, ys, yp
@@ -884,6 +890,10 @@ def main():
     tune = None
     if args.persistent:
         ctx.set_tuning(0, 0, 0, 0, 1)
+    elif args.tuning:
+        v = [int(x) for x in args.tuning.split(",")]
+        ctx.set_tuning(v[0], v[1], v[2], v[3], v[4], 0, v[5])
+        tune = {"fixed": ctx.get_tuning()}
     elif not args.no_autotune:
         t0 = time.perf_counter()
         tune = ctx.autotune(ms, As, Xs, reps=3)
@@ -930,11 +940,21 @@ def main():
     step_ms = {"median": float(np.median(dist_ms)), "p99": float(np.percentile(dist_ms, 99)),
                "runs": int(dist_ms.size)}
 
-    # per-kernel device times (second pass, kernels one by one)
+    # per-kernel device times (second pass, kernels one by one); a schedule
+    # with two compute streams is profiled on one (the same groups), so that
+    # each kernel's time is its own and not shared with a concurrent one
+    tun = ctx.get_tuning()
+    if tun["streams"] == 2:
+        ctx.set_tuning(tun["mult_batch"], tun["rot_batch"], tun["ntt_split"], tun["rows_tma"],
+                       tun["persistent"], tun["persist_blocks"], 1)
+        step()
     ctx.profile_enable(True)
     ms_profiled = time_steps(step, stream, args.steps, lambda: None)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
+    if tun["streams"] == 2:
+        ctx.set_tuning(tun["mult_batch"], tun["rot_batch"], tun["ntt_split"], tun["rows_tma"],
+                       tun["persistent"], tun["persist_blocks"], 2)
 
     extra = {}
     if batched:
@@ -1035,6 +1055,9 @@ def main():
     # the committed DRAM counters are for the BGV kernels of this workload
     if args.scheme != "bgv":
         roof["traffic"] = None
+    # the whole SpMV: every kernel's algorithmic mulmods over the timed step
+    alu_rate, _ = alu_peak()
+    roof["whole_step"]["alu_frac"] = roof["whole_step"]["mulmods"] / (ms_step * 1e-3) / alu_rate
 
     cpu = None
     if not args.no_cpu_baseline and args.scheme == "bgv":

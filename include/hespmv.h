@@ -517,6 +517,11 @@ typedef struct hespmv_tuning {
                            0: staged launches.  Rings with alpha <= 2, K <= 2,
                            N = 2^11 .. 2^15; not BFV.                              */
     int32_t persist_blocks; /* CTAs of the persistent launch (0: all resident)     */
+    int32_t streams;    /* staged device evaluations: 2 = consecutive HE-Mult groups
+                           alternate between two streams (each with its own scratch),
+                           so one group's kernels fill the other's tail waves;
+                           0 or 1 = one stream.  Host-buffer evaluations always use
+                           two when they have two or more groups.                  */
     double ms;          /* hespmv_autotune: device time of one evaluation             */
 } hespmv_tuning;
 

@@ -297,15 +297,17 @@ class Context:
 
     # ---- schedule tuning ----
     def set_tuning(self, mult_batch=0, rot_batch=0, ntt_split=0, rows_tma=0, persistent=0,
-                   persist_blocks=0):
-        t = B.hespmv_tuning(mult_batch, rot_batch, ntt_split, rows_tma, persistent, persist_blocks, 0.0)
+                   persist_blocks=0, streams=1):
+        t = B.hespmv_tuning(mult_batch, rot_batch, ntt_split, rows_tma, persistent, persist_blocks, streams,
+                            0.0)
         self.check(self.lib.hespmv_set_tuning(self.h, byref(t)))
 
     def get_tuning(self):
         t = B.hespmv_tuning()
         self.check(self.lib.hespmv_get_tuning(self.h, byref(t)))
         return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch, "ntt_split": t.ntt_split,
-                "rows_tma": t.rows_tma, "persistent": t.persistent, "persist_blocks": t.persist_blocks}
+                "rows_tma": t.rows_tma, "persistent": t.persistent, "persist_blocks": t.persist_blocks,
+                "streams": t.streams}
 
     def tuning_key(self, ms):
         """Cache key of a workload: device, ring and the stage sizes that the
@@ -332,7 +334,7 @@ class Context:
             if key in table:
                 b = table[key]["best"]
                 self.set_tuning(b["mult_batch"], b["rot_batch"], b["ntt_split"], b.get("rows_tma", 0),
-                                b.get("persistent", 0), b.get("persist_blocks", 0))
+                                b.get("persistent", 0), b.get("persist_blocks", 0), b.get("streams", 1))
                 return {"best": b, "tried": table[key].get("tried", []), "cached": True}
         n = len(ms)
         arr = c_void_p * n
@@ -349,7 +351,7 @@ class Context:
         def as_dict(t):
             return {"mult_batch": t.mult_batch, "rot_batch": t.rot_batch,
                     "ntt_split": t.ntt_split, "rows_tma": t.rows_tma, "persistent": t.persistent,
-                    "persist_blocks": t.persist_blocks, "ms": t.ms}
+                    "persist_blocks": t.persist_blocks, "streams": t.streams, "ms": t.ms}
         out = {"best": as_dict(best), "tried": [as_dict(tried[i]) for i in range(min(cap, nt.value))],
                "cached": False}
         if cache:

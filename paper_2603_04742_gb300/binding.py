@@ -53,7 +53,7 @@ class hespmv_params(ctypes.Structure):
 class hespmv_tuning(ctypes.Structure):
     _fields_ = [("mult_batch", c_int32), ("rot_batch", c_int32), ("ntt_split", c_int32),
                 ("rows_tma", c_int32), ("persistent", c_int32), ("persist_blocks", c_int32),
-                ("ms", ctypes.c_double)]
+                ("streams", c_int32), ("ms", ctypes.c_double)]
 
 
 u64p = POINTER(c_uint64)

@@ -967,6 +967,10 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         for (size_t i = 0; i < n_inst; ++i)
             for (size_t k = 0; k < ms[i]->plan.chunks.size(); ++k) all.push_back({i, k});
         const std::vector<std::pair<size_t, size_t>> groups = mult_groups(pp, all.size());
+        if (!pp.hA && pp.dual) {  // fork the second compute stream
+            CK(cudaEventRecord(ctx->copy_events[0], st));
+            CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->copy_events[0], 0));
+        }
         if (pp.hA) {  // uploads on the side stream, one event per group
             cudaStream_t cs = ctx->copy_stream;
             CK(cudaEventRecord(ctx->copy_events[0], st));  // fork
@@ -1172,20 +1176,24 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
     pp.pkA = pkA;
     pp.pkX = pkX;
     pp.pk_words = (int64_t)packed_ct_words(ctx->h);
-    if (hA) {  // side stream and one event per HE-Mult group (plus the fork)
-        if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-        const size_t n_groups = mult_groups(pp, pp.total_chunks).size();
-        if (!pt_matrix && n_groups > 1) {  // two or more groups: two compute streams
-            if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
-            if (!ctx->join_event) CK(cudaEventCreateWithFlags(&ctx->join_event, cudaEventDisableTiming));
-            pp.dual = true;
-            pp.need_bytes += pp.mult_w * 8;
-        }
-        while (ctx->copy_events.size() < n_groups + 1) {
-            cudaEvent_t e;
-            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            ctx->copy_events.push_back(e);
-        }
+    const size_t n_groups = mult_groups(pp, pp.total_chunks).size();
+    // two or more HE-Mult groups of a host evaluation (always) or of a device
+    // evaluation (schedule choice): two compute streams, groups alternating,
+    // each stream with its own scratch, so one group's kernels fill the
+    // other's tail waves
+    if (!pt_matrix && n_groups > 1 && (hA || ctx->streams == 2)) {
+        if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+        if (!ctx->join_event) CK(cudaEventCreateWithFlags(&ctx->join_event, cudaEventDisableTiming));
+        pp.dual = true;
+        pp.need_bytes += pp.mult_w * 8;
+    }
+    // one event per upload group plus the fork
+    const size_t n_events = hA ? n_groups + 1 : (pp.dual ? 1 : 0);
+    if (hA && !ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    while (ctx->copy_events.size() < n_events) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->copy_events.push_back(e);
     }
     uint64_t *ws = workspace(ctx, pp.need_bytes);
     if (!ws) FAIL(HESPMV_E_NOMEM, "workspace allocation failed");
@@ -2666,11 +2674,13 @@ struct TuneState {
     size_t G, GR;
     int split, rows_tma;
     int persistent = 0, blocks = 0;
+    int streams = 1;
 };
 
 void apply_tuning(hespmv_ctx *ctx, const TuneState &s) {
     if (ctx->tune_G != s.G || ctx->tune_GR != s.GR || ctx->ks_split != s.split ||
-        ctx->rows_tma != s.rows_tma || ctx->persistent != s.persistent || ctx->persist_blocks != s.blocks)
+        ctx->rows_tma != s.rows_tma || ctx->persistent != s.persistent || ctx->persist_blocks != s.blocks ||
+        ctx->streams != s.streams)
         drop_graphs(ctx);
     ctx->tune_G = s.G;
     ctx->tune_GR = s.GR;
@@ -2678,6 +2688,7 @@ void apply_tuning(hespmv_ctx *ctx, const TuneState &s) {
     ctx->rows_tma = s.rows_tma;
     ctx->persistent = s.persistent;
     ctx->persist_blocks = s.blocks;
+    ctx->streams = s.streams;
 }
 
 }  // namespace
@@ -2695,8 +2706,9 @@ int hespmv_set_tuning(hespmv_ctx *ctx, const hespmv_tuning *t) {
     if (t->persistent < 0 || t->persistent > 1 || (t->persistent && !persist_supported(view(ctx))))
         FAIL(HESPMV_E_INVALID, "no persistent evaluation for this ring");
     if (t->persist_blocks < 0) FAIL(HESPMV_E_INVALID, "persist_blocks must be >= 0");
+    if (t->streams < 0 || t->streams > 2) FAIL(HESPMV_E_INVALID, "streams must be 0, 1 or 2");
     const TuneState ts{(size_t)t->mult_batch, (size_t)t->rot_batch, t->ntt_split, t->rows_tma, t->persistent,
-                       t->persist_blocks};
+                       t->persist_blocks, t->streams == 2 ? 2 : 1};
     if (ctx->device >= 0) {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
@@ -2728,6 +2740,7 @@ int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t) {
     t->rows_tma = ctx->rows_tma;
     t->persistent = ctx->persistent;
     t->persist_blocks = ctx->persist_blocks;
+    t->streams = ctx->streams;
     t->ms = 0;
     return HESPMV_OK;
 }
@@ -2790,6 +2803,8 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         rec.rows_tma = s.rows_tma;
         rec.persistent = s.persistent;
         rec.persist_blocks = s.blocks;
+        rec.streams = s.streams;
+        if (s.streams == 2 && total > pp.G) pp.need_bytes += pp.mult_w * 8;  // the second stream's scratch
         if (s.persistent) {  // one launch: HE-Mult group G, concurrent totalSum chains
             const size_t Gp = persist_group(ctx, total);
             pp.need_bytes = persist_ws_words(c, total, rot, Gp) * 8;
@@ -2854,6 +2869,15 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         const TuneState base = bestS;
         for (size_t v : grs) consider({base.G, v, base.split, base.rows_tma});
     }
+    // two compute streams: the HE-Mult groups alternate between them (groups of
+    // about a half and a quarter of the chunks, and the best group so far)
+    if (total > 1) {
+        const TuneState base = bestS;
+        std::set<size_t> gd;
+        for (size_t v : {(total + 1) / 2, (total + 3) / 4, base.G ? base.G : (size_t)32})
+            if (v >= 1 && v < total) gd.insert(v);
+        for (size_t v : gd) consider({v, base.GR, base.split, base.rows_tma, 0, 0, 2});
+    }
     // the persistent form: HE-Mult groups of 4, 16, 64 (capped), then the other NTT split
     if (persist_supported(c) && ctx->h.scheme != HESPMV_SCHEME_BFV) {
         const TuneState staged = bestS;
@@ -2880,6 +2904,7 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
     best->rows_tma = bestS.rows_tma;
     best->persistent = bestS.persistent;
     best->persist_blocks = bestS.blocks;
+    best->streams = bestS.streams;
     if (bestS.persistent) {
         best->mult_batch = (int32_t)persist_group(ctx, total);
         best->rot_batch = bestS.GR ? (int32_t)bestS.GR : kPersistStagger;

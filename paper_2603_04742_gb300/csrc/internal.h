@@ -244,6 +244,7 @@ struct hespmv_ctx {
     int rows_tma = 0;    // fused key switch: persistent TMA-fed forward row pass
     int persistent = 0;  // 1: one persistent launch per evaluation (tune_G = its HE-Mult group)
     int persist_blocks = 0;  // CTAs of the persistent launch (0: every resident CTA)
+    int streams = 1;     // device evaluations: HE-Mult groups alternate over 1 or 2 streams
     // persistent evaluation programs, keyed by matrices, buffers, workspace and group
     std::map<std::vector<uint64_t>, hespmv::PersistPlan *> persist_plans;
     // staging for evaluations from host buffers, and the side stream and

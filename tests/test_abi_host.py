@@ -160,19 +160,21 @@ def test_server_needs_a_device_context():
 def test_tuning_round_trip_and_validation():
     ctx = host_ctx("c3")
     zero = {"mult_batch": 0, "rot_batch": 0, "ntt_split": 0, "rows_tma": 0, "persistent": 0,
-            "persist_blocks": 0}
+            "persist_blocks": 0, "streams": 1}
     assert ctx.get_tuning() == zero
     ctx.set_tuning(8, 16, 1, 1)
     want = dict(zero, mult_batch=8, rot_batch=16, ntt_split=1, rows_tma=1)
     assert ctx.get_tuning() == want
     for bad in [(-1, 0, 0), (0, -2, 0), (0, 0, 2), (5000, 0, 0), (0, 0, 0, 2), (0, 0, 0, 0, 2),
-                (0, 0, 0, 0, 1, -1)]:
+                (0, 0, 0, 0, 1, -1), (0, 0, 0, 0, 0, 0, 3)]:
         with pytest.raises(B.HespmvError) as e:
             ctx.set_tuning(*bad)
         assert e.value.code == B.HESPMV_E_INVALID
     assert ctx.get_tuning() == want
     ctx.set_tuning(16, 0, 0, 0, 1, 7)   # the persistent form (alpha = 2, K = 2: supported)
     assert ctx.get_tuning() == dict(zero, mult_batch=16, persistent=1, persist_blocks=7)
+    ctx.set_tuning(14, 0, 0, 0, 0, 0, 2)   # HE-Mult groups over two streams
+    assert ctx.get_tuning() == dict(zero, mult_batch=14, streams=2)
     small = Context(10, 3, 1, 3, 40961, device=-1, torch_alloc=False)   # unfused key switch
     with pytest.raises(B.HespmvError):
         small.set_tuning(0, 0, 1)

@@ -51,9 +51,11 @@ def test_autotune_results_identical_and_cached(logn, tmp_path):
     assert {r["ntt_split"] for r in timed} == {0, 1}
     assert {r["rows_tma"] for r in timed} == {0, 1}
     assert {r["persistent"] for r in timed} == {0, 1}
+    assert {r["streams"] for r in timed} == {1, 2}
     # every schedule timed gives the same ciphertexts
     for r in timed:
-        ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"])
+        ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"], 0,
+                       r["streams"])
         ys = ctx.spmv_batched(ms, As, Xs)
         torch.cuda.synchronize()
         for y, z in zip(ys, ref_bytes):
@@ -65,6 +67,7 @@ def test_autotune_results_identical_and_cached(logn, tmp_path):
     b = res["best"]
     assert ctx.get_tuning() == {"mult_batch": b["mult_batch"], "rot_batch": b["rot_batch"],
                                 "ntt_split": b["ntt_split"], "rows_tma": b["rows_tma"],
-                                "persistent": b["persistent"], "persist_blocks": b["persist_blocks"]}
+                                "persistent": b["persistent"], "persist_blocks": b["persist_blocks"],
+                                "streams": b["streams"]}
     ctx.device_status()
     assert os.path.exists(cache)

@@ -112,7 +112,8 @@ def test_batched_ring_every_autotuned_schedule_matches_oracle(batched_ring):
     assert len(timed) >= 3
     try:
         for r in timed:
-            ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"])
+            ctx.set_tuning(r["mult_batch"], r["rot_batch"], r["ntt_split"], r["rows_tma"], r["persistent"], 0,
+                           r["streams"])
             ys = ctx.spmv_batched(ms, As, Xs)
             torch.cuda.synchronize()
             _assert_equal_results(ys, want, r)
