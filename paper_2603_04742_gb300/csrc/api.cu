@@ -523,6 +523,10 @@ struct SpmvPrep {
     // tensor / key-switch scratch of mult_w words
     bool dual = false;
     size_t mult_w = 0;
+    // totalSum rotation groups (GR chunks each, independent of one another)
+    // alternate between the two streams, each with its own rot_w words
+    bool dual_rot = false;
+    size_t rot_w = 0;
     // HE-Mult group sizes of a host evaluation (empty: groups of G)
     std::vector<size_t> gsz;
     // pipelined host evaluation: the uploads wait for this event (or nothing)
@@ -581,6 +585,7 @@ void spmv_sizes(const Ctx &c, size_t total_chunks, size_t rot_chunks, SpmvPrep &
     const size_t mult_w = pp.G * 3 * LN + std::max(ks_words(c, pp.G), tensor_scratch_words(c, pp.G));
     const size_t rot_w = rot_chunks ? 4 * pp.GR * CT + ks_words(c, pp.GR) : 0;
     pp.mult_w = mult_w;
+    pp.rot_w = rot_w;
     pp.need_bytes = (prod_w + std::max(mult_w, rot_w)) * 8;
 }
 
@@ -1049,13 +1054,29 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
             CK(cudaStreamWaitEvent(st, ctx->join_event, 0));
         }
     }
-    // 2) totalSum: batched rotation rounds
+    // 2) totalSum: batched rotation rounds; groups of GR chunks are
+    //    independent, and alternate between two streams when dual_rot
     if (pp.rp) {
         Range r("hespmv: totalSum rotations");
         uint64_t *V = dbuf, *CUR = V + GR * CT, *PB = CUR + GR * CT, *OB = PB + GR * CT;
         uint64_t *ks = OB + GR * CT;
         const int32_t *I = pp.rp->d_idx;
+        const cudaStream_t st0 = st;
+        if (pp.dual_rot) {  // fork: every HE-Mult product is ready on st
+            CK(cudaEventRecord(ctx->copy_events[0], st0));
+            CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->copy_events[0], 0));
+        }
+        int64_t gi = -1;
         for (const RotOp &o : pp.rp->ops) {
+            if (o.kind == RotOp::kVInit && pp.dual_rot) {  // a new group: its stream and scratch
+                ++gi;
+                st = (gi & 1) ? ctx->aux_stream : st0;
+                V = dbuf + ((gi & 1) ? pp.rot_w : 0);
+                CUR = V + GR * CT;
+                PB = CUR + GR * CT;
+                OB = PB + GR * CT;
+                ks = OB + GR * CT;
+            }
             switch (o.kind) {
                 case RotOp::kVInit:
                     CK(op_ct_move(c, V, nullptr, prod, I + o.b, nullptr, false, o.m, st));
@@ -1085,6 +1106,11 @@ int spmv_enqueue(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
                     CK(op_ct_move(c, prod, I + o.a, CUR, I + o.b, nullptr, true, o.m, st));
                     break;
             }
+        }
+        st = st0;
+        if (pp.dual_rot) {  // join
+            CK(cudaEventRecord(ctx->join_event, ctx->aux_stream));
+            CK(cudaStreamWaitEvent(st, ctx->join_event, 0));
         }
     }
     // 3) masked accumulation per partition
@@ -1187,8 +1213,15 @@ int spmv_core(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms,
         pp.dual = true;
         pp.need_bytes += pp.mult_w * 8;
     }
+    // two or more rotation groups: alternate them over two streams too
+    if (ctx->streams == 2 && pp.rp && pp.rot_chunks > pp.GR) {
+        if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+        if (!ctx->join_event) CK(cudaEventCreateWithFlags(&ctx->join_event, cudaEventDisableTiming));
+        pp.dual_rot = true;
+        pp.need_bytes = std::max(pp.need_bytes, (pp.total_chunks * 2 * (size_t)ctx->h.L * ctx->h.N + 2 * pp.rot_w) * 8);
+    }
     // one event per upload group plus the fork
-    const size_t n_events = hA ? n_groups + 1 : (pp.dual ? 1 : 0);
+    const size_t n_events = std::max<size_t>(hA ? n_groups + 1 : (pp.dual ? 1 : 0), pp.dual_rot ? 1 : 0);
     if (hA && !ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     while (ctx->copy_events.size() < n_events) {
         cudaEvent_t e;
@@ -2805,6 +2838,8 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         rec.persist_blocks = s.blocks;
         rec.streams = s.streams;
         if (s.streams == 2 && total > pp.G) pp.need_bytes += pp.mult_w * 8;  // the second stream's scratch
+        if (s.streams == 2 && rot > pp.GR)
+            pp.need_bytes = std::max(pp.need_bytes, (total * 2 * (size_t)c.L * c.N + 2 * pp.rot_w) * 8);
         if (s.persistent) {  // one launch: HE-Mult group G, concurrent totalSum chains
             const size_t Gp = persist_group(ctx, total);
             pp.need_bytes = persist_ws_words(c, total, rot, Gp) * 8;
@@ -2877,6 +2912,13 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         for (size_t v : {(total + 1) / 2, (total + 3) / 4, base.G ? base.G : (size_t)32})
             if (v >= 1 && v < total) gd.insert(v);
         for (size_t v : gd) consider({v, base.GR, base.split, base.rows_tma, 0, 0, 2});
+    }
+    if (rot > 1) {  // rotation groups over two streams: about a half and a quarter of the rotating chunks
+        const TuneState base = bestS;
+        std::set<size_t> gr;
+        for (size_t v : {(rot + 1) / 2, (rot + 3) / 4})
+            if (v >= 1 && v < rot) gr.insert(v);
+        for (size_t v : gr) consider({base.G, v, base.split, base.rows_tma, 0, 0, 2});
     }
     // the persistent form: HE-Mult groups of 4, 16, 64 (capped), then the other NTT split
     if (persist_supported(c) && ctx->h.scheme != HESPMV_SCHEME_BFV) {

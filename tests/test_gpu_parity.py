@@ -237,6 +237,14 @@ def test_spmv_many_chunks_ragged_batches_parity(logn, rows, nnz, slots):
     orc.keygen(4, sorted({g for k in steps for g in orc.rotation_elements(k)}))
     m2, y, out, oout = run_spmv_pair(ctx, orc, A, x)
     assert list(out) == list(A.matvec(x)) == list(oout)
+    # HE-Mult groups and totalSum rotation groups alternating over two streams
+    want = y.download()
+    ctx.set_tuning(7, 10, 0, 0, 0, 0, 2)
+    ca = ctx.encrypt(m2, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m2, B.HESPMV_VECTOR, x=x, seed=3)
+    for _ in range(2):   # capture, then replay
+        assert np.array_equal(ctx.spmv(m2, ca, cx).download(), want)
+    ctx.set_tuning(0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("policy", ["pow2", "exact"])
