@@ -319,12 +319,13 @@ class OracleSample:
         return time.perf_counter() - t0
 
 
-def _allcores_worker(w, nw, A, x, ring, seeds, go, out):
+def _allcores_worker(w, nw, A, x, ring, seeds, inbox, out):
     """Worker w of nw: the oracle's cloud evaluation (HE-Mult with
     relinearisation, totalSum, mask product, partial sum per partition) of
-    chunks w, w + nw, ...; keys and encryptions are made first, the
-    evaluation starts when `go` is set and its end time (the system's
-    monotonic clock) is reported with the partial sums."""
+    chunks w, w + nw, ...; keys and encryptions are made first, then each
+    token from `inbox` starts one evaluation (None ends the worker), whose
+    end time (the system's monotonic clock) is reported with the partial
+    sums."""
     from oracle import spmv as S
     from oracle.bgv import Oracle
     from oracle.params import Params
@@ -343,13 +344,16 @@ def _allcores_worker(w, nw, A, x, ring, seeds, go, out):
     work = [(part_of[i], chunks[i], orc.encrypt(orc.encode(chunks[i].values), seeds[1], i),
              orc.encrypt(orc.encode(reorg[i]), seeds[2], i)) for i in sel]
     out.put(("ready", w, None))
-    go.wait()
-    sums = {}
-    for p, ch, a, b in work:   # Algorithm 1 (HE-Mult), Algorithm 4 (totalSum, mask)
-        v = S.total_sum(orc, orc.mult(a, b), ch.h, ch.c)
-        v = orc.cmult(v, S.mask_ntt(orc, ch.h))
-        sums[p] = orc.add(sums[p], v) if p in sums else v
-    out.put(("done", time.perf_counter(), {p: v.tobytes() for p, v in sums.items()}))
+    while True:
+        tok = inbox.get()
+        if tok is None:
+            return
+        sums = {}
+        for p, ch, a, b in work:   # Algorithm 1 (HE-Mult), Algorithm 4 (totalSum, mask)
+            v = S.total_sum(orc, orc.mult(a, b), ch.h, ch.c)
+            v = orc.cmult(v, S.mask_ntt(orc, ch.h))
+            sums[p] = orc.add(sums[p], v) if p in sums else v
+        out.put(("done", time.perf_counter(), {p: v.tobytes() for p, v in sums.items()} if tok else None))
 
 
 def _collect(out, procs, n, kind, limit_s):
@@ -367,11 +371,13 @@ def _collect(out, procs, n, kind, limit_s):
     return got
 
 
-def oracle_allcores(A, x, ring, seeds, cores=None, limit_s=900):
+def oracle_allcores(A, x, ring, seeds, cores=None, steps=1, limit_s=900, budget_s=None):
     """The oracle's cloud evaluation of a whole SpMV on every host core:
     one spawned process per core, chunks dealt round robin, partial sums
-    added per partition.  Returns (seconds from the start signal to the last
-    worker's end, cores, result ciphertexts [n_parts][2][L][N])."""
+    added per partition.  Runs `steps` evaluations (fewer once `budget_s`
+    seconds of them have run).  Returns (seconds of each evaluation, from
+    its start signal to its last worker's end; cores; result ciphertexts
+    [n_parts][2][L][N] of the last evaluation)."""
     import multiprocessing as mp
     from oracle import spmv as S
     from oracle.bgv import Oracle
@@ -379,65 +385,79 @@ def oracle_allcores(A, x, ring, seeds, cores=None, limit_s=900):
     logn, L, K, dnum, t = ring
     cores = cores or os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    go, out = ctx.Event(), ctx.Queue()
-    procs = [ctx.Process(target=_allcores_worker, args=(w, cores, A, x, ring, seeds, go, out), daemon=True)
-             for w in range(cores)]
+    out = ctx.Queue()
+    inboxes = [ctx.Queue() for _ in range(cores)]
+    procs = [ctx.Process(target=_allcores_worker, args=(w, cores, A, x, ring, seeds, inboxes[w], out),
+                         daemon=True) for w in range(cores)]
+    times, done = [], None
     try:
         for p in procs:
             p.start()
         _collect(out, procs, cores, "ready", limit_s)
-        t0 = time.perf_counter()
-        go.set()
-        done = _collect(out, procs, cores, "done", limit_s)
+        for k in range(steps):
+            last = k + 1 == steps or (budget_s is not None and sum(times) > budget_s)
+            t0 = time.perf_counter()
+            for q in inboxes:
+                q.put(bool(last))
+            done = _collect(out, procs, cores, "done", limit_s)
+            times.append(max(m[1] for m in done) - t0)
+            if last:
+                break
     finally:
+        for q in inboxes:
+            q.put(None)
         for p in procs:
             p.join(timeout=5)
             if p.is_alive():
                 p.terminate()
-    dt = max(m[1] for m in done) - t0
     orc = Oracle(Params(log2n=logn, L=L, K=K, dnum=dnum, t=t))
     n_parts = len(S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots).parts)
     res = [np.zeros((2, L, 1 << logn), dtype=np.uint64) for _ in range(n_parts)]
     for m in done:
         for p, b in m[2].items():
             res[p] = orc.add(res[p], np.frombuffer(b, dtype=np.uint64).reshape(2, L, 1 << logn))
-    return dt, cores, res
+    return times, cores, res
 
 
 REFERENCE_SECONDS = 150.0
 
 
 def run_reference(args):
-    """The oracle on the host cores: each step evaluates one chunk of the
-    workload; SpMV/s = 1 / (seconds per chunk x chunks per SpMV)."""
+    """The oracle as the reference arm, on every host core: each step is the
+    oracle's cloud evaluation of the whole SpMV (every chunk; one spawned
+    process per core, chunks dealt round robin, keys and encryptions made
+    before the first step), timed from its start signal to the last worker's
+    end; past REFERENCE_SECONDS of steps the remaining ones are not run (the
+    line says how many ran).  The result is decrypted and compared with A.x."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import spmv as S
+    from oracle.bgv import Oracle
+    from oracle.params import Params
     A, x, ring = load_workload(args.config)
-    smp = OracleSample(A, x, ring, 1)
-    times = []
-    for i in range(args.warmup + args.steps):
-        dt = smp.run()
-        if i >= args.warmup:
-            times.append(dt)
-        # one oracle chunk takes about a second at N = 2^15: past the time
-        # bound the remaining steps are not run (reported below)
-        if i >= args.warmup and sum(times) > REFERENCE_SECONDS:
-            break
-    n_total = smp.n_total
-    per_chunk = sum(times) / len(times)
-    value = 1.0 / (per_chunk * n_total)
+    seeds = (1, 2, 3)
+    times, cores, res = oracle_allcores(A, x, ring, seeds, steps=args.warmup + args.steps,
+                                        budget_s=REFERENCE_SECONDS)
+    timed = times[args.warmup:] or times[-1:]
+    per = sum(timed) / len(timed)
+    value = 1.0 / per
+    logn, L, K, dnum, t = ring
+    orc = Oracle(Params(log2n=logn, L=L, K=K, dnum=dnum, t=t))
+    orc.keygen(seeds[0], [])
+    plan = S.SpmvPlan(A.rows, A.cols, A.rowptr, A.colidx, A.vals, orc.p.slots)
+    correct = list(S.decrypt_result(orc, plan, res)) == list(A.matvec(x))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SpMV/s",
-            "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": per_chunk * n_total * 1e3, "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": len(timed), "steps_requested": args.steps,
+            "warmup": min(args.warmup, len(times) - len(timed)),
+            "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": CONFIGS[args.config]},
-            "nnz_per_s": value * A.nnz,
-            "cpu_baseline": {"value": value, "unit": "SpMV/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: the oracle's cloud evaluation of 1 of %d chunks "
-                                       "(HE-Mult, relinearisation, totalSum, mask, add); "
-                                       "extrapolated by the chunk count" % n_total},
+            "nnz_per_s": value * A.nnz, "correct": bool(correct),
+            "cpu_baseline": {"value": value, "unit": "SpMV/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: the oracle's cloud evaluation of the whole SpMV "
+                                       "(all %d chunks: HE-Mult, relinearisation, totalSum, mask, "
+                                       "add) on %d spawned processes, one per core" % (len(plan.chunks), cores)},
             "e2e": {"value": value, "unit": "SpMV/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -1078,7 +1098,8 @@ def main():
             # every host core: the whole SpMV, one process per core; its result
             # ciphertext is compared with the GPU's
             try:
-                dta, cores, res = oracle_allcores(A0, x0, ring, (1 + rank, 2 + 1000 * rank, 3 + 1000 * rank))
+                dts, cores, res = oracle_allcores(A0, x0, ring, (1 + rank, 2 + 1000 * rank, 3 + 1000 * rank))
+                dta = dts[-1]
                 gy = ys[0].download()
                 cpu["all_cores"] = {"value": 1.0 / dta, "unit": "SpMV/s", "cores": cores, "kind": "oracle",
                                     "seconds": dta, "nproc": os.cpu_count(),
