@@ -281,6 +281,14 @@ def test_spmv_c3_full_size_parity_and_tolerance():
     m, y, out, oout = run_spmv_pair(ctx, orc, A, x)
     exact = A.matvec(x)
     assert list(out) == list(exact)
+    # the autotuned schedule of this workload: groups of 14 and 13 on two streams
+    ref = y.download()
+    ctx.set_tuning(14, 0, 0, 0, 0, 0, 2)
+    ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
+    cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
+    for _ in range(2):
+        assert np.array_equal(ctx.spmv(m, ca, cx).download(), ref)
+    ctx.set_tuning(0, 0, 0, 0)
     # fixed point: result scale 2^30, tolerance 1e-3 relative in the max norm
     A.vals = Af
     yref = A.matvec(xf)
@@ -312,6 +320,14 @@ def test_spmv_no_rotation_partitions_parity():
     assert m.n_rot == 0 and m.n_parts == 2
     assert list(out) == list(A.matvec(x)) == list(oout)
     ref = y.download()
+    # two streams: HE-Mult groups alternating between them, one group
+    # spanning the partition boundary (G = 3), one not (G = 5)
+    for G in (3, 5):
+        ctx.set_tuning(G, 0, 0, 0, 0, 0, 2)
+        for _ in range(2):
+            assert np.array_equal(ctx.spmv(m, ctx.encrypt(m, B.HESPMV_MATRIX, seed=2),
+                                           ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)).download(), ref), G
+    ctx.set_tuning(0, 0, 0, 0)
     ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=2)
     cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=3)
     for _ in range(2):   # capture, then replay
