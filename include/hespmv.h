@@ -535,11 +535,15 @@ int hespmv_get_tuning(const hespmv_ctx *ctx, hespmv_tuning *t);
  * would run them, into its own result buffers, on its own stream) under
  * candidate schedules -- each NTT split, each row-pass form, then HE-Mult
  * batches 1, 2, 4, ... up to 128, then rotation round widths 4, 8, ... up to
- * 512 (capped by the chunk counts) -- by coordinate descent from the
- * default, `reps` timed evaluations after one warm-up each, skipping any
- * whose workspace would not fit in free device memory.  Applies the fastest
- * and returns it in *best; tried[0 .. min(cap, *n_tried)) lists every
- * setting timed (effective batch sizes; ms = -1: skipped).  Synchronous. */
+ * 512 (capped by the chunk counts), then two compute streams with HE-Mult
+ * batches of about a half and a quarter of the chunks and rotation rounds of
+ * about a half and a quarter of the rotating chunks, then every NTT split and
+ * row-pass form again under the best so far, then the persistent form with
+ * HE-Mult groups of 4, 16 and 64 -- by coordinate descent from the default,
+ * `reps` timed evaluations after one warm-up each, skipping any whose
+ * workspace would not fit in free device memory.  Applies the fastest and
+ * returns it in *best; tried[0 .. min(cap, *n_tried)) lists every setting
+ * timed (effective batch sizes; ms = -1: skipped).  Synchronous. */
 int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
                     const hespmv_ctbatch *const *A, const hespmv_ctbatch *const *X, int32_t reps,
                     hespmv_tuning *best, hespmv_tuning *tried, size_t cap, size_t *n_tried);

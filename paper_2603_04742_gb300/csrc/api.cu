@@ -787,8 +787,10 @@ int persist_build(hespmv_ctx *ctx, size_t n_inst, const hespmv_cssc *const *ms, 
             HostPhase h;
             for (int32_t q = 0; q < Pt.n_chunks; ++q) {
                 const size_t g = g0 + Pt.chunk0 + q;
+                auto mit = ctx->masks.find(pl.chunks[Pt.chunk0 + q].h);
+                if (mit == ctx->masks.end()) FAIL(HESPMV_E_INVALID, "mask plaintext missing");
                 tabs[tt].push_back(term[g]);
-                tabs[tt + 1].push_back(ctx->masks.at(pl.chunks[Pt.chunk0 + q].h));
+                tabs[tt + 1].push_back(mit->second);
                 h.deps.push_back(last_ph[g]);
                 h.grp = std::max(h.grp, (int32_t)(g / G));
             }
@@ -2919,6 +2921,14 @@ int hespmv_autotune(hespmv_ctx *ctx, size_t n, const hespmv_cssc *const *m,
         for (size_t v : {(rot + 1) / 2, (rot + 3) / 4})
             if (v >= 1 && v < rot) gr.insert(v);
         for (size_t v : gr) consider({base.G, v, base.split, base.rows_tma, 0, 0, 2});
+    }
+    // the NTT split and the row-pass form again, under the best staged schedule
+    if (ks_fused_supported(c)) {
+        const TuneState base = bestS;
+        for (int v = 0; v < ks_split_variants(c); ++v)
+            for (int tma = 0; tma <= 1; ++tma)
+                if (v != base.split || tma != base.rows_tma)
+                    consider({base.G, base.GR, v, tma, 0, 0, base.streams});
     }
     // the persistent form: HE-Mult groups of 4, 16, 64 (capped), then the other NTT split
     if (persist_supported(c) && ctx->h.scheme != HESPMV_SCHEME_BFV) {
