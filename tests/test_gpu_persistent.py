@@ -138,3 +138,39 @@ def test_persistent_dependency_wait_times_out_and_context_survives():
     ca = ctx.encrypt(m, B.HESPMV_MATRIX, seed=1)
     cx = ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=2)
     assert list(ctx.decrypt(m, ctx.spmv(m, ca, cx))) == list(A.matvec(x))
+
+
+def test_persistent_degenerate_matrices():
+    """The persistent program of an all-zero matrix (no chunk: zero result
+    ciphertexts), of a single non-zero, and a batch mixing them with an
+    ordinary matrix, over poisoned result buffers."""
+    from paper_2603_04742_gb300.api import Context, CtBatch
+    logn, L, K, dnum, t = synth.RING["c1"]
+    ctx = Context(logn, L, K, dnum, t, slots=64)
+    ctx.keygen(2)
+    ctx.set_tuning(0, 0, 0, 0, 1, 0)
+    zero = synth.CSR(4, 4, np.zeros(5, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    one = synth.CSR(3, 3, np.array([0, 0, 1, 1]), np.array([2], np.int32), np.array([7]))
+    big, xb = synth.small_matrix(4, 200, 150, 900)
+    cases = [(zero, np.zeros(4, np.int64)), (one, np.array([1, 2, 3])), (big, xb)]
+    ms, As, Xs = [], [], []
+    for A, x in cases:
+        m = ctx.encode_cssc(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        ms.append(m)
+        As.append(ctx.encrypt(m, B.HESPMV_MATRIX, seed=1))
+        Xs.append(ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=2))
+    CT = 2 * L * (1 << logn)
+    for single in (True, False):
+        ys = [CtBatch.create(ctx, m.n_parts) for m in ms]
+        for y, m in zip(ys, ms):
+            y.upload(np.full(m.n_parts * CT, np.iinfo(np.uint64).max, dtype=np.uint64))
+        if single:
+            for m, a, xx, y in zip(ms, As, Xs, ys):
+                ctx.spmv(m, a, xx, y=y)
+        else:
+            ctx.spmv_batched(ms, As, Xs, ys)
+        torch.cuda.synchronize()
+        assert not np.any(ys[0].download())
+        for (A, x), m, y in zip(cases, ms, ys):
+            assert list(ctx.decrypt(m, y)) == list(A.matvec(x)), single
+    ctx.device_status()
