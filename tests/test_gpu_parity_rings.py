@@ -186,3 +186,78 @@ def test_serving_ring_served_mix_matches_oracle(serving_ring):
     assert srv.stop(10000) == B.HESPMV_OK
     assert all(d == 1 for d in done) and st["batches"] >= 2
     _assert_equal_results(ys, [want[i] for i in reqs], "served")
+
+
+def _smallest(ms, k):
+    """Indices of the k instances with the fewest key switches."""
+    cost = [m.n_chunks + m.n_keyswitch for m in ms]
+    return sorted(range(len(ms)), key=lambda i: (cost[i], i))[:k]
+
+
+def test_c4_full_batch_sampled_oracle_parity():
+    """The whole batched workload (64 uneven SpMVs at N = 2^14) in the launch
+    configuration the bench times -- HE-Mult groups of 226, rotation rounds
+    of 119 chunks, two streams, the alternative NTT split -- with the three
+    instances of fewest key switches compared residue for residue with the
+    oracle's evaluation of each alone."""
+    from paper_2603_04742_gb300.api import Context
+    ring = synth.RING["c4"]
+    logn, L, K, dnum, t = ring
+    insts = synth.workload("c4", count=64)
+    ctx = Context(logn, L, K, dnum, t)
+    ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in insts]
+    ctx.keygen(1, sorted({s for m in ms for s in m.rotation_steps()}))
+    seeds = [(2 + i, 3 + i) for i in range(len(insts))]
+    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=sa) for m, (sa, _) in zip(ms, seeds)]
+    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=sx) for m, (_, x), (_, sx) in zip(ms, insts, seeds)]
+    ctx.set_tuning(226, 119, 1, 0, 0, 0, 2)
+    ys = ctx.spmv_batched(ms, As, Xs)
+    torch.cuda.synchronize()
+    pick = _smallest(ms, 3)
+    assert all(ms[i].n_rot > 0 for i in pick)   # rotations run in each sampled instance
+    steps = sorted({s for i in pick for s in ms[i].rotation_steps()})
+    want = _oracle_results(_oracle(ring, steps, 1), [insts[i] for i in pick], [seeds[i] for i in pick])
+    _assert_equal_results([ys[i] for i in pick], want, "c4 full batch")
+    for m, y, (A, x) in zip(ms, ys, insts):   # and every instance decrypts to A.x
+        assert list(ctx.decrypt(m, y)) == list(A.matvec(x))
+    ctx.set_tuning(0, 0, 0, 0)
+
+
+def test_c5_full_pool_served_sampled_oracle_parity():
+    """The serving pool (32 distinct instances, n up to 16384, at N = 2^15
+    with 8 + 2 primes) served with continuous batching as the bench serves it
+    (3 slots, batches of up to 16), two rounds of every instance; the two
+    instances of fewest key switches compared residue for residue with the
+    oracle, every result decrypted to A.x."""
+    from paper_2603_04742_gb300.api import Context, CtBatch, Server
+    ring = synth.RING["c5"]
+    logn, L, K, dnum, t = ring
+    pool = synth.workload("c5", pool=32)
+    ctx = Context(logn, L, K, dnum, t)
+    ms = [ctx.encode_cssc(a.rows, a.cols, a.rowptr, a.colidx, a.vals) for a, _ in pool]
+    ctx.keygen(1, sorted({s for m in ms for s in m.rotation_steps()}))
+    seeds = [(2 + i, 500 + i) for i in range(len(pool))]
+    As = [ctx.encrypt(m, B.HESPMV_MATRIX, seed=sa) for m, (sa, _) in zip(ms, seeds)]
+    Xs = [ctx.encrypt(m, B.HESPMV_VECTOR, x=x, seed=sx) for m, (_, x), (_, sx) in zip(ms, pool, seeds)]
+    reqs = list(range(len(pool))) * 2
+    ys = [CtBatch.create(ctx, ms[i].n_parts) for i in reqs]
+    torch.cuda.synchronize()
+    srv = Server(ctx, slots=3, mem_budget_bytes=3 * (6 << 30), max_batch=16)
+    tickets = [srv.submit(ms[i], As[i], Xs[i], y) for i, y in zip(reqs, ys)]
+    t0 = time.time()
+    while srv.stats()["completed"] < len(reqs):
+        assert time.time() - t0 < 300, "serving did not finish"
+        time.sleep(0.005)
+    assert all(srv.poll(tk)[0] == 1 for tk in tickets)
+    assert srv.stop(10000) == B.HESPMV_OK
+    pick = _smallest(ms, 2)
+    assert all(ms[i].n_rot > 0 for i in pick)
+    steps = sorted({s for i in pick for s in ms[i].rotation_steps()})
+    want = _oracle_results(_oracle(ring, steps, 1), [pool[i] for i in pick], [seeds[i] for i in pick])
+    for j, i in enumerate(pick):
+        for k, r in enumerate(reqs):
+            if r == i:
+                _assert_equal_results([ys[k]], [want[j]], ("c5 served", i, k))
+    for k, i in enumerate(reqs):
+        A, x = pool[i]
+        assert list(ctx.decrypt(ms[i], ys[k])) == list(A.matvec(x)), k
