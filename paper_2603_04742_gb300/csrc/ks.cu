@@ -67,33 +67,6 @@ __device__ __forceinline__ uint64_t mont_lazy(uint64_t a, uint64_t b, uint64_t c
     return hi + __umul64hi(t, m.q) + (lo != 0);
 }
 
-// A sum of products a * b with a < 2^57 and b < 2^51 (at most 64 of them),
-// kept as its three 32-bit partial-product columns: value = s0 + 2^32 sm +
-// 2^64 sh.  Each product costs four 32 x 32 -> 64-bit multiplies; the
-// column sums cannot overflow (a0 b1 + a1 b0 < 2^58 per product, and a carry
-// out of s0 moves 2^32 into sm).
-struct Acc3 {
-    uint64_t s0 = 0, sm = 0, sh = 0;
-};
-__device__ __forceinline__ void mac3(Acc3 &c, uint64_t a, uint64_t b) {
-    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
-    const uint64_t p0 = (uint64_t)a0 * b0;
-    c.s0 += p0;
-    c.sm += (uint64_t)a0 * b1 + (uint64_t)a1 * b0 + ((uint64_t)(c.s0 < p0) << 32);
-    c.sh += (uint64_t)a1 * b1;
-}
-// the 128-bit value hi:lo of an Acc3
-__device__ __forceinline__ void fold3(const Acc3 &c, uint64_t &hi, uint64_t &lo) {
-    lo = c.s0 + (c.sm << 32);
-    hi = c.sh + (c.sm >> 32) + (lo < c.s0);
-}
-
-__device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
-    const uint64_t m = lo * qneg;
-    uint64_t r = hi + __umul64hi(m, q) + (lo != 0);
-    return r >= q ? r - q : r;
-}
-
 // Launch bounds: the row passes fit 48 registers (5 CTAs, 40 warps per SM)
 // and the final row pass of 2^8 points 64 (4 CTAs) without spilling, which took 8 us off
 // each of the forward and final row passes on the stencil ring; the
@@ -364,9 +337,9 @@ cudaError_t rows_fwd_prepare() {
 // Items vary fastest so a key limb stays in L2 while every item uses it.
 // DN > 0: dnum known at compile time, every digit's loads issued before the
 // first product; DN = 0: any dnum, one digit at a time.
-template <int DN, int IT>
+template <int DN>
 __device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, const KsAdd &ad, const uint64_t *ext,
-                                            const uint64_t *key, uint64_t *acc, int n, int bx, int by) {
+                                            const uint64_t *key, uint64_t *acc, int n, int IT, int bx, int by) {
     // tiles: x = blocks of 256 coefficient pairs, y = l * ceil(n / IT) + item
     // group; IT items per thread share the key loads
     const int N = 1 << a.log2n, LK = a.L + a.K;
@@ -470,10 +443,10 @@ __device__ __forceinline__ void ks_mac_tile(const KsArgs &a, const KsSrc &s, con
     }
 }
 
-template <int DN, int IT>
+template <int DN>
 __global__ __launch_bounds__(256, DN >= 5 ? 2 : 3) void k_ks_mac(KsArgs a, KsSrc s, KsAdd ad, const uint64_t *ext,
-                                                                 const uint64_t *key, uint64_t *acc, int n) {
-    ks_mac_tile<DN, IT>(a, s, ad, ext, key, acc, n, blockIdx.x, blockIdx.y);
+                                                                 const uint64_t *key, uint64_t *acc, int n, int IT) {
+    ks_mac_tile<DN>(a, s, ad, ext, key, acc, n, IT, blockIdx.x, blockIdx.y);
 }
 
 // ModDown conversion of y (P limbs of acc, coefficient domain) to each Q prime
@@ -579,7 +552,8 @@ __global__ __launch_bounds__(kNttThreads, LR >= 8 ? 4 : 1) void k_ks_rows_final(
 // Parts of a column-pass launch of `ctas` CTAs that each make `outputs`
 // limbs: split (doubling) while the launch stays within one wave of 3 CTAs
 // per SM, so key switches of few ciphertexts are not left on a few SMs.
-static int col_parts(int ctas, int outputs) {
+// one wave of 3 CTAs of 256 threads per SM on the current device
+static int wave3() {
     static int wave = 0;
     if (!wave) {
         int dev = 0, sms = 0;
@@ -587,9 +561,25 @@ static int col_parts(int ctas, int outputs) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         wave = 3 * std::max(1, sms);
     }
+    return wave;
+}
+
+static int col_parts(int ctas, int outputs) {
+    const int wave = wave3();
     int parts = 1;
     while (2 * parts <= outputs && 2 * parts * ctas <= wave) parts *= 2;
     return parts;
+}
+
+// Items per thread of the key product (1, 2, 4 or 8): the most that keeps
+// two waves of 3 CTAs per SM, `per_item` CTAs per item group.  A thread's
+// items reuse its key words from L1; fewer, longer CTAs also leave room for
+// the kernels of a second compute stream.
+static int mac_items_per_thread(int n, int per_item) {
+    const int wave = wave3();
+    int it = 8;
+    while (it > 1 && (int64_t)((n + it - 1) / it) * per_item < 2 * wave) it /= 2;
+    return it;
 }
 
 template <int LC, int LR>
@@ -630,14 +620,14 @@ static cudaError_t ks_fused(const Ctx &c, const KsArgs &a, const KsSrc &s, const
     prof_end(c, r, st);
     r = prof_begin(c, "k_ks_mac", st);
     {
-        constexpr int IT = 2;  // items per thread
+        const int IT = mac_items_per_thread(n, (int)(LK * ((N / 2 + 255) / 256)));
         const dim3 g((unsigned)((N / 2 + 255) / 256), (unsigned)(((n + IT - 1) / IT) * LK));
         switch (c.dnum) {
-            case 2: k_ks_mac<2, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 3: k_ks_mac<3, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 4: k_ks_mac<4, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            case 5: k_ks_mac<5, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
-            default: k_ks_mac<0, IT><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n); break;
+            case 2: k_ks_mac<2><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n, IT); break;
+            case 3: k_ks_mac<3><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n, IT); break;
+            case 4: k_ks_mac<4><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n, IT); break;
+            case 5: k_ks_mac<5><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n, IT); break;
+            default: k_ks_mac<0><<<g, 256, 0, st>>>(a, s, ad, ext, key, acc, n, IT); break;
         }
     }
     prof_end(c, r, st);
@@ -701,21 +691,21 @@ __device__ __forceinline__ void mask_tile(const KsArgs &a, const PMask &J, int b
         uint64_t s[4] = {0, 0, 0, 0};
         for (int k0 = 0; k0 < J.nterms; k0 += 4096) {
             const int k1 = min(J.nterms, k0 + 4096);
-            uint64_t hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+            Acc3 c[4];  // residues below q < 2^50: 4096 products fit (modarith.cuh)
             for (int k = k0; k < k1; ++k) {
                 const ulonglong2 *w = (const ulonglong2 *)(J.terms[k] + i0);
                 const ulonglong2 *m = (const ulonglong2 *)(J.masks[k] + r0);
-                const ulonglong2 w0 = w[0], w1 = w[1], m0 = m[0], m1 = m[1];
+                const ulonglong2 w0 = __ldcs(w), w1 = __ldcs(w + 1), m0 = m[0], m1 = m[1];
                 const uint64_t wv[4] = {w0.x, w0.y, w1.x, w1.y}, mv[4] = {m0.x, m0.y, m1.x, m1.y};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const uint64_t pl = wv[e] * mv[e];
-                    lo[e] += pl;
-                    hi[e] += __umul64hi(wv[e], mv[e]) + (lo[e] < pl);
-                }
+                for (int e = 0; e < 4; ++e) mac3(c[e], wv[e], mv[e]);
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) s[e] = add_mod(s[e], redc(hi[e], lo[e], q, qneg), q);
+            for (int e = 0; e < 4; ++e) {
+                uint64_t hi, lo;
+                fold3(c[e], hi, lo);
+                s[e] = add_mod(s[e], redc(hi, lo, q, qneg), q);
+            }
         }
         ulonglong2 *o = (ulonglong2 *)(J.out + i0);
         o[0] = make_ulonglong2(s[0], s[1]);
@@ -772,7 +762,7 @@ __device__ __forceinline__ void pt_rows_fwd(const KsArgs &a, const PInst &I, int
 }
 __device__ __forceinline__ void pt_mac(const KsArgs &a, const PInst &I, int bx, int by) {
     const PScratch w = persist_scratch(a, I);
-    ks_mac_tile<0, 2>(a, I.s, I.ad, w.ext, I.key, w.acc, I.n, bx, by);
+    ks_mac_tile<0>(a, I.s, I.ad, w.ext, I.key, w.acc, I.n, 2, bx, by);
 }
 template <int LR>
 __device__ __forceinline__ void pt_intt_p(const KsArgs &a, const PInst &I, int bx, int by, uint64_t *sm) {

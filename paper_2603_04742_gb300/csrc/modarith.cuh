@@ -88,6 +88,34 @@ __device__ __forceinline__ uint64_t splitmix_at(uint64_t state, uint64_t i) {
     return splitmix_mix(state + (i + 1) * 0x9E3779B97F4A7C15ull);
 }
 
+// A sum of products a * b kept as its three 32-bit partial-product columns:
+// value = s0 + 2^32 sm + 2^64 sh.  Each product costs four 32 x 32 -> 64-bit
+// multiplies.  The column sums cannot overflow while the middle terms
+// a0 b1 + a1 b0 of all products (plus 2^32 per carry out of s0) stay below
+// 2^64: e.g. at most 64 products with a < 2^57, b < 2^51 (< 2^58 each), or
+// 4096 products with a, b < 2^50 (< 2^51 each).
+struct Acc3 {
+    uint64_t s0 = 0, sm = 0, sh = 0;
+};
+__device__ __forceinline__ void mac3(Acc3 &c, uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    const uint64_t p0 = (uint64_t)a0 * b0;
+    c.s0 += p0;
+    c.sm += (uint64_t)a0 * b1 + (uint64_t)a1 * b0 + ((uint64_t)(c.s0 < p0) << 32);
+    c.sh += (uint64_t)a1 * b1;
+}
+// the 128-bit value hi:lo of an Acc3
+__device__ __forceinline__ void fold3(const Acc3 &c, uint64_t &hi, uint64_t &lo) {
+    lo = c.s0 + (c.sm << 32);
+    hi = c.sh + (c.sm >> 32) + (lo < c.s0);
+}
+
+__device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qneg) {
+    const uint64_t m = lo * qneg;
+    uint64_t r = hi + __umul64hi(m, q) + (lo != 0);
+    return r >= q ? r - q : r;
+}
+
 #endif  // __CUDACC__
 
 }  // namespace hespmv

@@ -63,48 +63,72 @@ __global__ void k_cmult(const uint64_t *ct, const uint64_t *pt, uint64_t *out, i
     }
 }
 
+// the Montgomery reduction (times 2^-64 mod q) of an Acc3 below q 2^64
+__device__ __forceinline__ uint64_t acc3_reduce(const Acc3 &c, const ModConst &m) {
+    uint64_t hi, lo;
+    fold3(c, hi, lo);
+    return mont_reduce(hi, lo, m.q, m.qneg);
+}
+
 // out = sum_k w_k * mask_k over the nterms ciphertexts w_k = w0 + k * 2LN
 // (Algorithm 4, inter-chunk aggregation); masks in Montgomery form, 128-bit
 // sums reduced once per block of 4096 terms.  Each thread takes two
 // consecutive words (16-byte loads); the block stages the mask addresses in
-// shared memory, 256 at a time.
-__global__ __launch_bounds__(256) void k_mask_acc(const uint64_t *w0, const uint64_t *const *masks, int nterms,
-                                                  uint64_t *out, int64_t total, int log2n, int L,
-                                                  const ModConst *mc) {
+// shared memory, 256 at a time.  A streaming pass: every term word is read
+// once (evict-first loads), the masks (few distinct, shared by all threads
+// of a word) through the read-only path; four terms' loads are issued before
+// their products so each thread keeps eight 16-byte loads in flight.
+__global__ __launch_bounds__(256, 3) void k_mask_acc(const uint64_t *w0, const uint64_t *const *masks, int nterms,
+                                                     uint64_t *out, int64_t total, int log2n, int L,
+                                                     const ModConst *mc) {
+    constexpr int U = 4;
     __shared__ const uint64_t *sm_masks[256];
     const int64_t LN = (int64_t)L << log2n, CT = 2 * LN;
     const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);  // total = 2LN, even
     const bool active = i < total;
     const int64_t r = active ? i % LN : 0;
     const ModConst m = mc[(int)(r >> log2n)];
-    uint64_t s0 = 0, s1 = 0, h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-    for (int kb = 0; kb < nterms; kb += 256) {
+    // terms and masks are residues below q < 2^50: three-column sums of up to
+    // 4096 products, below 2^112 < q 2^64 for the Montgomery reduction
+    uint64_t s0 = 0, s1 = 0;
+    Acc3 c0, c1;
+    for (int kb = 0; kb < nterms; kb += 256) {  // 256 divides the 4096-term reduction interval
         const int kn = min(256, nterms - kb);
         __syncthreads();
         if ((int)threadIdx.x < kn) sm_masks[threadIdx.x] = masks[kb + threadIdx.x];
         __syncthreads();
         if (!active) continue;
         const uint64_t *w = w0 + (int64_t)kb * CT + i;
-#pragma unroll 4
-        for (int k = 0; k < kn; ++k) {
-            const ulonglong2 a = *(const ulonglong2 *)(w + (int64_t)k * CT);
-            const ulonglong2 b = *(const ulonglong2 *)(sm_masks[k] + r);
-            uint64_t p = a.x * b.x;
-            l0 += p;
-            h0 += __umul64hi(a.x, b.x) + (l0 < p);
-            p = a.y * b.y;
-            l1 += p;
-            h1 += __umul64hi(a.y, b.y) + (l1 < p);
-            if (((kb + k + 1) & 4095) == 0) {  // 4096 terms: reduce before the sum could reach q * 2^64
-                s0 = add_mod(s0, mont_reduce(h0, l0, m.q, m.qneg), m.q);
-                s1 = add_mod(s1, mont_reduce(h1, l1, m.q, m.qneg), m.q);
-                h0 = l0 = h1 = l1 = 0;
+        int k = 0;
+        for (; k + U <= kn; k += U) {
+            ulonglong2 a[U], b[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                a[u] = __ldcs((const ulonglong2 *)(w + (int64_t)(k + u) * CT));
+                b[u] = __ldg((const ulonglong2 *)(sm_masks[k + u] + r));
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                mac3(c0, a[u].x, b[u].x);
+                mac3(c1, a[u].y, b[u].y);
+            }
+        }
+        for (; k < kn; ++k) {
+            const ulonglong2 a = __ldcs((const ulonglong2 *)(w + (int64_t)k * CT));
+            const ulonglong2 b = __ldg((const ulonglong2 *)(sm_masks[k] + r));
+            mac3(c0, a.x, b.x);
+            mac3(c1, a.y, b.y);
+        }
+        if (((kb + kn) & 4095) == 0) {  // 4096 terms: reduce
+            s0 = add_mod(s0, acc3_reduce(c0, m), m.q);
+            s1 = add_mod(s1, acc3_reduce(c1, m), m.q);
+            c0 = Acc3{};
+            c1 = Acc3{};
         }
     }
     if (!active) return;
-    s0 = add_mod(s0, mont_reduce(h0, l0, m.q, m.qneg), m.q);
-    s1 = add_mod(s1, mont_reduce(h1, l1, m.q, m.qneg), m.q);
+    s0 = add_mod(s0, acc3_reduce(c0, m), m.q);
+    s1 = add_mod(s1, acc3_reduce(c1, m), m.q);
     *(ulonglong2 *)(out + i) = make_ulonglong2(s0, s1);
 }
 
