@@ -37,7 +37,8 @@ __global__ void k_rate_barrett(uint64_t *out, ModConst m, int iters) {
     out[t] = r;
 }
 
-// Returns modular multiplications per second (kind 0: Shoup, 1: Barrett).
+// Returns modular multiplications per second (kind 0: Shoup, 1: two variable
+// operands, the Barrett-style mul_mod).
 cudaError_t mulmod_rate(const HostTables &h, int kind, double *rate) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

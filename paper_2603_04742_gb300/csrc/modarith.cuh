@@ -14,10 +14,11 @@ struct ModConst {
     uint64_t w1ninv;  // psi^-1 * N^-1 mod q (last inverse butterfly)
     uint64_t w1ninv_s;
     int32_t k;        // bit length of q
-    int32_t pad;
+    int32_t bs;       // max(0, 2k - 64): shift of the quotient estimate of mul_mod
     uint64_t qneg;    // -q^-1 mod 2^64 (Montgomery reduction)
     uint64_t rmod;    // 2^64 mod q (to Montgomery form)
     uint64_t one_s;   // floor(2^64 / q): Shoup companion of 1 (full reduction)
+    uint64_t bmu;     // floor(2^(64 + bs) / q): quotient factor of mul_mod
 };
 
 #ifdef __CUDACC__
@@ -71,9 +72,35 @@ __device__ __forceinline__ uint64_t barrett_reduce(uint64_t hi, uint64_t lo, uin
     return r;
 }
 
-// a * b mod q for a, b < q.
+// a * b = hi:lo from its four 32 x 32 -> 64-bit partial products (any a, b):
+// the middle sums cannot overflow (each is below 2^64 - 2^32).
+__device__ __forceinline__ void mul_wide(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    const uint64_t p00 = (uint64_t)a0 * b0;
+    const uint64_t mid = (uint64_t)a0 * b1 + (p00 >> 32);
+    const uint64_t mid2 = (uint64_t)a1 * b0 + (uint32_t)mid;
+    lo = (mid2 << 32) | (uint32_t)p00;
+    hi = (uint64_t)a1 * b1 + (mid >> 32) + (mid2 >> 32);
+}
+
+// a * b mod q for a, b < q (any x = a b < 2^(2k), k the bit length of q <= 62).
+// Barrett-style: x1 = x >> s (s = max(0, 2k - 64), so x1 < 2^64) times
+// bmu = floor(2^(64+s) / q), high word, estimates floor(x / q) low by at most
+// two (each floor costs less than one); dropping the low-by-low partial
+// product of that high word costs at most one more, so x - estimate * q,
+// taken mod 2^64, is in [0, 4q).
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const ModConst &m) {
-    return barrett_reduce(__umul64hi(a, b), a * b, m.q, m.mu, m.k);
+    uint64_t hi, lo;
+    mul_wide(a, b, hi, lo);
+    const uint64_t x1 = m.bs ? (hi << (64 - m.bs)) | (lo >> m.bs) : lo;
+    const uint32_t x0 = (uint32_t)x1, x1h = (uint32_t)(x1 >> 32);
+    const uint32_t u0 = (uint32_t)m.bmu, u1 = (uint32_t)(m.bmu >> 32);
+    const uint64_t mid = (uint64_t)x0 * u1;
+    const uint64_t mid2 = (uint64_t)x1h * u0 + (uint32_t)mid;
+    const uint64_t qe = (uint64_t)x1h * u1 + (mid >> 32) + (mid2 >> 32);
+    uint64_t r = lo - qe * m.q;
+    r = r >= 2 * m.q ? r - 2 * m.q : r;
+    return r >= m.q ? r - m.q : r;
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014): output i of the generator with

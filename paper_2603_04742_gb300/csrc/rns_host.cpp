@@ -176,6 +176,8 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
         c.q = q;
         c.k = bitlen(q);
         c.mu = (uint64_t)(((u128)1 << (2 * c.k)) / q);
+        c.bs = std::max(0, 2 * c.k - 64);
+        c.bmu = (uint64_t)(((u128)1 << (64 + c.bs)) / q);
         c.ninv = invm(N % q, q);
         c.ninv_s = shoup(c.ninv, q);
         c.w1ninv = mulm(T[2 * N + 2], c.ninv, q);
