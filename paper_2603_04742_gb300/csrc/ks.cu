@@ -89,7 +89,7 @@ __device__ __forceinline__ void ks_intt_rows_tile(const KsArgs &a, const uint64_
     uint64_t *out = dst + item * ds + (int64_t)k * N + (int64_t)row * M;
     uint64_t v[8];
     load8(v, in + 8 * j);  // = Pass<LR>::last(j, e)
-    inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, itw, q);
+    inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdxW<M>(rr), itw, q);
 #pragma unroll
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
 }
@@ -135,7 +135,7 @@ __device__ __forceinline__ void ks_intt_rows_src_tile(const KsArgs &a, const KsS
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = mul_mod(x[e], y[e], mc);
     }
-    inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, itw, mc.q);
+    inv_body<LR, false>(v, j, (1u << n1) + row, sm, RowIdxW<M>(rr), itw, mc.q);
     uint64_t *out = dst + (int64_t)item * LN + off;
 #pragma unroll
     for (int e = 0; e < 8; ++e) out[Pass<LR>::first(j, e)] = v[e];
@@ -224,7 +224,7 @@ __device__ __forceinline__ void ks_rows_fwd_tile(const KsArgs &a, uint64_t *ext,
     uint64_t v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = x[Pass<LR>::first(j, e)];
-    fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
+    fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdxW<M>(rr), tw, q);
     store8(x + 8 * j, v);
 }
 
@@ -526,7 +526,7 @@ __device__ __forceinline__ void ks_rows_final_tile(const KsArgs &a, const uint64
     load8(xa, acc + ((int64_t)ic * LK + i) * N + rofs + 8 * j);  // fetched before the transform
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = src[Pass<LR>::first(j, e)];
-    fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdx<M>{rr}, tw, q);
+    fwd_body<LR>(v, j, (1u << n1) + row, sm, RowIdxW<M>(rr), tw, q);
     const uint64_t w = a.pinv[2 * i], ws = a.pinv[2 * i + 1];
 #pragma unroll
     for (int e = 0; e < 8; ++e)  // delta < 80q unreduced: (acc + 128q - delta) * P^-1, fully reduced

@@ -186,6 +186,17 @@ struct Pass {
     __device__ static __forceinline__ int last(int j, int e) { return elem_pos<LOGM, LS0, LNS>(j, e); }
 };
 
+// The barrier between the rounds of a pass: the whole CTA, or only the warp
+// when the index map keeps every warp's values in a region of its own (a row
+// tile whose rows are each held by one warp's threads).
+template <class SIdx>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (SIdx::kWarpLocal)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // Forward sub-transform of one tile.  On entry v[e] holds the element at
 // Pass::first(j, e); on return the result at Pass::last(j, e), raised by at
 // most 2q per stage (unreduced).
@@ -196,18 +207,18 @@ __device__ __forceinline__ void fwd_body(uint64_t (&v)[8], int j, uint32_t twb, 
                                          SIdx si, const TwPair *__restrict__ tw, uint64_t q) {
     constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
     fwd_round<LOGM, 0, 3>(v, j, twb, tw, q);
-    __syncthreads();
+    tile_sync<SIdx>();
 #pragma unroll
     for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 0, 3>(j, e))] = v[e];
-    __syncthreads();
+    tile_sync<SIdx>();
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3, R1>(j, e))];
     fwd_round<LOGM, 3, R1>(v, j, twb, tw, q);
     if constexpr (R2 > 0) {
-        __syncthreads();
+        tile_sync<SIdx>();
 #pragma unroll
         for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3, R1>(j, e))] = v[e];
-        __syncthreads();
+        tile_sync<SIdx>();
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))];
         fwd_round<LOGM, 3 + R1, R2>(v, j, twb, tw, q);
@@ -226,18 +237,18 @@ __device__ __forceinline__ void inv_body(uint64_t (&v)[8], int j, uint32_t twb, 
     constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
     if constexpr (R2 > 0) {
         inv_round<LOGM, 3 + R1, R2>(v, j, twb, itw, q);
-        __syncthreads();
+        tile_sync<SIdx>();
 #pragma unroll
         for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3 + R1, R2>(j, e))] = v[e];
-        __syncthreads();
+        tile_sync<SIdx>();
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 3, R1>(j, e))];
     }
     inv_round<LOGM, 3, R1>(v, j, twb, itw, q);
-    __syncthreads();
+    tile_sync<SIdx>();
 #pragma unroll
     for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 3, R1>(j, e))] = v[e];
-    __syncthreads();
+    tile_sync<SIdx>();
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = sm[si(elem_pos<LOGM, 0, 3>(j, e))];
     if constexpr (FOLD)
@@ -250,6 +261,7 @@ __device__ __forceinline__ void inv_body(uint64_t (&v)[8], int j, uint32_t twb, 
 // tiles (TR rows of M words).
 template <int TC>
 struct ColIdx {
+    static constexpr bool kWarpLocal = false;
     int cc;
     __device__ __forceinline__ int operator()(int pos) const { return pos * TC + cc; }
 };
@@ -257,10 +269,21 @@ struct ColIdx {
 // the later rounds fall into distinct banks.
 template <int M>
 struct RowIdx {
+    static constexpr bool kWarpLocal = false;
     int rr;
     __device__ __forceinline__ int operator()(int pos) const {
         return rr * (M + M / 8) + pos + (pos >> 3);
     }
+};
+// The same map for a row tile whose row rr is held by threads rr * M / 8 ..
+// rr * M / 8 + M / 8 - 1 (M <= 256: one warp holds whole rows), so the
+// exchanges between rounds need only warp barriers.  A caller that reuses
+// the shared buffer for anything else separates the uses with a CTA barrier.
+template <int M>
+struct RowIdxW : RowIdx<M> {
+    static_assert(M / 8 <= 32 && 32 % (M / 8) == 0, "a row within one warp");
+    static constexpr bool kWarpLocal = true;
+    __device__ __forceinline__ explicit RowIdxW(int r) : RowIdx<M>{r} {}
 };
 constexpr int kRowTileWords = kNttTile + kNttTile / 8;
 
