@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--persistent", action="store_true",
                     help="one persistent launch per evaluation (no autotuning)")
     ap.add_argument("--tuning", default=None,
-                    help="a fixed schedule instead of autotuning: mult_batch,rot_batch,ntt_split,rows_tma,"
+                    help="a fixed schedule instead of autotuning (c3..c5 and rot): mult_batch,rot_batch,ntt_split,rows_tma,"
                          "persistent,streams (e.g. 14,0,0,0,0,2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -672,7 +672,12 @@ def rotation_block(args, stream):
     ref = y.download()
     t0 = time.perf_counter()
     default_ms = time_steps(lambda: ctx.spmv(m, ca, cx, y=y, stream=stream), stream, 10, lambda: None)
-    tune = ctx.autotune([m], [ca], [cx], reps=3)
+    if args.config == "rot" and args.tuning:  # a fixed schedule (profiling runs)
+        v = [int(x) for x in args.tuning.split(",")]
+        ctx.set_tuning(v[0], v[1], v[2], v[3], v[4], 0, v[5])
+        tune = {"fixed": ctx.get_tuning()}
+    else:
+        tune = ctx.autotune([m], [ca], [cx], reps=3)
     tune["seconds"] = time.perf_counter() - t0
     tune["default_schedule_ms"] = default_ms
     ctx.spmv(m, ca, cx, y=y, stream=stream)
