@@ -1323,7 +1323,8 @@ int hespmv_create(const hespmv_params *p, hespmv_ctx **out) {
               upload(ctx, d.slot_idx, h.slot_idx) && upload(ctx, d.dec, h.dec) &&
               upload(ctx, d.dec_inv_q, h.dec_inv_q) && upload(ctx, d.t_mod, h.t_mod) &&
               upload(ctx, d.ks_zc, h.ks_zc) && upload(ctx, d.ks_yc, h.ks_yc) &&
-              upload(ctx, d.md_phat_t, h.md_phat_t);
+              upload(ctx, d.md_phat_t, h.md_phat_t) && upload(ctx, d.modup_modw, h.modup_modw) &&
+              upload(ctx, d.md_phat_tw, h.md_phat_tw);
     if (ok && h.scheme == HESPMV_SCHEME_BFV)
         ok = upload(ctx, d.bfv_delta, h.bfv_delta) && upload(ctx, d.bfv_const, h.bfv_const);
     if (ok) {

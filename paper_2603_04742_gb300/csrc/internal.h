@@ -59,6 +59,11 @@ struct HostTables {
     std::vector<uint64_t> ks_zc;       // [L][4]
     std::vector<uint64_t> ks_yc;       // [K][4]
     std::vector<uint64_t> md_phat_t;   // [K][L][2]
+    // the same conversion factors times the first forward butterfly stage's
+    // twiddle of the target prime (psi_l^bitrev(1), one per column pass):
+    // the fused conversions form the products of that stage directly
+    std::vector<uint64_t> modup_modw;  // [dnum][alpha][L+K][2]
+    std::vector<uint64_t> md_phat_tw;  // [K][L][2]
 };
 
 // Device copies of the tables.
@@ -81,6 +86,8 @@ struct DevTables {
     uint64_t *ks_zc = nullptr;
     uint64_t *ks_yc = nullptr;
     uint64_t *md_phat_t = nullptr;
+    uint64_t *modup_modw = nullptr;
+    uint64_t *md_phat_tw = nullptr;
     uint64_t *bfv_delta = nullptr;
     uint64_t *bfv_const = nullptr;
     int *err = nullptr;  // device error word written by bounded waits

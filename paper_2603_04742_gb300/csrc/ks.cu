@@ -189,13 +189,16 @@ __device__ __forceinline__ void ks_modup_cols_tile(const KsArgs &a, const uint64
 #pragma unroll
         for (int s = 0; s < AMAX; ++s) {
             if (s < na) {
-                const uint64_t *cst = a.modup_mod + (((int64_t)jd * a.alpha + s) * LK + l) * 2;
-                const uint64_t w = cst[0], ws = cst[1];
+                const int64_t at = (((int64_t)jd * a.alpha + s) * LK + l) * 2;
+                const uint64_t w = a.modup_mod[at], ws = a.modup_mod[at + 1];
+                const uint64_t ww = a.modup_modw[at], wws = a.modup_modw[at + 1];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] += mul_shoup_lazy4(zs[s][e], w, ws, q);  // < 4q each
+                for (int e = 0; e < 4; ++e) v[e] += mul_shoup_lazy4(zs[s][e], w, ws, q);  // < 4q each
+#pragma unroll
+                for (int e = 4; e < 8; ++e) v[e] += mul_shoup_lazy4(zs[s][e], ww, wws, q);  // stage 0's w y
             }
         }
-        fwd_body<LC>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
+        fwd_body<LC, 4 * AMAX>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
         uint64_t *dst = dst0 + (int64_t)l * N;
 #pragma unroll
         for (int e = 0; e < 8; ++e) dst[(int64_t)Pass<LC>::last(j, e) * C] = v[e];
@@ -484,13 +487,16 @@ __device__ __forceinline__ void ks_moddown_cols_tile(const KsArgs &a, const uint
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) {
             if (s < K) {
-                const uint64_t w = a.phat_t[((int64_t)s * L + i) * 2];
-                const uint64_t ws = a.phat_t[((int64_t)s * L + i) * 2 + 1];
+                const int64_t at = ((int64_t)s * L + i) * 2;
+                const uint64_t w = a.phat_t[at], ws = a.phat_t[at + 1];
+                const uint64_t ww = a.phat_tw[at], wws = a.phat_tw[at + 1];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] += mul_shoup_lazy4(ys[s][e], w, ws, q);  // < 4q each
+                for (int e = 0; e < 4; ++e) v[e] += mul_shoup_lazy4(ys[s][e], w, ws, q);  // < 4q each
+#pragma unroll
+                for (int e = 4; e < 8; ++e) v[e] += mul_shoup_lazy4(ys[s][e], ww, wws, q);  // stage 0's w y
             }
         }
-        fwd_body<LC>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
+        fwd_body<LC, 4 * KMAX>(v, j, 1, sm, ColIdx<TC>{cc}, tw, q);
         uint64_t *dst = dh + ((int64_t)ic * L + i) * N + cofs;
 #pragma unroll
         for (int e = 0; e < 8; ++e) dst[(int64_t)Pass<LC>::last(j, e) * C] = v[e];
@@ -951,6 +957,8 @@ static KsArgs ks_args(const Ctx &c) {
     a.yc = h->d.ks_yc;
     a.modup_mod = h->d.modup_mod;
     a.phat_t = h->d.md_phat_t;
+    a.modup_modw = h->d.modup_modw;
+    a.phat_tw = h->d.md_phat_tw;
     a.pinv = h->d.md_pinv;
     a.pmont = h->d.p_mont;
     a.pmont2 = h->d.p_mont2;

@@ -32,7 +32,9 @@ constexpr int kNttTile = 2048;  // words per CTA
 // (x, y) -> (x + w y, x - w y + 4q) without reducing x: w y is taken in
 // [0, 4q), so each stage raises the bound by at most 4q.  Inputs below 16q
 // (base-conversion sums of up to four lazy products) stay below
-// (16 + 4 log2 N) q <= 76q < 2^57 after a whole transform.
+// (16 + 4 log2 N) q <= 76q < 2^57 after a whole transform; when the
+// conversion also forms stage 0's products (below 4 alpha q <= 16q, see
+// fwd_round), that stage adds up to 16q: below 88q < 2^57.
 __device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
     const uint64_t t = mul_shoup_lazy4(y, w, ws, q);
@@ -81,9 +83,14 @@ __device__ __forceinline__ int elem_group(int j, int e, int u) {
 
 typedef ulonglong2 TwPair;  // (w, floor(w 2^64 / q))
 
-template <int LOGM, int S0, int NS>
+// PRE > 0 (first round of a column pass only: S0 = 0, twb = 1, where stage
+// 0 has the single twiddle psi^bitrev(1)): the caller has already formed
+// that stage's products, v[e + 4] = w * y below PRE * q, so stage 0 is
+// (x, t) -> (x + t, x + PRE q - t) without multiplies.
+template <int LOGM, int S0, int NS, int PRE = 0>
 __device__ __forceinline__ void fwd_round(uint64_t (&v)[8], int j, uint32_t twb,
                                           const TwPair *__restrict__ tw, uint64_t q) {
+    static_assert(PRE == 0 || (S0 == 0 && NS == 3), "stage 0 products only in a first round");
     const uint64_t q2 = 2 * q;
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
@@ -91,6 +98,12 @@ __device__ __forceinline__ void fwd_round(uint64_t (&v)[8], int j, uint32_t twb,
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             if ((e & ((1 << NS) - 1)) & dist) continue;
+            if (PRE > 0 && u == 0) {
+                const uint64_t t = v[e + dist];
+                v[e + dist] = v[e] + PRE * q - t;
+                v[e] += t;
+                continue;
+            }
             const uint32_t ti = (twb << (S0 + u)) + elem_group<LOGM, S0, NS>(j, e, u);
             const TwPair p = __ldg(tw + ti);
             ct_bfly(v[e], v[e + dist], p.x, p.y, q, q2);
@@ -202,11 +215,13 @@ __device__ __forceinline__ void tile_sync() {
 // most 2q per stage (unreduced).
 // `si` maps a position to its shared-memory word.  Starts with a barrier, so
 // a CTA can run it repeatedly on the same shared buffer.
-template <int LOGM, class SIdx>
+// PRE > 0: column pass (twb = 1) whose stage-0 products the caller formed
+// (see fwd_round).
+template <int LOGM, int PRE = 0, class SIdx>
 __device__ __forceinline__ void fwd_body(uint64_t (&v)[8], int j, uint32_t twb, uint64_t *sm,
                                          SIdx si, const TwPair *__restrict__ tw, uint64_t q) {
     constexpr int R1 = Sched<LOGM>::R1, R2 = Sched<LOGM>::R2;
-    fwd_round<LOGM, 0, 3>(v, j, twb, tw, q);
+    fwd_round<LOGM, 0, 3, PRE>(v, j, twb, tw, q);
     tile_sync<SIdx>();
 #pragma unroll
     for (int e = 0; e < 8; ++e) sm[si(elem_pos<LOGM, 0, 3>(j, e))] = v[e];

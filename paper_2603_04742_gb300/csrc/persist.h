@@ -15,6 +15,8 @@ struct KsArgs {
     const uint64_t *yc;        // [K][4]  fold constants of step 5
     const uint64_t *modup_mod; // [dnum][alpha][L+K][2]
     const uint64_t *phat_t;    // [K][L][2]  Phat_k * t mod q_i
+    const uint64_t *modup_modw;  // modup_mod times the target prime's first forward twiddle
+    const uint64_t *phat_tw;     // phat_t times the target prime's first forward twiddle
     const uint64_t *pinv;      // [L][2]
     const uint64_t *pmont;     // [L]     P * 2^64 mod q_i
     const uint64_t *pmont2;    // [L]     P * 2^128 mod q_i

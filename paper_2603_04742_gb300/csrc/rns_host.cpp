@@ -305,6 +305,23 @@ bool build_tables(const hespmv_params &p, HostTables &h, std::string &err) {
             h.md_phat_t[((size_t)k * L + i) * 2 + 1] = shoup(w, qi);
         }
     }
+    // conversion factors times the first forward stage's twiddle (pair 1 of
+    // the target prime's forward table)
+    auto w0 = [&](int l) { return h.tw[(size_t)l * 4 * N + 2]; };
+    h.modup_modw.assign(h.modup_mod.size(), 0);
+    for (size_t at = 0; at < h.modup_mod.size(); at += 2) {
+        const int l = (int)((at / 2) % LK);
+        const uint64_t ql = h.q[l], v = mulm(h.modup_mod[at], w0(l), ql);
+        h.modup_modw[at] = v;
+        h.modup_modw[at + 1] = shoup(v, ql);
+    }
+    h.md_phat_tw.assign(h.md_phat_t.size(), 0);
+    for (size_t at = 0; at < h.md_phat_t.size(); at += 2) {
+        const int i = (int)((at / 2) % L);
+        const uint64_t qi = h.q[i], v = mulm(h.md_phat_t[at], w0(i), qi);
+        h.md_phat_tw[at] = v;
+        h.md_phat_tw[at + 1] = shoup(v, qi);
+    }
     if (bfv && !bfv_tables(p, h, err)) return false;
     // batching slot positions
     h.slot_idx.resize(N);
